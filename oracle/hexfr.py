@@ -1,0 +1,299 @@
+"""Hexahedral FR residual for the compressible Navier-Stokes equations (oracle; test infrastructure only).
+
+Follows the section "FR Algorithm" of arXiv 2308.06605 step by step, in plain FP64 with dense
+per-element operators built as Kronecker products of the 1D arrays of `basis`:
+
+  Eq. 1   Q^ = |J| Q, F^_d = sum_j S_dj F_j with S = |J| J^-1 (J_ij = dx_i/dxi_j), from the
+          trilinear map of each hexahedron.
+  Eq. 2   nodal Lagrange interpolants on the N^3 tensor Gauss-Legendre points; point index
+          m = i + N j + N^2 k (i along xi, j along eta, k along zeta).
+  Eq. 3   dQ/dt = -|J|^-1 [ sum_d D_d F^_d + sum_faces C_f (F^I_perp - F_perp) ] + S, where
+          F_perp is the interpolated transformed flux dotted with the outward reference normal,
+          F^I_perp the common normal flux (Rusanov) times the area-scaled physical normal, and
+          C_f the divergence of the face's correction field: along the face's normal line it
+          takes the values g_R'(s xi_i) (s = outward sign), the DG-equivalent choice.
+  Viscous part (BR2; the paper uses LDG, this build's reading takes BR2): the common solution
+  Q^I = (Q- + Q+)/2 corrects the reference gradient with the same correction fields,
+  grad_x Q = J^-T grad_xi Q; at each face the side gradient is the uncorrected gradient
+  interpolated to the face plus eta times the face's own lifting r_f interpolated to the face;
+  the common gradient is the average of the two sides; the common viscous flux is
+  F_v(Q^I, common gradient) . n.
+  Time: classical four-stage Runge-Kutta.
+
+Reference faces: f = 2 d + (s + 1)/2, i.e. 0: xi=-1, 1: xi=+1, 2: eta=-1, 3: eta=+1,
+4: zeta=-1, 5: zeta=+1.  Flux points of face f are ordered by the two remaining axes with the
+lower axis fastest.
+
+Connectivity is found geometrically: faces are paired by their (periodically shifted)
+centroids, flux points by their physical coordinates.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+from . import gas
+from .basis import Basis1D
+
+FACE_AXIS = (0, 0, 1, 1, 2, 2)
+FACE_SIGN = (-1, 1, -1, 1, -1, 1)
+HEX_REF_VERTS = np.array([
+    [-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+    [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.float64)
+
+BC_WALL_ISOTHERMAL = 1
+BC_CHAR_INFLOW = 2
+BC_CHAR_OUTFLOW = 3
+BC_DIRICHLET = 4
+
+
+def trilinear_geometry(X, ref):
+    """Physical points, Jacobian determinant and S = |J| J^-1 of trilinear hexahedra.
+
+    X: [E][8][3] vertex coordinates, ref: [M][3] reference points.  Shape functions
+    N_v = prod_a (1 + c_va xi_a)/2 with c_v the reference vertex coordinates.
+    Returns x [E][M][3], detJ [E][M], S [E][M][3][3] with S[d][j] = |J| (J^-1)_dj.
+    """
+    c = HEX_REF_VERTS
+    fac = (1.0 + ref[:, None, :] * c[None, :, :]) / 2.0          # [M][8][3]
+    Nv = np.prod(fac, axis=2)                                    # [M][8]
+    dN = np.empty(ref.shape[:1] + (8, 3))                        # dN_v/dxi_b
+    for b in range(3):
+        others = [a for a in range(3) if a != b]
+        dN[:, :, b] = (c[None, :, b] / 2.0) * fac[:, :, others[0]] * fac[:, :, others[1]]
+    x = np.einsum('mv,evi->emi', Nv, X)
+    J = np.einsum('mvb,evi->emib', dN, X)                        # J[i][b] = dx_i/dxi_b
+    detJ = np.linalg.det(J)
+    S = detJ[..., None, None] * np.linalg.inv(J)
+    return x, detJ, S
+
+
+class HexFR:
+    """Oracle FR discretisation of one hexahedral mesh at uniform order p."""
+
+    def __init__(self, desc, phys, p: int):
+        self.phys = phys
+        self.p = p
+        self.b = b = Basis1D(p)
+        self.N = N = p + 1
+        self.Np = N ** 3
+        self.Nf = N * N
+        I = np.eye(N)
+        D = b.D
+        self.Dop = [np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)), np.kron(D, np.kron(I, I))]
+        self.Lf, self.Cf = [], []
+        for f in range(6):
+            d, s = FACE_AXIS[f], FACE_SIGN[f]
+            row = (b.l_plus if s > 0 else b.l_minus)[None, :]
+            col = (b.h_plus if s > 0 else b.h_minus)[:, None]
+            if d == 0:
+                self.Lf.append(np.kron(I, np.kron(I, row)))
+                self.Cf.append(np.kron(I, np.kron(I, col)))
+            elif d == 1:
+                self.Lf.append(np.kron(I, np.kron(row, I)))
+                self.Cf.append(np.kron(I, np.kron(col, I)))
+            else:
+                self.Lf.append(np.kron(row, np.kron(I, I)))
+                self.Cf.append(np.kron(col, np.kron(I, I)))
+        xi = b.nodes
+        K, Jj, Ii = np.meshgrid(xi, xi, xi, indexing="ij")        # [k][j][i]
+        self.ref_sol = np.stack([Ii.ravel(), Jj.ravel(), K.ravel()], axis=1)
+        self.ref_face = []
+        for f in range(6):
+            d, s = FACE_AXIS[f], FACE_SIGN[f]
+            A, B = np.meshgrid(xi, xi, indexing="ij")             # [slow][fast]
+            pts = np.zeros((self.Nf, 3))
+            tang = [a for a in range(3) if a != d]
+            pts[:, tang[0]] = B.ravel()
+            pts[:, tang[1]] = A.ravel()
+            pts[:, d] = s
+            self.ref_face.append(pts)
+        self._geometry(desc)
+        self._connect(desc)
+
+    # ------------------------------------------------------------------ geometry (Eq. 1)
+    def _geometry(self, desc):
+        X = desc.xyz[desc.hex]
+        self.E = X.shape[0]
+        self.x, self.detJ, self.S = trilinear_geometry(X, self.ref_sol)
+        if np.any(self.detJ <= 0):
+            raise ValueError("non-positive Jacobian")
+        self.xf = np.empty((self.E, 6, self.Nf, 3))
+        self.nf = np.empty((self.E, 6, self.Nf, 3))                # area-scaled outward normal
+        for f in range(6):
+            xf, _, Sf = trilinear_geometry(X, self.ref_face[f])
+            self.xf[:, f] = xf
+            self.nf[:, f] = FACE_SIGN[f] * Sf[:, :, FACE_AXIS[f], :]
+        w = self.b.weights
+        W = np.kron(w, np.kron(w, w))                             # quadrature weights at m
+        self.W = W
+        self.vol = np.sum(W[None, :] * self.detJ, axis=1)
+        self.h = self.vol ** (1.0 / 3.0)
+
+    # ------------------------------------------------------------------ connectivity
+    def _connect(self, desc):
+        E, N = self.E, self.N
+        corner_ids = [np.where(HEX_REF_VERTS[:, FACE_AXIS[f]] == FACE_SIGN[f])[0] for f in range(6)]
+        btag = {tuple(sorted(nodes)): int(t) for nodes, t in zip(desc.bface_nodes.tolist(), desc.bface_tag.tolist())}
+        shift_of_tag = {}
+        for per in desc.periodic:
+            shift_of_tag[per.tag_b] = np.asarray(per.t, dtype=np.float64)
+            shift_of_tag.setdefault(per.tag_a, np.zeros(3))
+        bc_of_tag = {bc.tag: bc for bc in desc.bcs}
+        cent = np.empty((E * 6, 3))
+        shift = np.zeros((E * 6, 3))
+        face_tag = np.zeros(E * 6, dtype=np.int64)
+        for e in range(E):
+            for f in range(6):
+                nodes = desc.hex[e, corner_ids[f]]
+                cent[6 * e + f] = desc.xyz[nodes].mean(axis=0)
+                face_tag[6 * e + f] = btag.get(tuple(sorted(nodes.tolist())), 0)
+        bc_faces = []
+        pairable = np.ones(E * 6, dtype=bool)
+        for g in range(E * 6):
+            t = face_tag[g]
+            if t == 0:
+                continue
+            if t in shift_of_tag:
+                shift[g] = shift_of_tag[t]
+            elif t in bc_of_tag:
+                bc_faces.append(g)
+                pairable[g] = False
+            else:
+                raise ValueError(f"boundary tag {t} has no boundary condition")
+        idx = np.where(pairable)[0]
+        key = cent[idx] - shift[idx]
+        hmin = float(np.min(self.h))
+        tree = cKDTree(key)
+        pairs = np.array(sorted(tree.query_pairs(r=1e-6 * hmin)), dtype=np.int64).reshape(-1, 2)
+        if len(pairs) * 2 != len(idx) or len(np.unique(pairs)) != len(idx):
+            raise ValueError("unmatched or multiply matched faces")
+        gL, gR = idx[pairs[:, 0]], idx[pairs[:, 1]]
+        self.eL, self.fL = gL // 6, gL % 6
+        self.eR, self.fR = gR // 6, gR % 6
+        xL = self.xf[self.eL, self.fL] - shift[gL][:, None, :]
+        xR = self.xf[self.eR, self.fR] - shift[gR][:, None, :]
+        dist = np.linalg.norm(xL[:, :, None, :] - xR[:, None, :, :], axis=-1)
+        self.perm = np.argmin(dist, axis=2)                       # R fpt matching L fpt q
+        if np.max(np.min(dist, axis=2)) > 1e-6 * hmin:
+            raise ValueError("flux points do not match across an interface")
+        self.invperm = np.argsort(self.perm, axis=1)
+        P = len(gL)
+        self.n_if = P
+        rows = np.arange(P)[:, None]
+        self.nL = self.nf[self.eL, self.fL]
+        self.nR_matched = self.nf[self.eR, self.fR][rows, self.perm]
+        bc_faces = np.array(bc_faces, dtype=np.int64)
+        self.bE, self.bF = bc_faces // 6, bc_faces % 6
+        self.b_kind = np.array([bc_of_tag[face_tag[g]].kind for g in bc_faces], dtype=np.int64)
+        self.b_params = [np.asarray(bc_of_tag[face_tag[g]].params, dtype=np.float64) for g in bc_faces]
+
+    # ------------------------------------------------------------------ helpers
+    def solution_points(self):
+        """Physical coordinates of the solution points, [E][N^3][3] in canonical order."""
+        return self.x.copy()
+
+    def _interp_faces(self, A):
+        """A [E][Np][...] -> [E][6][Nf][...] values at the flux points of each face."""
+        return np.stack([np.einsum('qm,em...->eq...', self.Lf[f], A) for f in range(6)], axis=1)
+
+    def _lift(self, f, B):
+        """C_f applied to face data B [E][Nf][...] -> [E][Np][...]."""
+        return np.einsum('mq,eq...->em...', self.Cf[f], B)
+
+    def _ghost(self, Qm, k):
+        """Ghost state behind boundary face k given the interior trace Qm [Nf][5]."""
+        kind = self.b_kind[k]
+        if kind == BC_DIRICHLET:
+            return np.broadcast_to(self.b_params[k][:5], Qm.shape).copy()
+        raise NotImplementedError("boundary kind %d not in the oracle yet" % kind)
+
+    # ------------------------------------------------------------------ residual (Eq. 3)
+    def residual(self, Q, t=0.0):
+        """dQ/dt at the solution points; Q and the result are [E][N^3][5]."""
+        ph = self.phys
+        gam = ph.gamma
+        viscous = ph.viscous != 0 and ph.mu != 0.0
+        E, Nf = self.E, self.Nf
+        rows = np.arange(self.n_if)[:, None]
+        # Solution at flux points, both sides of every interface.
+        Qf = self._interp_faces(Q)                                 # [E][6][Nf][5]
+        QL = Qf[self.eL, self.fL]
+        QR = Qf[self.eR, self.fR][rows, self.perm]
+        Qc_face = np.empty_like(Qf)                                # common solution per element face
+        QI = 0.5 * (QL + QR)
+        Qc_face[self.eL, self.fL] = QI
+        Qc_face[self.eR, self.fR] = QI[rows, self.invperm]
+        ghosts = []
+        for k in range(len(self.bE)):
+            Qm = Qf[self.bE[k], self.bF[k]]
+            Qp = self._ghost(Qm, k)
+            ghosts.append(Qp)
+            Qc_face[self.bE[k], self.bF[k]] = 0.5 * (Qm + Qp)
+        dQ = Qc_face - Qf                                          # Q^I - Q- per element face
+        Sinv = self.S / self.detJ[..., None, None]                 # J^-1, [E][Np][d][j]
+        if viscous:
+            # Reference gradients: uncorrected D_d Q, corrected adds sum_f s_f C_f dQ_f on axis d_f.
+            g_unc = np.stack([np.einsum('mn,env->emv', self.Dop[d], Q) for d in range(3)], axis=2)  # [E][Np][d][5]
+            g_cor = g_unc.copy()
+            lifts = []
+            for f in range(6):
+                lf = FACE_SIGN[f] * self._lift(f, dQ[:, f])        # [E][Np][5]
+                g_cor[:, :, FACE_AXIS[f], :] += lf
+                lifts.append(lf)
+            grad = np.einsum('emdj,emdv->emjv', Sinv, g_cor)       # physical, corrected
+            grad_unc = np.einsum('emdj,emdv->emjv', Sinv, g_unc)
+            # Face gradient per side: interpolated uncorrected gradient + eta * own lift r_f.
+            gface = np.empty((E, 6, Nf, 3, 5))
+            for f in range(6):
+                r_f = np.einsum('emj,emv->emjv', Sinv[:, :, FACE_AXIS[f], :], lifts[f])
+                gface[:, f] = np.einsum('qm,emjv->eqjv', self.Lf[f], grad_unc + ph.br2_eta * r_f)
+            Fv = gas.viscous_flux(Q, grad, gam, ph.R, ph.mu, ph.Pr)
+        # Physical and transformed flux at solution points.
+        H = gas.inviscid_flux(Q, gam)                              # [E][Np][j][5]
+        if viscous:
+            H = H - Fv
+        Hhat = np.einsum('emdj,emjv->emdv', self.S, H)             # [E][Np][d][5]
+        div = sum(np.einsum('mn,env->emv', self.Dop[d], Hhat[:, :, d, :]) for d in range(3))
+        # Own normal flux at the flux points (interpolated transformed flux . outward normal).
+        Fperp = np.stack([FACE_SIGN[f] * np.einsum('qm,emv->eqv', self.Lf[f], Hhat[:, :, FACE_AXIS[f], :])
+                          for f in range(6)], axis=1)              # [E][6][Nf][5]
+        # Common normal flux along side L's normal.
+        FI = gas.rusanov(QL, QR, self.nL, gam)
+        if viscous:
+            gL = gface[self.eL, self.fL]
+            gR = gface[self.eR, self.fR][rows, self.perm]
+            gc = 0.5 * (gL + gR)
+            FI = FI - np.einsum('pqjv,pqj->pqv', gas.viscous_flux(QI, gc, gam, ph.R, ph.mu, ph.Pr), self.nL)
+        Fc = np.empty_like(Fperp)
+        Fc[self.eL, self.fL] = FI
+        Fc[self.eR, self.fR] = -FI[rows, self.invperm]
+        for k in range(len(self.bE)):
+            e, f = self.bE[k], self.bF[k]
+            n = self.nf[e, f]
+            Qm, Qp = Qf[e, f], ghosts[k]
+            Fb = gas.rusanov(Qm, Qp, n, gam)
+            if viscous:
+                Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(0.5 * (Qm + Qp), gface[e, f], gam, ph.R, ph.mu, ph.Pr), n)
+            Fc[e, f] = Fb
+        corr = sum(self._lift(f, Fc[:, f] - Fperp[:, f]) for f in range(6))
+        return -(div + corr) / self.detJ[..., None]
+
+    # ------------------------------------------------------------------ time integration
+    def rk44_step(self, Q, t, dt):
+        """Classical four-stage Runge-Kutta step."""
+        k1 = self.residual(Q, t)
+        k2 = self.residual(Q + 0.5 * dt * k1, t + 0.5 * dt)
+        k3 = self.residual(Q + 0.5 * dt * k2, t + 0.5 * dt)
+        k4 = self.residual(Q + dt * k3, t + dt)
+        return Q + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+    def max_dt(self, Q, cfl):
+        """dt = CFL min_e h_e / ((2p+1) max_pts(|u| + c)), h_e = vol_e^{1/3}."""
+        rho, u, p = gas.primitives(Q, self.phys.gamma)
+        lam = np.sqrt(np.sum(u * u, axis=-1)) + np.sqrt(self.phys.gamma * p / rho)
+        return cfl * float(np.min(self.h / ((2 * self.p + 1) * np.max(lam, axis=1))))
+
+    def integrate(self, Q, w=None):
+        """Quadrature sum_e sum_m W_m |J|_m Q_m per variable (the discrete integral over the mesh)."""
+        return np.einsum('m,em,emv->v', self.W, self.detJ, Q)

@@ -1,0 +1,293 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the oracle.
+
+This module holds workload definitions only: hexahedral box meshes (with optional element
+shuffling, random local vertex rotations and interior-node perturbation), boundary tags,
+periodic pairings, and the initial-condition fields (Taylor-Green vortex, isentropic vortex,
+uniform flow) as functions of physical coordinates.  It contains none of the flux-reconstruction
+arithmetic: no basis, no operators, no fluxes.  Both the CUDA library and the oracle receive the
+same arrays from here and build everything else on their own.
+
+Vertex order of a hexahedron follows VTK/CGNS: bottom face (zeta=-1) counter-clockwise seen
+from inside +zeta, then the top face in the same order.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+# Boundary-condition kinds (match the C enum in include/fr.h).
+BC_WALL_ISOTHERMAL = 1      # no-slip isothermal wall, params[0] = T_wall
+BC_CHAR_INFLOW = 2          # characteristic subsonic inflow, params = (p0, T0, nx, ny, nz)
+BC_CHAR_OUTFLOW = 3         # characteristic subsonic outflow, params[0] = p_static
+BC_DIRICHLET = 4            # exact-state ghost, params = (rho, rhou, rhov, rhow, E)
+
+# Reference coordinates of the 8 hex vertices in VTK order.
+HEX_REF_VERTS = np.array([
+    [-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+    [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.int64)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n uint64 draws of the splitmix64 generator (Steele, Lea & Flood 2014) from `seed`."""
+    out = np.empty(n, dtype=np.uint64)
+    s = int(seed) & 0xFFFFFFFFFFFFFFFF
+    for i in range(n):
+        s = (s + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+        z = s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+        out[i] = z ^ (z >> 31)
+    return out
+
+
+def splitmix64_uniform(seed: int, n: int) -> np.ndarray:
+    """n doubles in [0,1) from the top 53 bits of splitmix64 draws."""
+    return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass
+class BC:
+    tag: int
+    kind: int
+    params: Tuple[float, ...] = ()
+
+
+@dataclass
+class Periodic:
+    """Faces tagged `tag_b` are the faces tagged `tag_a` translated by `t`."""
+    tag_a: int
+    tag_b: int
+    t: Tuple[float, float, float]
+
+
+@dataclass
+class MeshDesc:
+    xyz: np.ndarray                     # [n_nodes][3] float64
+    hex: np.ndarray                     # [E][8] int64 node ids, VTK order
+    bface_nodes: np.ndarray             # [nb][4] int64 node ids of each boundary quad
+    bface_tag: np.ndarray               # [nb] int32
+    periodic: List[Periodic] = field(default_factory=list)
+    bcs: List[BC] = field(default_factory=list)
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.hex.shape[0])
+
+
+def cube_rotations() -> np.ndarray:
+    """The 24 proper rotations of the cube as signed 3x3 permutation matrices (det = +1)."""
+    mats = []
+    for perm in [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]:
+        for sx in (1, -1):
+            for sy in (1, -1):
+                for sz in (1, -1):
+                    m = np.zeros((3, 3), dtype=np.int64)
+                    for r, (c, s) in enumerate(zip(perm, (sx, sy, sz))):
+                        m[r, c] = s
+                    if round(np.linalg.det(m)) == 1:
+                        mats.append(m)
+    assert len(mats) == 24
+    return np.array(mats)
+
+
+def rotation_vertex_permutations() -> np.ndarray:
+    """[24][8]: new local vertex k takes the old local vertex perm[r][k].
+
+    Rotating the reference frame maps reference vertex k to R @ c_k; the element's shape is
+    unchanged, only its local frame changes.
+    """
+    lookup = {tuple(v): i for i, v in enumerate(HEX_REF_VERTS.tolist())}
+    perms = []
+    for R in cube_rotations():
+        perms.append([lookup[tuple((R @ c).tolist())] for c in HEX_REF_VERTS])
+    return np.array(perms, dtype=np.int64)
+
+
+def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
+                 periodic=(True, True, True), seed: int | None = None,
+                 shuffle: bool = False, rotate: bool = False, perturb: float = 0.0,
+                 wall_tags: dict | None = None, affine=None) -> MeshDesc:
+    """Structured box of nx*ny*nz hexahedra stored as an unstructured mesh.
+
+    Boundary faces are tagged 1..6 for x-, x+, y-, y+, z-, z+.  Periodic axes pair (1,2), (3,4),
+    (5,6) with the box length as translation.  `perturb` moves interior nodes by a seeded
+    uniform displacement of that fraction of the local spacing (straight-sided trilinear
+    elements).  `shuffle` permutes the element order and `rotate` applies a random one of the
+    24 cube rotations to each element's local vertex order; both are seeded.  `affine` (3x3)
+    maps the box about `lo` (x -> lo + A (x - lo)), giving a sheared lattice of parallelepipeds;
+    periodic translations are mapped with it.
+    """
+    nx, ny, nz = (int(v) for v in n)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    rng = np.random.default_rng(seed if seed is not None else 0)
+    xs = [np.linspace(lo[a], hi[a], m + 1) for a, m in enumerate((nx, ny, nz))]
+    X, Y, Z = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
+    xyz = np.stack([X, Y, Z], axis=-1)            # [nx+1][ny+1][nz+1][3]
+    if perturb > 0.0:
+        h = (hi - lo) / np.array([nx, ny, nz])
+        d = rng.uniform(-perturb, perturb, size=xyz.shape) * h
+        interior = np.zeros(xyz.shape[:3], dtype=bool)
+        interior[1:-1, 1:-1, 1:-1] = True
+        xyz = xyz + d * interior[..., None]
+    nid = np.arange((nx + 1) * (ny + 1) * (nz + 1)).reshape(nx + 1, ny + 1, nz + 1)
+    xyz = xyz.reshape(-1, 3)
+    A = np.eye(3) if affine is None else np.asarray(affine, dtype=np.float64)
+    xyz = lo[None, :] + (xyz - lo[None, :]) @ A.T
+    hexes = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                hexes.append([nid[i, j, k], nid[i + 1, j, k], nid[i + 1, j + 1, k], nid[i, j + 1, k],
+                              nid[i, j, k + 1], nid[i + 1, j, k + 1], nid[i + 1, j + 1, k + 1],
+                              nid[i, j + 1, k + 1]])
+    hexes = np.array(hexes, dtype=np.int64)
+    # Boundary quads with tags.
+    bnodes, btags = [], []
+    for j in range(ny):
+        for k in range(nz):
+            bnodes.append([nid[0, j, k], nid[0, j + 1, k], nid[0, j + 1, k + 1], nid[0, j, k + 1]]); btags.append(1)
+            bnodes.append([nid[nx, j, k], nid[nx, j + 1, k], nid[nx, j + 1, k + 1], nid[nx, j, k + 1]]); btags.append(2)
+    for i in range(nx):
+        for k in range(nz):
+            bnodes.append([nid[i, 0, k], nid[i + 1, 0, k], nid[i + 1, 0, k + 1], nid[i, 0, k + 1]]); btags.append(3)
+            bnodes.append([nid[i, ny, k], nid[i + 1, ny, k], nid[i + 1, ny, k + 1], nid[i, ny, k + 1]]); btags.append(4)
+    for i in range(nx):
+        for j in range(ny):
+            bnodes.append([nid[i, j, 0], nid[i + 1, j, 0], nid[i + 1, j + 1, 0], nid[i, j + 1, 0]]); btags.append(5)
+            bnodes.append([nid[i, j, nz], nid[i + 1, j, nz], nid[i + 1, j + 1, nz], nid[i, j + 1, nz]]); btags.append(6)
+    per = []
+    L = hi - lo
+    for a in range(3):
+        if periodic[a]:
+            t = np.zeros(3)
+            t[a] = float(L[a])
+            per.append(Periodic(2 * a + 1, 2 * a + 2, tuple(float(v) for v in A @ t)))
+    bcs = []
+    if wall_tags:
+        for tag, (kind, params) in wall_tags.items():
+            bcs.append(BC(int(tag), int(kind), tuple(float(v) for v in params)))
+    if rotate:
+        perms = rotation_vertex_permutations()
+        r = rng.integers(0, 24, size=hexes.shape[0])
+        hexes = np.take_along_axis(hexes, perms[r], axis=1)
+    if shuffle:
+        hexes = hexes[rng.permutation(hexes.shape[0])]
+    return MeshDesc(xyz=np.ascontiguousarray(xyz, dtype=np.float64),
+                    hex=np.ascontiguousarray(hexes, dtype=np.int64),
+                    bface_nodes=np.array(bnodes, dtype=np.int64).reshape(-1, 4),
+                    bface_tag=np.array(btags, dtype=np.int32),
+                    periodic=per, bcs=bcs)
+
+
+# ---------------------------------------------------------------------------------------------
+# Physical parameters and initial conditions (functions of physical coordinates only).
+# ---------------------------------------------------------------------------------------------
+
+@dataclass
+class Physics:
+    gamma: float = 1.4
+    R: float = 1.0
+    mu: float = 0.0
+    Pr: float = 0.71
+    inviscid_flux: int = 0      # 0 = Rusanov, 1 = Roe
+    viscous: int = 1            # 0 = Euler, 1 = BR2
+    br2_eta: float = 6.0
+    vcjh_c: float = 0.0
+    precision: int = 0          # 0 = FP64, 1 = mixed (FP32 element operators)
+
+
+def tgv_physics(Ma: float = 0.1, Re: float = 1600.0, gamma: float = 1.4, Pr: float = 0.71) -> Physics:
+    """Taylor-Green vortex in units rho0 = V0 = L = T0 = 1, p0 = 1/(gamma Ma^2), R = p0."""
+    p0 = 1.0 / (gamma * Ma * Ma)
+    return Physics(gamma=gamma, R=p0, mu=1.0 / Re, Pr=Pr, viscous=1, br2_eta=6.0)
+
+
+def conserved(rho, u, v, w, p, gamma):
+    """Stack primitive fields into conserved variables (rho, rho u, rho v, rho w, E) on the last axis."""
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E], axis=-1)
+
+
+def tgv_state(x: np.ndarray, Ma: float = 0.1, gamma: float = 1.4, perturb: float = 0.0,
+              seed: int = 0) -> np.ndarray:
+    """Taylor-Green vortex at points x[..., 3] (conserved variables on the last axis).
+
+    Velocity u = sin x cos y cos z, v = -cos x sin y cos z, w = 0; pressure
+    p = p0 + (cos 2x + cos 2y)(cos 2z + 2)/16 with p0 = 1/(gamma Ma^2); density from the ideal
+    gas law at uniform temperature T0 = 1 (R = p0).  `perturb` > 0 adds a seeded sum of
+    random-phase Fourier modes (wavenumbers 1..3) of that amplitude to the three velocities.
+    """
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    p0 = 1.0 / (gamma * Ma * Ma)
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = np.zeros_like(X)
+    p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        vel = [u, v, w]
+        for c in range(3):
+            for _ in range(4):
+                kv = rng.integers(1, 4, size=3)
+                ph = rng.uniform(0, 2 * np.pi)
+                vel[c] = vel[c] + perturb * np.sin(kv[0] * X + kv[1] * Y + kv[2] * Z + ph)
+        u, v, w = vel
+    rho = p / p0
+    return conserved(rho, u, v, w, p, gamma)
+
+
+def isentropic_vortex_state(x: np.ndarray, t: float = 0.0, centre=(0.0, 0.0), beta: float = 5.0,
+                            Ma: float = 0.5, direction=(1.0, 1.0), gamma: float = 1.4,
+                            period=None) -> np.ndarray:
+    """Isentropic (Shu-type) vortex in the x-y plane, uniform in z, exact for the Euler equations.
+
+    Free stream rho = 1, p = 1 (so T = p/rho = 1 with R = 1) and speed Ma * sqrt(gamma) along
+    `direction`.  The perturbation about the advected centre is
+    du = -beta/(2 pi) e^{(1-r^2)/2} (y - yc), dv = beta/(2 pi) e^{(1-r^2)/2} (x - xc),
+    dT = -(gamma-1) beta^2/(8 gamma pi^2) e^{1-r^2}, with rho = T^{1/(gamma-1)}, p = rho T.
+    With `period` = (Lx, Ly) the nearest periodic image of the centre is used.
+    """
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    U = Ma * np.sqrt(gamma)
+    u0, v0 = U * d[0], U * d[1]
+    xc = centre[0] + u0 * t
+    yc = centre[1] + v0 * t
+    dx = x[..., 0] - xc
+    dy = x[..., 1] - yc
+    if period is not None:
+        dx = dx - period[0] * np.round(dx / period[0])
+        dy = dy - period[1] * np.round(dy / period[1])
+    r2 = dx * dx + dy * dy
+    f = np.exp(0.5 * (1.0 - r2))
+    u = u0 - beta / (2 * np.pi) * f * dy
+    v = v0 + beta / (2 * np.pi) * f * dx
+    T = 1.0 - (gamma - 1.0) * beta * beta / (8.0 * gamma * np.pi * np.pi) * f * f
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return conserved(rho, u, v, np.zeros_like(u), p, gamma)
+
+
+def uniform_state(shape, rho=1.0, vel=(0.3, 0.2, 0.1), p=None, gamma=1.4) -> np.ndarray:
+    """Uniform flow (free stream) of the given shape; default p = 1/gamma."""
+    if p is None:
+        p = 1.0 / gamma
+    one = np.ones(shape)
+    return conserved(rho * one, vel[0] * one, vel[1] * one, vel[2] * one, p * one, gamma)
+
+
+def vortex_ensemble(n_cases: int = 64, seed0: int = 0):
+    """Case list of a batched isentropic-vortex ensemble: per case i (seed i) an edge count
+    n ~ U{8..24}, an order p ~ U{2..5} and a vortex centre ~ U(domain), all from splitmix64."""
+    cases = []
+    for i in range(n_cases):
+        r = splitmix64_uniform(seed0 + i, 4)
+        n = 8 + int(r[0] * 17)
+        p = 2 + int(r[1] * 4)
+        L = 20.0
+        cases.append(dict(seed=seed0 + i, n=n, p=p, L=L,
+                          centre=(-L / 2 + L * r[2], -L / 2 + L * r[3])))
+    return cases

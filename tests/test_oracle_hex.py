@@ -1,0 +1,180 @@
+"""Pins of the oracle's 3D hexahedral FR residual and RK44 against properties the method fixes (CPU)."""
+import numpy as np
+import pytest
+
+from paper_2308_06605_gb300 import inputs as I
+from oracle import gas
+from oracle.hexfr import HexFR
+
+
+def _flux_scale(m, Q):
+    F = gas.inviscid_flux(Q, m.phys.gamma)
+    return np.abs(F).max() / m.h.min()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kind", ["affine", "rotated", "perturbed"])
+def test_free_stream_preservation(p, kind):
+    """Uniform flow is an exact steady solution: max|R| <= 1e-13 max|F|/h_min."""
+    if kind == "affine":
+        d = I.hex_box_mesh((3, 2, 2), affine=[[1, 0.2, 0], [0, 1, 0.1], [0.1, 0, 1]])
+    elif kind == "rotated":
+        d = I.hex_box_mesh((3, 3, 2), seed=p, shuffle=True, rotate=True)
+    else:
+        d = I.hex_box_mesh((3, 3, 3), seed=p, perturb=0.2, rotate=True)
+    m = HexFR(d, I.tgv_physics(), p)
+    Q = I.uniform_state(m.x.shape[:2])
+    R = m.residual(Q)
+    assert np.abs(R).max() <= 1e-13 * _flux_scale(m, Q)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_discrete_conservation_periodic(p):
+    """On a periodic mesh the quadrature-weighted residual sums to zero per variable."""
+    d = I.hex_box_mesh((3, 3, 3), seed=7, perturb=0.15, rotate=True, shuffle=True)
+    m = HexFR(d, I.tgv_physics(Ma=0.3, Re=200.0), p)
+    Q = I.tgv_state(m.x, Ma=0.3, perturb=1e-2, seed=p)
+    R = m.residual(Q)
+    s = np.abs(m.integrate(R))
+    a = np.einsum('m,em,emv->v', m.W, m.detJ, np.abs(R))
+    assert np.all(s <= 1e-12 * a), s / a
+
+
+def _match_points(ma, mb):
+    """Map solution points of mesh b onto mesh a by physical coordinates: idx with xb.flat[idx] = xa."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(mb.x.reshape(-1, 3))
+    dist, idx = tree.query(ma.x.reshape(-1, 3))
+    assert dist.max() < 1e-9
+    return idx
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_orientation_and_ordering_invariance(p):
+    """Random local vertex rotations (24 per element) and element shuffling leave R unchanged."""
+    phys = I.tgv_physics(Ma=0.2, Re=400.0)
+    ma = HexFR(I.hex_box_mesh((3, 3, 3)), phys, p)
+    mb = HexFR(I.hex_box_mesh((3, 3, 3), seed=11, rotate=True, shuffle=True), phys, p)
+    Qa = I.tgv_state(ma.x, Ma=0.2, perturb=1e-2, seed=1)
+    Qb = I.tgv_state(mb.x, Ma=0.2, perturb=1e-2, seed=1)
+    Ra = ma.residual(Qa)
+    Rb = mb.residual(Qb)
+    idx = _match_points(ma, mb)
+    np.testing.assert_allclose(Rb.reshape(-1, 5)[idx], Ra.reshape(-1, 5), rtol=0,
+                               atol=1e-12 * np.abs(Ra).max())
+
+
+def test_axis_permutation_symmetry():
+    """Cycling the axes of mesh and initial state cycles the momentum residuals."""
+    phys = I.tgv_physics(Ma=0.2, Re=400.0)
+    m = HexFR(I.hex_box_mesh((3, 2, 2), hi=(3.0, 2.0, 2.5)), phys, 2)
+    mp_ = HexFR(I.hex_box_mesh((2, 3, 2), hi=(2.5, 3.0, 2.0)), phys, 2)   # (x,y,z) -> (y,z,x)
+    def state(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        rho = 1 + 0.1 * np.sin(2 * np.pi * X / 3) * np.cos(2 * np.pi * Z / 2.5)
+        u = 0.2 * np.cos(2 * np.pi * Y / 2)
+        v = 0.1 * np.sin(2 * np.pi * Z / 2.5 + 1)
+        w = 0.15 * np.sin(2 * np.pi * X / 3)
+        p = 10 + 0.3 * np.cos(2 * np.pi * (X / 3 + Y / 2))
+        return rho, u, v, w, p
+    Q = I.conserved(*state(m.x), 1.4)
+    # Permuted point x' = (X2, X0, X1) of the original point X, so X = (x'_1, x'_2, x'_0).
+    xo = np.stack([mp_.x[..., 1], mp_.x[..., 2], mp_.x[..., 0]], axis=-1)
+    rho, u, v, w, p = state(xo)
+    Qp = I.conserved(rho, w, u, v, p, 1.4)
+    R = m.residual(Q)
+    Rp = mp_.residual(Qp)
+    from scipy.spatial import cKDTree
+    idx = cKDTree(xo.reshape(-1, 3)).query(m.x.reshape(-1, 3))[1]
+    Rp = Rp.reshape(-1, 5)[idx]
+    want = R.reshape(-1, 5)[:, [0, 3, 1, 2, 4]]
+    np.testing.assert_allclose(Rp, want, rtol=0, atol=1e-11 * np.abs(R).max())
+
+
+def test_gas_fluxes_closed_forms():
+    g, Rg, mu, Pr = 1.4, 2.0, 0.3, 0.7
+    rho, u, p = 1.3, np.array([0.4, -0.2, 0.1]), 2.5
+    Q = I.conserved(np.array(rho), *[np.array(c) for c in u], np.array(p), g)
+    F = gas.inviscid_flux(Q, g)
+    E = p / (g - 1) + 0.5 * rho * u @ u
+    for j in range(3):
+        want = np.concatenate([[rho * u[j]], rho * u * u[j] + p * np.eye(3)[j], [(E + p) * u[j]]])
+        np.testing.assert_allclose(F[j], want, rtol=1e-15)
+    # Couette-like linear velocity u_x = a y with uniform rho, p: tau_xy = mu a, heat flux from T.
+    a = 0.7
+    grad = np.zeros((3, 5))
+    grad[1, 1] = rho * a                             # d(rho u)/dy
+    grad[1, 4] = rho * u[0] * a                      # dE/dy (kinetic part only, p uniform)
+    Fv = gas.viscous_flux(Q, grad, g, Rg, mu, Pr)
+    np.testing.assert_allclose(Fv[1, 1], mu * a, rtol=1e-14)
+    np.testing.assert_allclose(Fv[0, 2], mu * a, rtol=1e-14)
+    np.testing.assert_allclose(Fv[1, 4], u[0] * mu * a, rtol=1e-13, atol=1e-15)
+    # Pure temperature gradient at rest: q_j = -kappa dT/dx_j with kappa = mu cp / Pr.
+    Q0 = I.conserved(np.array(rho), np.array(0.0), np.array(0.0), np.array(0.0), np.array(p), g)
+    grad = np.zeros((3, 5))
+    dTdz = 0.9
+    grad[2, 4] = rho * Rg / (g - 1) * dTdz           # dE/dz = rho cv dT/dz at fixed rho
+    Fv = gas.viscous_flux(Q0, grad, g, Rg, mu, Pr)
+    kappa = mu * (g * Rg / (g - 1)) / Pr
+    np.testing.assert_allclose(Fv[2, 4], kappa * dTdz, rtol=1e-14)
+    np.testing.assert_allclose(Fv[:, 1:4], 0, atol=1e-15)
+
+
+def test_rusanov_consistency_and_antisymmetry():
+    rng = np.random.default_rng(0)
+    n = rng.standard_normal((10, 3))
+    QA = I.conserved(1 + 0.2 * rng.random(10), *(0.3 * rng.standard_normal((3, 10))), 1 + 0.2 * rng.random(10), 1.4)
+    QB = I.conserved(1 + 0.2 * rng.random(10), *(0.3 * rng.standard_normal((3, 10))), 1 + 0.2 * rng.random(10), 1.4)
+    FA = np.einsum('kjv,kj->kv', gas.inviscid_flux(QA, 1.4), n)
+    np.testing.assert_allclose(gas.rusanov(QA, QA, n, 1.4), FA, rtol=1e-14)
+    np.testing.assert_allclose(gas.rusanov(QA, QB, n, 1.4), -gas.rusanov(QB, QA, -n, 1.4), rtol=1e-14)
+
+
+def test_rk44_linear_ode_taylor_polynomial():
+    """For R(Q) = lambda Q one RK44 step multiplies by 1 + z + z^2/2 + z^3/6 + z^4/24, z = lambda dt."""
+    m = HexFR(I.hex_box_mesh((2, 2, 2)), I.tgv_physics(), 1)
+    lam, dt = -1.7, 0.3
+    m.residual = lambda Q, t=0.0: lam * Q
+    Q0 = np.random.default_rng(0).random((8, 8, 5))
+    z = lam * dt
+    np.testing.assert_allclose(m.rk44_step(Q0, 0.0, dt), Q0 * (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24), rtol=1e-15)
+
+
+def test_tgv_energy_and_dissipation():
+    """TGV at t = 0 (Ma = 0.1): kinetic energy ~ vol/8 and dK/dt ~ -mu int |omega|^2 = -6 pi^3 mu."""
+    phys = I.tgv_physics(Ma=0.1, Re=1600.0)
+    m = HexFR(I.hex_box_mesh((6, 6, 6)), phys, 3)
+    Q = I.tgv_state(m.x, Ma=0.1)
+    rho, u, _ = gas.primitives(Q, phys.gamma)
+    ke = np.einsum('m,em,em->', m.W, m.detJ, 0.5 * rho * np.sum(u * u, axis=-1))
+    vol = (2 * np.pi) ** 3
+    assert abs(ke / (vol / 8) - 1) < 2e-3
+    R = m.residual(Q)
+    dke = np.einsum('m,em,em->', m.W, m.detJ, np.sum(u * R[..., 1:4], axis=-1) - 0.5 * np.sum(u * u, axis=-1) * R[..., 0])
+    want = -6 * np.pi ** 3 * phys.mu
+    assert abs(dke / want - 1) < 2e-2, dke / want
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_isentropic_vortex_convergence(p):
+    """Euler, exact advected vortex: L2 error after a short time converges at >= p + 1 - 0.2."""
+    phys = I.Physics(gamma=1.4, R=1.0, mu=0.0, viscous=0)
+    Lh = 7.0                      # periodic images of the Gaussian tail are below 1e-10
+    levels = {1: (8, 16, 32), 2: (8, 16, 32), 3: (6, 12, 24)}[p]
+    errs = []
+    t_end = 0.2
+    for n in levels:
+        h = 2 * Lh / n
+        d = I.hex_box_mesh((n, n, 1), lo=(-Lh, -Lh, 0.0), hi=(Lh, Lh, h))
+        m = HexFR(d, phys, p)
+        kw = dict(beta=5.0, Ma=0.5, centre=(0.0, 0.0), period=(2 * Lh, 2 * Lh))
+        Q = I.isentropic_vortex_state(m.x, 0.0, **kw)
+        nsteps = int(np.ceil(t_end / (0.1 * h / (p + 1))))
+        dt = t_end / nsteps
+        for s in range(nsteps):
+            Q = m.rk44_step(Q, s * dt, dt)
+        ex = I.isentropic_vortex_state(m.x, t_end, **kw)
+        errs.append(np.sqrt(np.einsum('m,em,em->', m.W, m.detJ, (Q[..., 0] - ex[..., 0]) ** 2)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] >= p + 1 - 0.2, (errs, rates)
