@@ -1,0 +1,274 @@
+"""Benchmark: solution-point RK-stage updates/s of the FR residual + RK44 stage update.
+
+Workload: Taylor-Green vortex (Ma 0.1, Re 1600) on a periodic 64^3 hexahedral mesh at p = 4
+(125 Gauss-Legendre points per element, 32.8 M solution points, 164 M unknowns), compressible
+Navier-Stokes with Rusanov + BR2 fluxes and the DG-equivalent correction; FP64 path.
+One step = one RK44 time step = 4 RK stages (each: residual + stage update); the metric counts
+solution points x stages per second.  Inputs are synthetic and seeded; the device working set
+(~18 GB) is far larger than L2, so no flush is needed between iterations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the path has no
+data exchange between GPUs at this size: "replicas only"), timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solution-pt RK-stage updates/s at p=3..7, mixed-prec vs FP64, at stated error"
+UNIT = "updates/s"
+N_EDGE, ORDER, CFL = 64, 4, 0.3
+WORKLOAD = "tgv_64cube_p4_fp64"
+
+
+def config(precision="fp64"):
+    n_pts = N_EDGE ** 3 * (ORDER + 1) ** 3
+    return {"workload": WORKLOAD, "mesh": f"{N_EDGE}^3 periodic hex [0,2pi]^3", "p": ORDER,
+            "n_points": n_pts, "unknowns": 5 * n_pts, "case": "TGV Ma=0.1 Re=1600 gamma=1.4 Pr=0.71",
+            "flux": "Rusanov + BR2, VCJH c=0 (DG)", "integrator": "RK44, CFL 0.3", "precision": precision,
+            "l2": "no flush: working set ~18 GB >> 129 MB L2"}
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [s.strip() for s in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(budget_s=12.0, max_steps=None, n=8, p=ORDER):
+    """Time the oracle (as it stands) on an n^3, order-p periodic TGV: RK44 steps until the
+    budget is used.  Returns (updates/s, sample description, threads used)."""
+    from oracle.hexfr import HexFR
+    from paper_2308_06605_gb300 import inputs as I
+    m = HexFR(I.hex_box_mesh((n, n, n)), I.tgv_physics(), p)
+    Q = I.tgv_state(m.x)
+    dt = m.max_dt(Q, CFL)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        Q = m.rk44_step(Q, 0.0, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps and steps >= max_steps) or (not max_steps and el >= budget_s):
+            break
+    rate = m.E * m.Np * 4 * steps / el
+    return rate, f"oracle RK44 on {n}^3 hex p={p} TGV ({m.E * m.Np} points), {steps} steps in {el:.1f} s", 1
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_rate(max_steps=1)
+    t0 = time.perf_counter()
+    rate, sample, cores = oracle_rate(max_steps=args.steps)
+    el = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU path
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_2308_06605_gb300 import fr, inputs as I, perfmodel
+    if not os.path.exists(fr.LIB_PATH):
+        from paper_2308_06605_gb300 import build as B
+        B.build()
+    fr.load()
+    stream = torch.cuda.current_stream()
+    desc = I.hex_box_mesh((N_EDGE, N_EDGE, N_EDGE))
+    phys = I.tgv_physics()
+    mesh = fr.Mesh(desc, phys, ORDER, stream=stream.cuda_stream)
+    x = mesh.solution_points()
+    Q0 = np.ascontiguousarray(I.tgv_state(x, Ma=0.1))
+    del x
+    Qd = torch.from_numpy(Q0).to(f"cuda:{dev}")
+    mesh.set_state(Qd)
+    dt = mesh.max_dt(CFL)
+    n_pts = mesh.n_elem * mesh.n_pts
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def step(t):
+        for s in range(4):
+            mesh.rk_stage(s, t, dt)
+
+    t = 0.0
+    for _ in range(args.warmup):
+        step(t)
+        t += dt
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else str(dev))
+    sampler = ClockSampler(gid)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(t)
+        t += dt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n_pts * 4 * args.steps / (ms * 1e-3)
+
+    # Per-kernel device times over the same number of steps (events on the launching stream).
+    mesh.profile(True)
+    for _ in range(args.steps):
+        step(t)
+        t += dt
+    kms, kcnt = mesh.profile_read(4)
+    mesh.profile(False)
+    kernels = {}
+    fl = perfmodel.flops_per_point(ORDER)
+    by = perfmodel.bytes_per_point(ORDER)
+    for k, name in enumerate(perfmodel.KERNELS):
+        avg = kms[k] / max(1, kcnt[k])
+        kernels[name] = {"launches": kcnt[k], "avg_ms": avg, "share": kms[k] / max(1e-30, sum(kms)),
+                         "gflops": fl[name] * n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None,
+                         "gbs": by[name] * n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None}
+    dom = max(kernels, key=lambda n_: kernels[n_]["share"])
+    fp64_peak = fr.probe_fma(0, 4000)
+    ach = kernels[dom]["gflops"] * 1e9
+    roofline = {"bound": "alu", "kernel": dom, "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "measured FP64 DFMA rate of this GPU (fr_probe_fma, 8 chains x 152x8 blocks)",
+                "algorithmic_flops_per_point": fl[dom], "algorithmic_bytes_per_point": by[dom]}
+
+    # End to end through the public API with host buffers: set_state from pinned host memory,
+    # four stages, get_state back to pinned host memory, every step.
+    Qh = torch.from_numpy(Q0).pin_memory()
+    Out = torch.empty_like(Qh).pin_memory()
+    k_e2e = max(1, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(k_e2e):
+        mesh.set_state(Qh)
+        step(0.0)
+        mesh.get_state(out=Out)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    if world > 1:
+        tt = torch.tensor([te], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": world * n_pts * 4 * k_e2e / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8)}
+    mesh.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(),
+            "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * 4 * args.steps, "roofline": roofline,
+            "kernels": kernels, "fp64_fma_peak_tflops": fp64_peak / 1e12}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, cores = oracle_rate(budget_s=12.0)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

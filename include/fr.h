@@ -1,0 +1,180 @@
+/*
+ * fr.h — C ABI of the GB300 flux-reconstruction (FR) library.
+ *
+ * The library evaluates the semi-discrete FR residual of the compressible Navier–Stokes
+ * equations on unstructured hexahedral meshes at orders p = 1..7 and advances it with explicit
+ * Runge–Kutta stages, all on one CUDA device (arXiv 2308.06605, section "FR Algorithm",
+ * Eq. 1–3).  Plain C types only; device pointers are raw CUDA pointers, host pointers are plain
+ * host memory.  Every call returns an fr_status; nothing aborts.
+ *
+ * Conventions (all calls):
+ *  - Canonical state layout is [element][point][variable], elements in input order, points
+ *    m = i + N j + N^2 k (N = p + 1) on ascending Gauss–Legendre nodes along the element's
+ *    reference axes xi, eta, zeta, variables (rho, rho u, rho v, rho w, E).  Reference vertex
+ *    order of a hexahedron follows VTK/CGNS (bottom face counter-clockwise, then top face).
+ *  - The library copies every host array it is given at create time; pointers passed to other
+ *    calls are borrowed for the duration of the call only.
+ *  - All device work is enqueued on the stream given to fr_mesh_create (0 = legacy default
+ *    stream).  Calls with FR_DEVICE pointers return without synchronising; calls with FR_HOST
+ *    pointers synchronise that stream before returning.
+ *  - After FR_ECUDA or FR_ETIMEOUT a mesh is poisoned: every later call except fr_free and
+ *    fr_last_error returns the same status.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FR_OK = 0,
+  FR_EINVAL = 1,        /* bad argument (NULL pointer, out-of-range value) */
+  FR_ENOMEM = 2,        /* host or device allocation failed */
+  FR_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed (mesh poisoned) */
+  FR_EMESH = 4,         /* invalid mesh: unmatched face, unknown tag, non-positive Jacobian */
+  FR_EUNSUPPORTED = 5,  /* valid request that this build does not implement */
+  FR_ENONFINITE = 6,    /* a non-finite value appeared in the updated state */
+  FR_ETIMEOUT = 7       /* a bounded device-side wait expired (mesh poisoned) */
+} fr_status;
+
+enum { FR_HOST = 0, FR_DEVICE = 1 };                       /* where a state pointer lives */
+enum { FR_RUSANOV = 0, FR_ROE = 1 };                       /* inviscid common flux */
+enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1 };                /* viscous treatment */
+enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1 };              /* arithmetic of the element operators */
+enum { FR_RK44 = 0 };                                      /* classical four-stage Runge–Kutta */
+enum {                                                     /* boundary-condition kinds */
+  FR_BC_WALL_ISOTHERMAL = 1,  /* params[0] = wall temperature */
+  FR_BC_CHAR_INFLOW = 2,      /* params = total pressure, total temperature, flow direction (3) */
+  FR_BC_CHAR_OUTFLOW = 3,     /* params[0] = static pressure */
+  FR_BC_DIRICHLET = 4         /* params[0..4] = exterior conserved state */
+};
+
+typedef struct fr_mesh fr_mesh;                            /* opaque, owned by the library */
+
+typedef struct {
+  int32_t tag;          /* boundary tag as used in fr_mesh_desc.bface_tag */
+  int32_t kind;         /* FR_BC_* */
+  double params[8];
+} fr_bc;
+
+typedef struct {
+  int32_t tag_a, tag_b; /* faces tagged tag_b are the faces tagged tag_a translated by t */
+  double t[3];
+} fr_periodic;
+
+typedef struct {
+  int64_t n_nodes;
+  const double *xyz;            /* [n_nodes][3] vertex coordinates (host) */
+  int64_t n_hex;
+  const int64_t *hex;           /* [n_hex][8] vertex ids, VTK order (host) */
+  int32_t p;                    /* polynomial order, 1..7, uniform over the mesh */
+  int64_t n_bface;
+  const int64_t *bface_nodes;   /* [n_bface][4] vertex ids of each boundary quadrilateral */
+  const int32_t *bface_tag;     /* [n_bface] */
+  int32_t n_bc;
+  const fr_bc *bc;              /* [n_bc] tag -> condition */
+  int32_t n_periodic;
+  const fr_periodic *periodic;  /* [n_periodic] */
+} fr_mesh_desc;
+
+typedef struct {
+  double gamma;         /* ratio of specific heats */
+  double R;             /* gas constant (p = rho R T) */
+  double mu;            /* dynamic viscosity (constant) */
+  double Pr;            /* Prandtl number */
+  int32_t inviscid;     /* FR_RUSANOV | FR_ROE */
+  int32_t viscous;      /* FR_VISC_NONE | FR_VISC_BR2 */
+  double br2_eta;       /* BR2 penalty factor (number of faces, 6, by default) */
+  int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED */
+} fr_physics;
+
+typedef struct {
+  int64_t n_elem;       /* elements */
+  int32_t p, n_pts;     /* order and solution points per element ((p+1)^3) */
+  int64_t n_iface;      /* interior + periodic interfaces */
+  int64_t n_bface;      /* boundary-condition faces */
+  int64_t device_bytes; /* device memory held by the mesh */
+} fr_mesh_info;
+
+/*
+ * fr_mesh_create — build connectivity, geometry and device buffers (section "FR Algorithm",
+ * Eq. 1: |J| and S = |J| J^-1 at the solution points; the paper's face construction: faces are
+ * keyed by their sorted vertex ids, sorted so coupled faces are adjacent, then paired).
+ * Periodic faces are paired by translated centroids.  Validates everything before allocating
+ * device memory: unmatched interior faces, boundary faces without a condition, non-positive
+ * Jacobians -> FR_EMESH; p outside 1..7, NULL arrays, bad physics -> FR_EINVAL.  `stream` is a
+ * cudaStream_t cast to uintptr_t.  On success *out owns all device memory until fr_free.
+ */
+fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
+                         fr_mesh **out);
+
+/* fr_mesh_query — sizes of a created mesh (host struct filled). */
+fr_status fr_mesh_query(const fr_mesh *mesh, fr_mesh_info *info);
+
+/*
+ * fr_solution_points — physical coordinates of the solution points, [n_elem][n_pts][3] in the
+ * canonical order, written to host memory (Eq. 2: the nodal points of the element map).
+ */
+fr_status fr_solution_points(fr_mesh *mesh, double *xyz_host);
+
+/*
+ * fr_set_state / fr_get_state — copy the solution Q (canonical layout, n_elem*n_pts*5 doubles)
+ * into / out of the mesh.  `where` = FR_HOST or FR_DEVICE.  fr_set_state also resets the
+ * Runge–Kutta registers (the solution becomes the start of a new step).
+ */
+fr_status fr_set_state(fr_mesh *mesh, const double *Q, int32_t where);
+fr_status fr_get_state(fr_mesh *mesh, double *Q, int32_t where);
+
+/*
+ * fr_residual — R = dQ/dt of the current state (Eq. 3: -|J|^-1 [div_xi F^ + sum over faces and
+ * flux points of div(g) (F^I_perp - F_perp)] with the DG-equivalent correction, the Rusanov
+ * common flux and the BR2 viscous flux), written in the canonical layout to R (FR_HOST or
+ * FR_DEVICE).  `t` is the physical time (used by time-dependent boundary data).
+ */
+fr_status fr_residual(fr_mesh *mesh, double t, double *R, int32_t where);
+
+/*
+ * fr_rk_stage — one stage of the explicit Runge–Kutta scheme (the paper advances Eq. 3 with an
+ * explicit RK method; this library provides classical RK44).  Stage k in 0..3 evaluates the
+ * residual of the current stage state at time t + c_k dt and updates, in FP64,
+ *   acc += b_k dt R,  U = U_n + a_{k+1} dt R       (k < 3)
+ *   U_n = U_n + acc + b_3 dt R,  U = U_n           (k = 3)
+ * with a = (1/2, 1/2, 1), b = (1/6, 1/3, 1/3, 1/6).  Stages must be called in order 0,1,2,3;
+ * `t` is the time at the start of the step.  Returns FR_ENONFINITE (checked at stage 3 only) if
+ * a non-finite value was written.
+ */
+fr_status fr_rk_stage(fr_mesh *mesh, int32_t scheme, int32_t stage, double t, double dt);
+
+/*
+ * fr_max_dt — dt = cfl * min_e h_e / ((2p + 1) max over the element's points of (|u| + c)),
+ * h_e = volume^(1/3): an explicit-stability estimate (not specified by the paper).
+ */
+fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
+
+/*
+ * Instrumentation (not part of the method).  fr_profile(mesh, 1) makes every later residual
+ * evaluation record CUDA events around each of its kernels on the mesh's stream;
+ * fr_profile_read accumulates, per kernel k < n, the summed device time in milliseconds
+ * (ms[k]) and the number of launches (launches[k]) since profiling was enabled, synchronising
+ * the stream first.  Kernel order: 0 face interpolation, 1 volume, 2 interface flux,
+ * 3 correction + update.  fr_profile(mesh, 0) stops recording and clears the totals.
+ */
+#define FR_N_KERNELS 4
+fr_status fr_profile(fr_mesh *mesh, int32_t enable);
+fr_status fr_profile_read(fr_mesh *mesh, double *ms, int64_t *launches, int32_t n);
+
+/* fr_free — release all host and device memory of the mesh (NULL-safe). */
+void fr_free(fr_mesh *mesh);
+
+/* fr_last_error — human-readable message of the last failing call on `mesh` (or of the last
+ * failing fr_mesh_create when mesh is NULL).  Owned by the library. */
+const char *fr_last_error(const fr_mesh *mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_H */

@@ -1,0 +1,354 @@
+// C ABI (include/fr.h): mesh lifetime, state transfer, residual and RK44 stages.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fr_device.hpp"
+
+using namespace frx;
+
+struct fr_mesh {
+  HostMesh host;            // keeps xsol for fr_solution_points; bulk arrays released after upload
+  fr_physics phys{};
+  DevPhys dphys{};
+  DevMesh dev{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  fr_status poisoned = FR_OK;
+  std::string err;
+  int64_t bytes = 0;
+  double *h_scalar = nullptr;   // pinned host scalar for dt / flags
+  // Instrumentation: one event set per recorded residual evaluation.
+  bool profiling = false;
+  std::vector<PhaseEvents> ev_pool;
+  size_t ev_used = 0;
+};
+
+static void clear_events(fr_mesh *m) {
+  for (PhaseEvents &p : m->ev_pool)
+    for (int k = 0; k < 4; ++k) {
+      cudaEventDestroy(p.start[k]);
+      cudaEventDestroy(p.stop[k]);
+    }
+  m->ev_pool.clear();
+  m->ev_used = 0;
+}
+
+// Next event set when profiling, else null.
+static const PhaseEvents *next_events(fr_mesh *m) {
+  if (!m->profiling) return nullptr;
+  if (m->ev_used == m->ev_pool.size()) {
+    PhaseEvents p;
+    for (int k = 0; k < 4; ++k) {
+      if (cudaEventCreate(&p.start[k]) != cudaSuccess || cudaEventCreate(&p.stop[k]) != cudaSuccess) return nullptr;
+    }
+    m->ev_pool.push_back(p);
+  }
+  return &m->ev_pool[m->ev_used++];
+}
+
+static std::string g_create_error;
+static std::mutex g_mutex;
+
+static fr_status fail(fr_mesh *m, fr_status st, const std::string &msg) {
+  if (m) {
+    m->err = msg;
+    if (st == FR_ECUDA || st == FR_ETIMEOUT) m->poisoned = st;
+  } else {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    g_create_error = msg;
+  }
+  return st;
+}
+
+static fr_status cuda_fail(fr_mesh *m, cudaError_t e, const char *what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(m, FR_ECUDA, msg);
+}
+
+#define FR_CUDA(m, call)                                 \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(m, e_, #call); \
+  } while (0)
+
+static fr_status check_mesh(fr_mesh *m) {
+  if (!m) return FR_EINVAL;
+  if (m->poisoned != FR_OK) return m->poisoned;
+  return FR_OK;
+}
+
+static void release(fr_mesh *m) {
+  DevMesh &d = m->dev;
+  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf};
+  for (double *p : dbl)
+    if (p) cudaFree(p);
+  if (d.ef) cudaFree(d.ef);
+  if (d.if_bc) cudaFree(d.if_bc);
+  if (d.bcs) cudaFree(d.bcs);
+  if (d.flag) cudaFree(d.flag);
+  if (m->h_scalar) cudaFreeHost(m->h_scalar);
+  d = DevMesh{};
+  m->h_scalar = nullptr;
+}
+
+template <typename T>
+static fr_status dalloc(fr_mesh *m, T **p, size_t count) {
+  size_t bytes = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(m, e == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  m->bytes += (int64_t)bytes;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
+                                    fr_mesh **out) {
+  if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!desc || !phys) return fail(nullptr, FR_EINVAL, "desc or phys is NULL");
+  if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
+  if (desc->n_hex <= 0 || !desc->hex || desc->n_nodes <= 0 || !desc->xyz)
+    return fail(nullptr, FR_EINVAL, "empty mesh or NULL arrays");
+  if (desc->n_bface < 0 || (desc->n_bface > 0 && (!desc->bface_nodes || !desc->bface_tag)))
+    return fail(nullptr, FR_EINVAL, "bad boundary-face arrays");
+  if (desc->n_bc < 0 || (desc->n_bc > 0 && !desc->bc) || desc->n_periodic < 0 ||
+      (desc->n_periodic > 0 && !desc->periodic))
+    return fail(nullptr, FR_EINVAL, "bad boundary-condition or periodic arrays");
+  if (!(phys->gamma > 1.0) || !(phys->R > 0.0) || !(phys->mu >= 0.0) || !(phys->Pr > 0.0) ||
+      !(phys->br2_eta >= 0.0))
+    return fail(nullptr, FR_EINVAL, "bad physical parameters");
+  if (phys->inviscid != FR_RUSANOV) return fail(nullptr, FR_EUNSUPPORTED, "only the Rusanov flux is built");
+  if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2)
+    return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
+  if (phys->precision != FR_PREC_FP64) return fail(nullptr, FR_EUNSUPPORTED, "only FP64 is built");
+
+  fr_mesh *m = new (std::nothrow) fr_mesh();
+  if (!m) return fail(nullptr, FR_ENOMEM, "host allocation failed");
+  std::string err;
+  fr_status st;
+  try {
+    st = build_host_mesh(desc, m->host, err);
+  } catch (const std::bad_alloc &) {
+    st = FR_ENOMEM;
+    err = "host allocation failed while building the mesh";
+  }
+  if (st != FR_OK) {
+    delete m;
+    return fail(nullptr, st, err);
+  }
+  if (m->host.n_if > m->host.n_interior) {
+    delete m;
+    return fail(nullptr, FR_EUNSUPPORTED, "boundary-condition faces are not built in this version");
+  }
+  m->phys = *phys;
+  m->stream = (cudaStream_t)stream;
+  DevPhys &dp = m->dphys;
+  dp.gamma = phys->gamma;
+  dp.R = phys->R;
+  dp.mu = phys->mu;
+  dp.kappa = phys->mu * phys->gamma * phys->R / ((phys->gamma - 1.0) * phys->Pr);
+  dp.eta = phys->br2_eta;
+  dp.viscous = (phys->viscous == FR_VISC_BR2 && phys->mu > 0.0) ? 1 : 0;
+  dp.inviscid = phys->inviscid;
+
+  auto bail = [&](fr_status s) {
+    std::string msg = m->err;
+    release(m);
+    delete m;
+    return fail(nullptr, s, msg);
+  };
+  cudaError_t ce = cudaGetDevice(&m->device);
+  if (ce != cudaSuccess) { m->err = cudaGetErrorString(ce); return bail(FR_ECUDA); }
+  {
+    static bool uploaded[64] = {false};
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (m->device < 64 && !uploaded[m->device]) {
+      ce = upload_basis_tables();
+      if (ce != cudaSuccess) { m->err = std::string("basis upload: ") + cudaGetErrorString(ce); }
+      else uploaded[m->device] = true;
+    }
+  }
+  if (ce != cudaSuccess) return bail(FR_ECUDA);
+  HostMesh &h = m->host;
+  DevMesh &d = m->dev;
+  d.p = h.p; d.N = h.N; d.Np = h.Np; d.Nf = h.Nf;
+  d.E = h.E; d.n_if = h.n_if; d.n_interior = h.n_interior;
+  const size_t nsol = (size_t)h.E * h.Np * 5;
+  const size_t Nf = h.Nf;
+  if ((st = dalloc(m, &d.Q, nsol)) || (st = dalloc(m, &d.Un, nsol)) || (st = dalloc(m, &d.acc, nsol)) ||
+      (st = dalloc(m, &d.Rpart, nsol)) || (st = dalloc(m, &d.metrics, h.metrics.size())) ||
+      (st = dalloc(m, &d.liftfac, h.liftfac.size())) || (st = dalloc(m, &d.normals, h.normals.size())) ||
+      (st = dalloc(m, &d.Qtr, (size_t)h.n_if * 2 * 5 * Nf)) ||
+      (st = dalloc(m, &d.Gtr, (size_t)h.n_if * 2 * 15 * Nf)) || (st = dalloc(m, &d.FI, (size_t)h.n_if * 5 * Nf)) ||
+      (st = dalloc(m, &d.h, (size_t)h.E)) || (st = dalloc(m, &d.dtbuf, (size_t)h.E + 1)) ||
+      (st = dalloc(m, &d.ef, h.ef.size())) || (st = dalloc(m, &d.if_bc, h.if_bc.size())) ||
+      (st = dalloc(m, &d.bcs, h.bcs.size())) || (st = dalloc(m, &d.flag, 1)))
+    return bail(st);
+  ce = cudaMallocHost((void **)&m->h_scalar, 4 * sizeof(double));
+  if (ce != cudaSuccess) { m->err = cudaGetErrorString(ce); return bail(FR_ENOMEM); }
+  struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
+      {d.metrics, h.metrics.data(), h.metrics.size() * sizeof(double)},
+      {d.liftfac, h.liftfac.data(), h.liftfac.size() * sizeof(double)},
+      {d.normals, h.normals.data(), h.normals.size() * sizeof(double)},
+      {d.h, h.h.data(), h.h.size() * sizeof(double)},
+      {d.ef, h.ef.data(), h.ef.size() * sizeof(int32_t)},
+      {d.if_bc, h.if_bc.data(), h.if_bc.size() * sizeof(int32_t)},
+      {d.bcs, h.bcs.data(), h.bcs.size() * sizeof(fr_bc)},
+  };
+  for (const Up &u : ups) {
+    if (u.bytes == 0) continue;
+    ce = cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, m->stream);
+    if (ce != cudaSuccess) { m->err = std::string("upload: ") + cudaGetErrorString(ce); return bail(FR_ECUDA); }
+  }
+  // Interface buffers start at zero; the state is undefined until fr_set_state.
+  ce = cudaMemsetAsync(d.Qtr, 0, (size_t)h.n_if * 2 * 5 * Nf * sizeof(double), m->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Gtr, 0, (size_t)h.n_if * 2 * 15 * Nf * sizeof(double), m->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.flag, 0, sizeof(int), m->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(m->stream);
+  if (ce != cudaSuccess) { m->err = std::string("init: ") + cudaGetErrorString(ce); return bail(FR_ECUDA); }
+  // Bulk host copies are no longer needed.
+  std::vector<double>().swap(h.metrics);
+  std::vector<double>().swap(h.liftfac);
+  std::vector<double>().swap(h.normals);
+  *out = m;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_query(const fr_mesh *m, fr_mesh_info *info) {
+  if (!m || !info) return FR_EINVAL;
+  info->n_elem = m->host.E;
+  info->p = m->host.p;
+  info->n_pts = m->host.Np;
+  info->n_iface = m->host.n_interior;
+  info->n_bface = m->host.n_if - m->host.n_interior;
+  info->device_bytes = m->bytes;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_solution_points(fr_mesh *m, double *xyz) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!xyz) return fail(m, FR_EINVAL, "xyz is NULL");
+  std::memcpy(xyz, m->host.xsol.data(), m->host.xsol.size() * sizeof(double));
+  return FR_OK;
+}
+
+static cudaMemcpyKind kind_of(int where, bool to_device) {
+  if (where == FR_DEVICE) return cudaMemcpyDeviceToDevice;
+  return to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+}
+
+extern "C" fr_status fr_set_state(fr_mesh *m, const double *Q, int32_t where) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!Q || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad state pointer or where");
+  const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+  FR_CUDA(m, cudaMemcpyAsync(m->dev.Q, Q, bytes, kind_of(where, true), m->stream));
+  FR_CUDA(m, cudaMemcpyAsync(m->dev.Un, m->dev.Q, bytes, cudaMemcpyDeviceToDevice, m->stream));
+  if (where == FR_HOST) FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+extern "C" fr_status fr_get_state(fr_mesh *m, double *Q, int32_t where) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!Q || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad state pointer or where");
+  const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+  FR_CUDA(m, cudaMemcpyAsync(Q, m->dev.Q, bytes, kind_of(where, false), m->stream));
+  if (where == FR_HOST) FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  return FR_OK;
+}
+
+extern "C" fr_status fr_residual(fr_mesh *m, double t, double *R, int32_t where) {
+  (void)t;
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!R || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad residual pointer or where");
+  double *dst = (where == FR_DEVICE) ? R : m->dev.acc;   // acc is free outside an RK step
+  FR_CUDA(m, launch_residual(m->dev, m->dphys, MODE_RESIDUAL, 0, 0.0, dst, m->stream, next_events(m)));
+  if (where == FR_HOST) {
+    const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+    FR_CUDA(m, cudaMemcpyAsync(R, dst, bytes, cudaMemcpyDeviceToHost, m->stream));
+    FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  }
+  return FR_OK;
+}
+
+extern "C" fr_status fr_rk_stage(fr_mesh *m, int32_t scheme, int32_t stage, double t, double dt) {
+  (void)t;
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (scheme != FR_RK44) return fail(m, FR_EUNSUPPORTED, "only RK44 is built");
+  if (stage < 0 || stage > 3 || !std::isfinite(dt)) return fail(m, FR_EINVAL, "bad stage or dt");
+  FR_CUDA(m, launch_residual(m->dev, m->dphys, MODE_RK, stage, dt, nullptr, m->stream, next_events(m)));
+  if (stage == 3) {
+    int *hflag = reinterpret_cast<int *>(m->h_scalar);
+    FR_CUDA(m, cudaMemcpyAsync(hflag, m->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    FR_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (*hflag) {
+      FR_CUDA(m, cudaMemsetAsync(m->dev.flag, 0, sizeof(int), m->stream));
+      return fail(m, FR_ENONFINITE, "non-finite value in the updated state");
+    }
+  }
+  return FR_OK;
+}
+
+extern "C" fr_status fr_max_dt(fr_mesh *m, double cfl, double *dt) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!dt || !(cfl > 0.0)) return fail(m, FR_EINVAL, "bad dt pointer or cfl");
+  double *d_out = m->dev.dtbuf + m->dev.E;
+  FR_CUDA(m, launch_max_dt(m->dev, m->dphys, cfl, d_out, m->stream));
+  FR_CUDA(m, cudaMemcpyAsync(m->h_scalar, d_out, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  *dt = m->h_scalar[0];
+  return FR_OK;
+}
+
+extern "C" fr_status fr_profile(fr_mesh *m, int32_t enable) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  clear_events(m);
+  m->profiling = enable != 0;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_profile_read(fr_mesh *m, double *ms, int64_t *launches, int32_t n) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!ms || !launches || n < 0) return fail(m, FR_EINVAL, "bad profile buffers");
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int k = 0; k < n; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  for (size_t i = 0; i < m->ev_used; ++i)
+    for (int k = 0; k < 4 && k < n; ++k) {
+      float t = 0.f;
+      FR_CUDA(m, cudaEventElapsedTime(&t, m->ev_pool[i].start[k], m->ev_pool[i].stop[k]));
+      ms[k] += t;
+      launches[k] += 1;
+    }
+  return FR_OK;
+}
+
+extern "C" void fr_free(fr_mesh *m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  clear_events(m);
+  release(m);
+  delete m;
+}
+
+extern "C" const char *fr_last_error(const fr_mesh *m) {
+  if (m) return m->err.c_str();
+  return g_create_error.c_str();
+}

@@ -1,0 +1,48 @@
+// Device-side declarations: basis tables in constant memory and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fr_internal.hpp"
+
+namespace frx {
+
+struct DevBasis {
+  double D[kMaxN * kMaxN];    // D[i*N + a] = l_a'(x_i)
+  double Dt[kMaxN * kMaxN];   // D - hp (x) lp + hm (x) lm: divergence with the own-flux correction
+  double lm[kMaxN], lp[kMaxN], hm[kMaxN], hp[kMaxN];
+};
+
+struct DevPhys {
+  double gamma, R, mu, kappa, eta;
+  int viscous;
+  int inviscid;
+};
+
+// Device buffers of one mesh (all owned by the mesh).
+struct DevMesh {
+  int p, N, Np, Nf;
+  int64_t E, n_if, n_interior;
+  double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf;
+  int32_t *ef, *if_bc;
+  fr_bc *bcs;
+  int *flag;
+};
+
+enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
+
+// Optional per-kernel event pairs (instrumentation); null = off.
+struct PhaseEvents {
+  cudaEvent_t start[4], stop[4];
+};
+
+cudaError_t upload_basis_tables();
+// Residual of the current state dev.Q; MODE_RESIDUAL writes R (canonical layout) to Rout,
+// MODE_RK applies RK44 stage `stage` with step dt.
+cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
+                            double *Rout, cudaStream_t st, const PhaseEvents *ev = nullptr);
+cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, double *d_out, cudaStream_t st);
+
+}  // namespace frx

@@ -1,0 +1,527 @@
+// Host-side construction of the FR discretisation: 1D basis, face connectivity, orientation
+// codes and element metrics (arXiv 2308.06605, section "FR Algorithm", Eq. 1-2, and the face
+// construction of the pre-processor section: faces keyed by sorted vertex ids, sorted so that
+// coupled faces are adjacent, then paired).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <unordered_map>
+
+#include "fr_internal.hpp"
+
+namespace frx {
+
+using ld = long double;
+
+// ------------------------------------------------------------------------------------------
+// Gauss-Legendre nodes by Golub-Welsch: eigenvalues of the symmetric tridiagonal Jacobi matrix
+// of the Legendre recurrence (zero diagonal, off-diagonal k / sqrt(4k^2 - 1)), found with the
+// implicit QL iteration, then polished by Newton steps on P_N.
+// ------------------------------------------------------------------------------------------
+static void tridiag_ql(int n, ld *d, ld *e) {
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0; iter < 200; ++iter) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        ld dd = fabsl(d[m]) + fabsl(d[m + 1]);
+        if (fabsl(e[m]) <= 1e-30L * dd + 1e-300L) break;
+      }
+      if (m == l) break;
+      ld g = (d[l + 1] - d[l]) / (2.0L * e[l]);
+      ld r = sqrtl(g * g + 1.0L);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      ld s = 1.0L, c = 1.0L, p = 0.0L;
+      int i = m - 1;
+      bool underflow = false;
+      for (; i >= l; --i) {
+        ld f = s * e[i], b = c * e[i];
+        r = sqrtl(f * f + g * g);
+        e[i + 1] = r;
+        if (r == 0.0L) { d[i + 1] -= p; e[m] = 0.0L; underflow = true; break; }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0L * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+      }
+      if (underflow) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0L;
+    }
+  }
+}
+
+static void legendre_pd(int n, ld x, ld &P, ld &dP) {
+  ld p0 = 1.0L, p1 = x;
+  if (n == 0) { P = 1.0L; dP = 0.0L; return; }
+  for (int k = 1; k < n; ++k) {
+    ld p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  dP = n * (p0 - x * p1) / (1.0L - x * x);   // valid inside (-1, 1)
+}
+
+Basis1D make_basis(int p) {
+  Basis1D b;
+  const int N = p + 1;
+  b.p = p;
+  b.N = N;
+  ld d[kMaxN] = {0}, e[kMaxN] = {0}, x[kMaxN], w[kMaxN];
+  for (int k = 1; k < N; ++k) e[k - 1] = (ld)k / sqrtl(4.0L * k * k - 1.0L);
+  tridiag_ql(N, d, e);
+  std::sort(d, d + N);
+  for (int i = 0; i < N; ++i) {
+    ld xi = d[i];
+    for (int it = 0; it < 3; ++it) {
+      ld P, dP;
+      legendre_pd(N, xi, P, dP);
+      xi -= P / dP;
+    }
+    x[i] = xi;
+  }
+  for (int i = 0; i < N / 2; ++i) {            // exact symmetry x_{N-1-i} = -x_i
+    ld s = 0.5L * (x[N - 1 - i] - x[i]);
+    x[i] = -s;
+    x[N - 1 - i] = s;
+  }
+  if (N % 2) x[N / 2] = 0.0L;
+  for (int i = 0; i < N; ++i) {
+    ld P, dP;
+    legendre_pd(N, x[i], P, dP);
+    w[i] = 2.0L / ((1.0L - x[i] * x[i]) * dP * dP);
+  }
+  // Barycentric weights, derivative matrix and boundary values of the Lagrange basis.
+  ld lam[kMaxN];
+  for (int j = 0; j < N; ++j) {
+    ld q = 1.0L;
+    for (int m = 0; m < N; ++m)
+      if (m != j) q *= (x[j] - x[m]);
+    lam[j] = 1.0L / q;
+  }
+  for (int i = 0; i < N; ++i) {
+    ld diag = 0.0L;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      ld v = (lam[j] / lam[i]) / (x[i] - x[j]);
+      b.D[i * N + j] = (double)v;
+      diag -= v;
+    }
+    b.D[i * N + i] = (double)diag;
+  }
+  for (int side = 0; side < 2; ++side) {
+    ld xe = side ? 1.0L : -1.0L, den = 0.0L;
+    for (int k = 0; k < N; ++k) den += lam[k] / (xe - x[k]);
+    for (int j = 0; j < N; ++j) {
+      ld v = (lam[j] / (xe - x[j])) / den;
+      if (side) b.lp[j] = (double)v; else b.lm[j] = (double)v;
+    }
+  }
+  // DG-equivalent (c = 0) correction: on Gauss-Legendre points the derivative of the right
+  // Radau polynomial equals the lifting l_i(1) / w_i (exact mass matrix), and by symmetry the
+  // left one's (negated, mirrored) equals l_i(-1) / w_i.
+  for (int i = 0; i < N; ++i) {
+    b.x[i] = (double)x[i];
+    b.w[i] = (double)w[i];
+    ld lpv = 0, lmv = 0;
+    {
+      ld den = 0.0L;
+      for (int k = 0; k < N; ++k) den += lam[k] / (1.0L - x[k]);
+      lpv = (lam[i] / (1.0L - x[i])) / den;
+      den = 0.0L;
+      for (int k = 0; k < N; ++k) den += lam[k] / (-1.0L - x[k]);
+      lmv = (lam[i] / (-1.0L - x[i])) / den;
+    }
+    b.hp[i] = (double)(lpv / w[i]);
+    b.hm[i] = (double)(lmv / w[i]);
+  }
+  return b;
+}
+
+// ------------------------------------------------------------------------------------------
+// Geometry of the trilinear hexahedron.
+// ------------------------------------------------------------------------------------------
+static const int kVert[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+struct Jac {
+  double x[3];
+  double J[3][3];   // J[i][b] = dx_i / dxi_b
+};
+
+static Jac trilinear(const double (*X)[3], const double xi[3]) {
+  Jac r{};
+  for (int v = 0; v < 8; ++v) {
+    double f[3];
+    for (int a = 0; a < 3; ++a) f[a] = 0.5 * (1.0 + kVert[v][a] * xi[a]);
+    double Nv = f[0] * f[1] * f[2];
+    double dN[3] = {0.5 * kVert[v][0] * f[1] * f[2], 0.5 * kVert[v][1] * f[0] * f[2],
+                    0.5 * kVert[v][2] * f[0] * f[1]};
+    for (int i = 0; i < 3; ++i) {
+      r.x[i] += Nv * X[v][i];
+      for (int b = 0; b < 3; ++b) r.J[i][b] += dN[b] * X[v][i];
+    }
+  }
+  return r;
+}
+
+// S = |J| J^-1: row d is the cross product of the other two columns of J (cyclic order).
+static void adjugate_rows(const double J[3][3], double S[3][3], double &det) {
+  for (int d = 0; d < 3; ++d) {
+    int b1 = (d + 1) % 3, b2 = (d + 2) % 3;
+    S[d][0] = J[1][b1] * J[2][b2] - J[2][b1] * J[1][b2];
+    S[d][1] = J[2][b1] * J[0][b2] - J[0][b1] * J[2][b2];
+    S[d][2] = J[0][b1] * J[1][b2] - J[1][b1] * J[0][b2];
+  }
+  det = J[0][0] * S[0][0] + J[1][0] * S[0][1] + J[2][0] * S[0][2];
+}
+
+static inline void face_axes(int f, int &d, int &s, int &t0, int &t1) {
+  d = f / 2;
+  s = (f % 2) ? 1 : -1;
+  t0 = (d == 0) ? 1 : 0;
+  t1 = (d == 2) ? 1 : 2;
+}
+
+// ------------------------------------------------------------------------------------------
+// Connectivity.
+// ------------------------------------------------------------------------------------------
+struct FaceRec {
+  std::array<int64_t, 4> key;
+  int64_t e;
+  int f;
+};
+
+struct Side {
+  int64_t e;
+  int f;
+};
+
+static void face_corners(const int64_t *hex, int64_t e, int f, int64_t out[4], int ref[4][2]) {
+  int d, s, t0, t1;
+  face_axes(f, d, s, t0, t1);
+  int c = 0;
+  for (int v = 0; v < 8; ++v) {
+    if (kVert[v][d] != s) continue;
+    out[c] = hex[e * 8 + v];
+    ref[c][0] = kVert[v][t0];
+    ref[c][1] = kVert[v][t1];
+    ++c;
+  }
+}
+
+// Orientation code mapping side-1 face coordinates onto side-0 face coordinates.
+static int find_orientation(const double c0[4][3], const int r0[4][2], const double c1[4][3],
+                            const int r1[4][2], const double shift1[3], double tol) {
+  // For each side-1 corner find the side-0 corner at the same physical location.
+  int match[4];
+  for (int a = 0; a < 4; ++a) {
+    match[a] = -1;
+    for (int b = 0; b < 4; ++b) {
+      double dx = c1[a][0] - shift1[0] - c0[b][0], dy = c1[a][1] - shift1[1] - c0[b][1],
+             dz = c1[a][2] - shift1[2] - c0[b][2];
+      if (dx * dx + dy * dy + dz * dz <= tol * tol) { match[a] = b; break; }
+    }
+    if (match[a] < 0) return -1;
+  }
+  for (int code = 0; code < 8; ++code) {
+    bool ok = true;
+    for (int a = 0; a < 4 && ok; ++a) {
+      int u = r1[a][0], v = r1[a][1];
+      if (code & 4) std::swap(u, v);
+      if (code & 1) u = -u;
+      if (code & 2) v = -v;
+      ok = (u == r0[match[a]][0] && v == r0[match[a]][1]);
+    }
+    if (ok) return code;
+  }
+  return -1;
+}
+
+fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &err) {
+  char buf[256];
+  const int p = desc->p;
+  const int N = p + 1, Np = N * N * N, Nf = N * N;
+  const int64_t E = desc->n_hex;
+  m.p = p; m.N = N; m.Np = Np; m.Nf = Nf; m.E = E;
+  for (int64_t i = 0; i < E * 8; ++i) {
+    if (desc->hex[i] < 0 || desc->hex[i] >= desc->n_nodes) {
+      err = "hex vertex id out of range";
+      return FR_EINVAL;
+    }
+  }
+  const double(*xyz)[3] = reinterpret_cast<const double(*)[3]>(desc->xyz);
+  auto elem_verts = [&](int64_t e, double X[8][3]) {
+    for (int v = 0; v < 8; ++v)
+      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->hex[e * 8 + v]][i];
+  };
+  // Minimum element size for tolerances.
+  double hmin = 1e300;
+  for (int64_t e = 0; e < E; ++e) {
+    double X[8][3];
+    elem_verts(e, X);
+    double dx = X[6][0] - X[0][0], dy = X[6][1] - X[0][1], dz = X[6][2] - X[0][2];
+    hmin = std::min(hmin, std::sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  const double tol = 1e-7 * hmin;
+
+  // Faces keyed by sorted vertex ids; sorting makes coupled faces adjacent.
+  std::vector<FaceRec> faces(E * 6);
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int64_t c[4];
+      int r[4][2];
+      face_corners(desc->hex, e, f, c, r);
+      std::array<int64_t, 4> k = {c[0], c[1], c[2], c[3]};
+      std::sort(k.begin(), k.end());
+      faces[e * 6 + f] = {k, e, f};
+    }
+  std::sort(faces.begin(), faces.end(), [](const FaceRec &a, const FaceRec &b) {
+    if (a.key != b.key) return a.key < b.key;
+    return a.e * 6 + a.f < b.e * 6 + b.f;
+  });
+  std::vector<std::pair<Side, Side>> pairs;
+  std::vector<FaceRec> open;
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && faces[j].key == faces[i].key) ++j;
+    if (j - i == 2) {
+      pairs.push_back({{faces[i].e, faces[i].f}, {faces[i + 1].e, faces[i + 1].f}});
+    } else if (j - i == 1) {
+      open.push_back(faces[i]);
+    } else {
+      snprintf(buf, sizeof buf, "face shared by %zu elements", j - i);
+      err = buf;
+      return FR_EMESH;
+    }
+    i = j;
+  }
+  // Boundary tags of the unpaired faces.
+  std::vector<std::pair<std::array<int64_t, 4>, int32_t>> btags(desc->n_bface);
+  for (int64_t i = 0; i < desc->n_bface; ++i) {
+    std::array<int64_t, 4> k = {desc->bface_nodes[4 * i], desc->bface_nodes[4 * i + 1],
+                                desc->bface_nodes[4 * i + 2], desc->bface_nodes[4 * i + 3]};
+    std::sort(k.begin(), k.end());
+    btags[i] = {k, desc->bface_tag[i]};
+  }
+  std::sort(btags.begin(), btags.end());
+  struct Open { Side s; int32_t tag; double cent[3]; };
+  std::vector<Open> opens;
+  opens.reserve(open.size());
+  for (const FaceRec &fr : open) {
+    auto it = std::lower_bound(btags.begin(), btags.end(), std::make_pair(fr.key, INT32_MIN));
+    if (it == btags.end() || it->first != fr.key) {
+      err = "unmatched face with no boundary tag";
+      return FR_EMESH;
+    }
+    Open o{{fr.e, fr.f}, it->second, {0, 0, 0}};
+    for (int c = 0; c < 4; ++c)
+      for (int i = 0; i < 3; ++i) o.cent[i] += 0.25 * xyz[fr.key[c]][i];
+    opens.push_back(o);
+  }
+  // Periodic pairing by translated centroids on a hashed grid.
+  std::vector<int> used(opens.size(), 0);
+  std::vector<std::array<double, 3>> pshift;   // shift of side 1 per periodic pair
+  std::vector<std::pair<Side, Side>> ppairs;
+  const double cell = 0.25 * hmin;
+  for (int ip = 0; ip < desc->n_periodic; ++ip) {
+    const fr_periodic &P = desc->periodic[ip];
+    std::unordered_map<int64_t, std::vector<int>> grid;
+    auto key_of = [&](const double c[3], int dx, int dy, int dz) {
+      int64_t ix = (int64_t)std::floor(c[0] / cell) + dx, iy = (int64_t)std::floor(c[1] / cell) + dy,
+              iz = (int64_t)std::floor(c[2] / cell) + dz;
+      return (ix * 73856093LL) ^ (iy * 19349663LL) ^ (iz * 83492791LL);
+    };
+    for (size_t i = 0; i < opens.size(); ++i)
+      if (opens[i].tag == P.tag_a) grid[key_of(opens[i].cent, 0, 0, 0)].push_back((int)i);
+    for (size_t i = 0; i < opens.size(); ++i) {
+      if (opens[i].tag != P.tag_b) continue;
+      double c[3] = {opens[i].cent[0] - P.t[0], opens[i].cent[1] - P.t[1], opens[i].cent[2] - P.t[2]};
+      int found = -1;
+      for (int dx = -1; dx <= 1 && found < 0; ++dx)
+        for (int dy = -1; dy <= 1 && found < 0; ++dy)
+          for (int dz = -1; dz <= 1 && found < 0; ++dz) {
+            auto it = grid.find(key_of(c, dx, dy, dz));
+            if (it == grid.end()) continue;
+            for (int j : it->second) {
+              double ex = opens[j].cent[0] - c[0], ey = opens[j].cent[1] - c[1], ez = opens[j].cent[2] - c[2];
+              if (!used[j] && ex * ex + ey * ey + ez * ez <= tol * tol) { found = j; break; }
+            }
+          }
+      if (found < 0) {
+        snprintf(buf, sizeof buf, "periodic face (tag %d) without a partner (tag %d)", P.tag_b, P.tag_a);
+        err = buf;
+        return FR_EMESH;
+      }
+      used[found] = 1;
+      used[i] = 1;
+      ppairs.push_back({opens[found].s, opens[i].s});
+      pshift.push_back({P.t[0], P.t[1], P.t[2]});
+    }
+  }
+  // Remaining open faces need a boundary condition.
+  std::vector<std::pair<Side, int>> bfaces;
+  m.bcs.clear();
+  for (size_t i = 0; i < opens.size(); ++i) {
+    if (used[i]) continue;
+    int bi = -1;
+    for (int k = 0; k < desc->n_bc; ++k)
+      if (desc->bc[k].tag == opens[i].tag) bi = k;
+    bool periodic_tag = false;
+    for (int ip = 0; ip < desc->n_periodic; ++ip)
+      periodic_tag |= (desc->periodic[ip].tag_a == opens[i].tag || desc->periodic[ip].tag_b == opens[i].tag);
+    if (bi < 0 || periodic_tag) {
+      snprintf(buf, sizeof buf, "boundary face with tag %d has no condition or partner", opens[i].tag);
+      err = buf;
+      return FR_EMESH;
+    }
+    bfaces.push_back({opens[i].s, bi});
+  }
+  if (desc->n_bc > kMaxBC) {
+    err = "too many boundary conditions";
+    return FR_EUNSUPPORTED;
+  }
+  for (int k = 0; k < desc->n_bc; ++k) m.bcs.push_back(desc->bc[k]);
+
+  const int64_t n_int = (int64_t)pairs.size() + (int64_t)ppairs.size();
+  m.n_interior = n_int;
+  m.n_if = n_int + (int64_t)bfaces.size();
+  if (m.n_if >= (int64_t(1) << 27)) {
+    err = "too many interfaces for this build";
+    return FR_EUNSUPPORTED;
+  }
+  m.ef.assign(E * 6, -1);
+  m.if_bc.assign(m.n_if, -1);
+  std::vector<int> orient(n_int, 0);
+  // Orientation of side 1 relative to side 0.
+  auto corner_xyz = [&](Side s, double c[4][3], int r[4][2]) {
+    int64_t ids[4];
+    face_corners(desc->hex, s.e, s.f, ids, r);
+    for (int k = 0; k < 4; ++k)
+      for (int i = 0; i < 3; ++i) c[k][i] = xyz[ids[k]][i];
+  };
+  for (int64_t I = 0; I < n_int; ++I) {
+    bool per = I >= (int64_t)pairs.size();
+    const auto &pr = per ? ppairs[I - pairs.size()] : pairs[I];
+    double shift[3] = {0, 0, 0};
+    if (per)
+      for (int i = 0; i < 3; ++i) shift[i] = pshift[I - pairs.size()][i];
+    double c0[4][3], c1[4][3];
+    int r0[4][2], r1[4][2];
+    corner_xyz(pr.first, c0, r0);
+    corner_xyz(pr.second, c1, r1);
+    int code = find_orientation(c0, r0, c1, r1, shift, tol);
+    if (code < 0) {
+      err = "could not orient a matched face pair";
+      return FR_EMESH;
+    }
+    orient[I] = code;
+    m.ef[pr.first.e * 6 + pr.first.f] = (int32_t)((I << 4) | (0 << 3) | 0);
+    m.ef[pr.second.e * 6 + pr.second.f] = (int32_t)((I << 4) | (1 << 3) | code);
+  }
+  for (size_t k = 0; k < bfaces.size(); ++k) {
+    int64_t I = n_int + (int64_t)k;
+    m.if_bc[I] = bfaces[k].second;
+    m.ef[bfaces[k].first.e * 6 + bfaces[k].first.f] = (int32_t)(I << 4);
+  }
+  for (int64_t i = 0; i < E * 6; ++i)
+    if (m.ef[i] < 0) {
+      err = "internal: element face without interface";
+      return FR_EMESH;
+    }
+
+  // Geometry at solution and flux points.
+  Basis1D b = make_basis(p);
+  m.metrics.assign((size_t)E * 10 * Np, 0.0);
+  m.liftfac.assign((size_t)E * 6 * 3 * Nf, 0.0);
+  m.normals.assign((size_t)m.n_if * 3 * Nf, 0.0);
+  m.xsol.assign((size_t)E * Np * 3, 0.0);
+  m.h.assign(E, 0.0);
+  std::vector<double> fx((size_t)E * 6 * Nf * 3);     // flux-point coordinates for the match check
+  for (int64_t e = 0; e < E; ++e) {
+    double X[8][3];
+    elem_verts(e, X);
+    double vol = 0.0;
+    double *met = &m.metrics[(size_t)e * 10 * Np];
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          int mm = i + N * j + N * N * k;
+          double xi[3] = {b.x[i], b.x[j], b.x[k]};
+          Jac g = trilinear(X, xi);
+          double S[3][3], det;
+          adjugate_rows(g.J, S, det);
+          if (!(det > 0.0)) {
+            snprintf(buf, sizeof buf, "non-positive Jacobian in element %lld", (long long)e);
+            err = buf;
+            return FR_EMESH;
+          }
+          for (int d = 0; d < 3; ++d)
+            for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Np + mm] = S[d][jj];
+          met[9 * Np + mm] = 1.0 / det;
+          vol += b.w[i] * b.w[j] * b.w[k] * det;
+          for (int c = 0; c < 3; ++c) m.xsol[((size_t)e * Np + mm) * 3 + c] = g.x[c];
+        }
+    m.h[e] = std::cbrt(vol);
+    for (int f = 0; f < 6; ++f) {
+      int d, s, t0, t1;
+      face_axes(f, d, s, t0, t1);
+      const double *lv = (s > 0) ? b.lp : b.lm;
+      const double *hv = (s > 0) ? b.hp : b.hm;
+      int packed = m.ef[e * 6 + f];
+      int64_t I = packed >> 4;
+      int side = (packed >> 3) & 1;
+      for (int bb = 0; bb < N; ++bb)
+        for (int aa = 0; aa < N; ++aa) {
+          int r = aa + N * bb;
+          double acc[3] = {0, 0, 0};
+          for (int c = 0; c < N; ++c) {
+            int idx[3];
+            idx[d] = c; idx[t0] = aa; idx[t1] = bb;
+            int mm = idx[0] + N * idx[1] + N * N * idx[2];
+            for (int jj = 0; jj < 3; ++jj)
+              acc[jj] += lv[c] * hv[c] * met[(d * 3 + jj) * Np + mm] * met[9 * Np + mm];
+          }
+          for (int jj = 0; jj < 3; ++jj)
+            m.liftfac[(((size_t)e * 6 + f) * 3 + jj) * Nf + r] = s * acc[jj];
+          double xi[3];
+          xi[d] = (double)s; xi[t0] = b.x[aa]; xi[t1] = b.x[bb];
+          Jac g = trilinear(X, xi);
+          double S[3][3], det;
+          adjugate_rows(g.J, S, det);
+          for (int c = 0; c < 3; ++c) fx[(((size_t)e * 6 + f) * Nf + r) * 3 + c] = g.x[c];
+          if (side == 0)
+            for (int jj = 0; jj < 3; ++jj) m.normals[((size_t)I * 3 + jj) * Nf + r] = s * S[d][jj];
+        }
+    }
+  }
+  // Check that every side-1 flux point lands on its side-0 slot (coordinates, with shift).
+  for (int64_t I = 0; I < n_int; ++I) {
+    bool per = I >= (int64_t)pairs.size();
+    const auto &pr = per ? ppairs[I - pairs.size()] : pairs[I];
+    double shift[3] = {0, 0, 0};
+    if (per)
+      for (int i = 0; i < 3; ++i) shift[i] = pshift[I - pairs.size()][i];
+    for (int bb = 0; bb < N; ++bb)
+      for (int aa = 0; aa < N; ++aa) {
+        int r = aa + N * bb;
+        int q = orient_slot(orient[I], aa, bb, N);
+        const double *x1 = &fx[(((size_t)pr.second.e * 6 + pr.second.f) * Nf + r) * 3];
+        const double *x0 = &fx[(((size_t)pr.first.e * 6 + pr.first.f) * Nf + q) * 3];
+        double dd = 0;
+        for (int c = 0; c < 3; ++c) dd += (x1[c] - shift[c] - x0[c]) * (x1[c] - shift[c] - x0[c]);
+        if (dd > 1e4 * tol * tol) {
+          err = "flux points of a matched face pair do not coincide";
+          return FR_EMESH;
+        }
+      }
+  }
+  return FR_OK;
+}
+
+}  // namespace frx

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of the C ABI in include/fr.h (argument marshalling only).
+
+Every computation happens in the CUDA library `lib/libfr.so`; this module converts NumPy / torch
+arguments into pointers and sizes and turns non-OK statuses into exceptions.  It never computes
+a residual itself and has no CPU fallback: `load()` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .inputs import MeshDesc, Physics
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfr.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_EUNSUPPORTED, FR_ENONFINITE, FR_ETIMEOUT = range(8)
+STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_EUNSUPPORTED",
+                "FR_ENONFINITE", "FR_ETIMEOUT"]
+FR_HOST, FR_DEVICE = 0, 1
+FR_RK44 = 0
+
+
+class FRError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class fr_bc(C.Structure):
+    _fields_ = [("tag", C.c_int32), ("kind", C.c_int32), ("params", C.c_double * 8)]
+
+
+class fr_periodic(C.Structure):
+    _fields_ = [("tag_a", C.c_int32), ("tag_b", C.c_int32), ("t", C.c_double * 3)]
+
+
+class fr_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("n_hex", C.c_int64), ("hex", C.POINTER(C.c_int64)),
+                ("p", C.c_int32),
+                ("n_bface", C.c_int64), ("bface_nodes", C.POINTER(C.c_int64)),
+                ("bface_tag", C.POINTER(C.c_int32)),
+                ("n_bc", C.c_int32), ("bc", C.POINTER(fr_bc)),
+                ("n_periodic", C.c_int32), ("periodic", C.POINTER(fr_periodic))]
+
+
+class fr_physics(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("mu", C.c_double), ("Pr", C.c_double),
+                ("inviscid", C.c_int32), ("viscous", C.c_int32), ("br2_eta", C.c_double),
+                ("precision", C.c_int32)]
+
+
+class fr_mesh_info(C.Structure):
+    _fields_ = [("n_elem", C.c_int64), ("p", C.c_int32), ("n_pts", C.c_int32),
+                ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+# Exported functions: name -> (restype, argtypes)
+SIGNATURES = {
+    "fr_mesh_create": (C.c_int, [C.POINTER(fr_mesh_desc), C.POINTER(fr_physics), C.c_size_t, C.POINTER(C.c_void_p)]),
+    "fr_mesh_query": (C.c_int, [C.c_void_p, C.POINTER(fr_mesh_info)]),
+    "fr_solution_points": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fr_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "fr_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "fr_residual": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int32]),
+    "fr_rk_stage": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_double]),
+    "fr_max_dt": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "fr_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fr_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "fr_probe_fma": (C.c_int32, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "fr_free": (None, [C.c_void_p]),
+    "fr_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} not built: run `python -m paper_2308_06605_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _data_ptr(x):
+    """(pointer, where) for a NumPy array (host) or a torch tensor (host or CUDA)."""
+    if isinstance(x, np.ndarray):
+        if not (x.flags["C_CONTIGUOUS"] and x.dtype == np.float64):
+            raise ValueError("state arrays must be C-contiguous float64")
+        return C.c_void_p(x.ctypes.data), FR_HOST
+    if not (x.is_contiguous() and str(x.dtype) == "torch.float64"):
+        raise ValueError("state tensors must be contiguous float64")
+    return C.c_void_p(x.data_ptr()), (FR_DEVICE if x.is_cuda else FR_HOST)
+
+
+def probe_fma(precision: int = 0, iters: int = 20000) -> float:
+    """Measured FMA throughput of the current device in FLOP/s (0 = FP64, 1 = FP32)."""
+    lib = load()
+    v = C.c_double()
+    if lib.fr_probe_fma(precision, iters, C.byref(v)) != 0:
+        raise RuntimeError("fr_probe_fma failed")
+    return v.value
+
+
+class Mesh:
+    """One FR discretisation living on the current CUDA device (owns the C-side fr_mesh)."""
+
+    def __init__(self, desc: MeshDesc, phys: Physics, p: int, stream: int = 0):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
+        hexa = np.ascontiguousarray(desc.hex, dtype=np.int64)
+        bn = np.ascontiguousarray(desc.bface_nodes, dtype=np.int64).reshape(-1, 4)
+        bt = np.ascontiguousarray(desc.bface_tag, dtype=np.int32)
+        bcs = (fr_bc * max(1, len(desc.bcs)))()
+        for i, bc in enumerate(desc.bcs):
+            bcs[i].tag, bcs[i].kind = bc.tag, bc.kind
+            for k, v in enumerate(bc.params[:8]):
+                bcs[i].params[k] = v
+        per = (fr_periodic * max(1, len(desc.periodic)))()
+        for i, pp in enumerate(desc.periodic):
+            per[i].tag_a, per[i].tag_b = pp.tag_a, pp.tag_b
+            for k in range(3):
+                per[i].t[k] = pp.t[k]
+        self._keep += [xyz, hexa, bn, bt, bcs, per]
+        d = fr_mesh_desc(n_nodes=xyz.shape[0], xyz=_ptr(xyz, C.c_double), n_hex=hexa.shape[0],
+                         hex=_ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
+                         bface_nodes=_ptr(bn, C.c_int64), bface_tag=_ptr(bt, C.c_int32),
+                         n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per)
+        ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
+                        viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision)
+        h = C.c_void_p()
+        st = lib.fr_mesh_create(C.byref(d), C.byref(ph), stream, C.byref(h))
+        if st != FR_OK:
+            raise FRError(st, lib.fr_last_error(None).decode())
+        self._h = h
+        info = fr_mesh_info()
+        lib.fr_mesh_query(h, C.byref(info))
+        self.n_elem, self.p, self.n_pts = info.n_elem, info.p, info.n_pts
+        self.n_iface, self.n_bface, self.device_bytes = info.n_iface, info.n_bface, info.device_bytes
+        self.shape = (self.n_elem, self.n_pts, 5)
+
+    def _check(self, st):
+        if st != FR_OK:
+            raise FRError(st, self._lib.fr_last_error(self._h).decode())
+
+    def solution_points(self) -> np.ndarray:
+        x = np.empty((self.n_elem, self.n_pts, 3))
+        self._check(self._lib.fr_solution_points(self._h, C.c_void_p(x.ctypes.data)))
+        return x
+
+    def set_state(self, Q):
+        p, where = _data_ptr(Q)
+        self._check(self._lib.fr_set_state(self._h, p, where))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, where = _data_ptr(out)
+        self._check(self._lib.fr_get_state(self._h, p, where))
+        return out
+
+    def residual(self, t: float = 0.0, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, where = _data_ptr(out)
+        self._check(self._lib.fr_residual(self._h, t, p, where))
+        return out
+
+    def rk_stage(self, stage: int, t: float, dt: float, scheme: int = FR_RK44):
+        self._check(self._lib.fr_rk_stage(self._h, scheme, stage, t, dt))
+
+    def rk_step(self, t: float, dt: float):
+        for s in range(4):
+            self.rk_stage(s, t, dt)
+
+    def max_dt(self, cfl: float) -> float:
+        v = C.c_double()
+        self._check(self._lib.fr_max_dt(self._h, cfl, C.byref(v)))
+        return v.value
+
+    def profile(self, enable: bool):
+        self._check(self._lib.fr_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, n: int = 4):
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        self._check(self._lib.fr_profile_read(self._h, ms, cnt, n))
+        return list(ms), list(cnt)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fr_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
