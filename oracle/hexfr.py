@@ -201,16 +201,79 @@ class HexFR:
         """C_f applied to face data B [E][Nf][...] -> [E][Np][...]."""
         return np.einsum('mq,eq...->em...', self.Cf[f], B)
 
-    def _ghost(self, Qm, k):
-        """Ghost state behind boundary face k given the interior trace Qm [Nf][5]."""
+    def _boundary_states(self, Qm, n, k):
+        """Boundary face k: (ghost state for the Riemann flux, common solution Q^I) at its flux
+        points, from the interior trace Qm [Nf][5] and the outward area-scaled normal n [Nf][3].
+
+        The paper lists boundary conditions among its physical models without stating them;
+        this build's readings are:
+          wall (isothermal no-slip, T_w): ghost = interior density and energy with reversed
+            momentum (the mirror state); Q^I = wall state (interior density, zero velocity,
+            T = T_w).
+          Dirichlet (exterior state Q_b): ghost = Q^I = Q_b.
+          characteristic outflow (static p_b): interior entropy, tangential velocity and the
+            outgoing invariant u.n^ + 2c/(gamma-1); ghost = Q^I = that boundary state.
+          characteristic inflow (total p0, total T0, unit direction d): interior outgoing
+            invariant; speed V from (d.n^)V + 2c_b/(gamma-1) = invariant with
+            c_b^2 = gamma R (T0 - V^2/(2 cp)); static state from the isentropic relations;
+            ghost = Q^I = that state.
+        """
+        ph = self.phys
+        g, Rg = ph.gamma, ph.R
         kind = self.b_kind[k]
+        prm = self.b_params[k]
+        rho, u, p = gas.primitives(Qm, g)
         if kind == BC_DIRICHLET:
-            return np.broadcast_to(self.b_params[k][:5], Qm.shape).copy()
-        raise NotImplementedError("boundary kind %d not in the oracle yet" % kind)
+            Qb = np.broadcast_to(prm[:5], Qm.shape).copy()
+            return Qb, Qb
+        if kind == BC_WALL_ISOTHERMAL:
+            ghost = Qm.copy()
+            ghost[..., 1:4] *= -1.0
+            Qi = np.zeros_like(Qm)
+            Qi[..., 0] = rho
+            Qi[..., 4] = rho * Rg * prm[0] / (g - 1.0)
+            return ghost, Qi
+        nh = n / np.linalg.norm(n, axis=-1, keepdims=True)
+        un = np.sum(u * nh, axis=-1)
+        c = np.sqrt(g * p / rho)
+        Rplus = un + 2.0 * c / (g - 1.0)
+        if kind == BC_CHAR_OUTFLOW:
+            pb = prm[0]
+            s_ent = p / rho ** g
+            rb = (pb / s_ent) ** (1.0 / g)
+            cb = np.sqrt(g * pb / rb)
+            unb = Rplus - 2.0 * cb / (g - 1.0)
+            ub = u + (unb - un)[..., None] * nh
+            Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
+                           pb / (g - 1.0) + 0.5 * rb * np.sum(ub * ub, axis=-1)], axis=-1)
+            return Qb, Qb
+        if kind == BC_CHAR_INFLOW:
+            p0, T0 = prm[0], prm[1]
+            d = np.asarray(prm[2:5], dtype=np.float64)
+            d = d / np.linalg.norm(d)
+            a = nh @ d
+            A = a * a + 2.0 / (g - 1.0)
+            B = -2.0 * a * Rplus
+            Cc = Rplus * Rplus - (2.0 / (g - 1.0)) ** 2 * g * Rg * T0
+            V = (-B + np.sqrt(B * B - 4.0 * A * Cc)) / (2.0 * A)
+            cp = g * Rg / (g - 1.0)
+            Tb = T0 - V * V / (2.0 * cp)
+            pb = p0 * (Tb / T0) ** (g / (g - 1.0))
+            rb = pb / (Rg * Tb)
+            ub = V[..., None] * d
+            Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
+                           pb / (g - 1.0) + 0.5 * rb * V * V], axis=-1)
+            return Qb, Qb
+        raise ValueError("unknown boundary kind %d" % kind)
 
     # ------------------------------------------------------------------ residual (Eq. 3)
-    def residual(self, Q, t=0.0):
-        """dQ/dt at the solution points; Q and the result are [E][N^3][5]."""
+    def residual(self, Q, t=0.0, magnitude=False):
+        """dQ/dt at the solution points; Q and the result are [E][N^3][5].
+
+        With magnitude=True it returns instead the entrywise magnitude of the final sum,
+        |J|^-1 [sum_d |D_d| |F^_d| + sum_f |C_f| (|F^I_perp| + |L_f| |F^_d|)], the natural scale of
+        the rounding error of any evaluation order of Eq. 3 (used for tolerances).
+        """
         ph = self.phys
         gam = ph.gamma
         viscous = ph.viscous != 0 and ph.mu != 0.0
@@ -224,12 +287,13 @@ class HexFR:
         QI = 0.5 * (QL + QR)
         Qc_face[self.eL, self.fL] = QI
         Qc_face[self.eR, self.fR] = QI[rows, self.invperm]
-        ghosts = []
+        ghosts, bstates = [], []
         for k in range(len(self.bE)):
             Qm = Qf[self.bE[k], self.bF[k]]
-            Qp = self._ghost(Qm, k)
-            ghosts.append(Qp)
-            Qc_face[self.bE[k], self.bF[k]] = 0.5 * (Qm + Qp)
+            Qg, Qb = self._boundary_states(Qm, self.nf[self.bE[k], self.bF[k]], k)
+            ghosts.append(Qg)
+            bstates.append(Qb)
+            Qc_face[self.bE[k], self.bF[k]] = Qb
         dQ = Qc_face - Qf                                          # Q^I - Q- per element face
         Sinv = self.S / self.detJ[..., None, None]                 # J^-1, [E][Np][d][j]
         if viscous:
@@ -271,11 +335,19 @@ class HexFR:
         for k in range(len(self.bE)):
             e, f = self.bE[k], self.bF[k]
             n = self.nf[e, f]
-            Qm, Qp = Qf[e, f], ghosts[k]
-            Fb = gas.rusanov(Qm, Qp, n, gam)
+            Qm = Qf[e, f]
+            Fb = gas.rusanov(Qm, ghosts[k], n, gam)
             if viscous:
-                Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(0.5 * (Qm + Qp), gface[e, f], gam, ph.R, ph.mu, ph.Pr), n)
+                # Common gradient at a boundary: the interior side's face gradient.
+                Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(bstates[k], gface[e, f], gam, ph.R, ph.mu, ph.Pr), n)
             Fc[e, f] = Fb
+        if magnitude:
+            A = np.abs(Hhat)
+            mag = sum(np.einsum('mn,env->emv', np.abs(self.Dop[d]), A[:, :, d, :]) for d in range(3))
+            for f in range(6):
+                own = np.einsum('qm,emv->eqv', np.abs(self.Lf[f]), A[:, :, FACE_AXIS[f], :])
+                mag = mag + np.einsum('mq,eqv->emv', np.abs(self.Cf[f]), np.abs(Fc[:, f]) + own)
+            return mag / self.detJ[..., None]
         corr = sum(self._lift(f, Fc[:, f] - Fperp[:, f]) for f in range(6))
         return -(div + corr) / self.detJ[..., None]
 

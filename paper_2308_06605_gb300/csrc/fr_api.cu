@@ -131,6 +131,21 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2)
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
   if (phys->precision != FR_PREC_FP64) return fail(nullptr, FR_EUNSUPPORTED, "only FP64 is built");
+  for (int k = 0; k < desc->n_bc; ++k) {
+    const fr_bc &b = desc->bc[k];
+    if (b.kind < FR_BC_WALL_ISOTHERMAL || b.kind > FR_BC_DIRICHLET)
+      return fail(nullptr, FR_EINVAL, "unknown boundary-condition kind");
+    if (b.kind == FR_BC_WALL_ISOTHERMAL && !(b.params[0] > 0.0))
+      return fail(nullptr, FR_EINVAL, "wall temperature must be positive");
+    if (b.kind == FR_BC_CHAR_OUTFLOW && !(b.params[0] > 0.0))
+      return fail(nullptr, FR_EINVAL, "outflow pressure must be positive");
+    if (b.kind == FR_BC_CHAR_INFLOW &&
+        (!(b.params[0] > 0.0) || !(b.params[1] > 0.0) ||
+         !(b.params[2] * b.params[2] + b.params[3] * b.params[3] + b.params[4] * b.params[4] > 0.0)))
+      return fail(nullptr, FR_EINVAL, "inflow needs positive total pressure/temperature and a direction");
+    if (b.kind == FR_BC_DIRICHLET && !(b.params[0] > 0.0))
+      return fail(nullptr, FR_EINVAL, "Dirichlet density must be positive");
+  }
 
   fr_mesh *m = new (std::nothrow) fr_mesh();
   if (!m) return fail(nullptr, FR_ENOMEM, "host allocation failed");
@@ -145,10 +160,6 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   if (st != FR_OK) {
     delete m;
     return fail(nullptr, st, err);
-  }
-  if (m->host.n_if > m->host.n_interior) {
-    delete m;
-    return fail(nullptr, FR_EUNSUPPORTED, "boundary-condition faces are not built in this version");
   }
   m->phys = *phys;
   m->stream = (cudaStream_t)stream;

@@ -332,6 +332,117 @@ __global__ void k_iface_flux(const double *__restrict__ Qtr, const double *__res
 }
 
 // ------------------------------------------------------------------------------------------
+// 3b. Boundary faces.  Side 0 of a boundary interface is the element; its side-1 slot holds
+// 2 Q^I - Q- so that the volume kernel's (other - own)/2 equals Q^I - Q- for the BR2 jump.
+// ------------------------------------------------------------------------------------------
+// Ghost state (for the Rusanov flux) and boundary common solution Q^I from the interior trace.
+__device__ void boundary_states(const double qm[5], const double n[3], const fr_bc &bc, const DevPhys &ph,
+                                double ghost[5], double qi[5]) {
+  const double g = ph.gamma, Rg = ph.R;
+  const double ri = 1.0 / qm[0];
+  const double u[3] = {qm[1] * ri, qm[2] * ri, qm[3] * ri};
+  const double p = (g - 1.0) * (qm[4] - 0.5 * (qm[1] * u[0] + qm[2] * u[1] + qm[3] * u[2]));
+  if (bc.kind == FR_BC_DIRICHLET) {
+    for (int v = 0; v < 5; ++v) ghost[v] = qi[v] = bc.params[v];
+    return;
+  }
+  if (bc.kind == FR_BC_WALL_ISOTHERMAL) {
+    ghost[0] = qm[0]; ghost[1] = -qm[1]; ghost[2] = -qm[2]; ghost[3] = -qm[3]; ghost[4] = qm[4];
+    qi[0] = qm[0]; qi[1] = qi[2] = qi[3] = 0.0;
+    qi[4] = qm[0] * Rg * bc.params[0] / (g - 1.0);
+    return;
+  }
+  const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+  const double un = u[0] * nh[0] + u[1] * nh[1] + u[2] * nh[2];
+  const double c = sqrt(g * p * ri);
+  const double Rp = un + 2.0 * c / (g - 1.0);          // outgoing Riemann invariant
+  double rb, ub[3], pb;
+  if (bc.kind == FR_BC_CHAR_OUTFLOW) {
+    pb = bc.params[0];
+    const double sent = p / pow(qm[0], g);
+    rb = pow(pb / sent, 1.0 / g);
+    const double unb = Rp - 2.0 * sqrt(g * pb / rb) / (g - 1.0);
+    for (int c3 = 0; c3 < 3; ++c3) ub[c3] = u[c3] + (unb - un) * nh[c3];
+  } else {  // FR_BC_CHAR_INFLOW: total pressure, total temperature, direction
+    const double p0 = bc.params[0], T0 = bc.params[1];
+    double d[3] = {bc.params[2], bc.params[3], bc.params[4]};
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int c3 = 0; c3 < 3; ++c3) d[c3] /= dn;
+    const double a = nh[0] * d[0] + nh[1] * d[1] + nh[2] * d[2];
+    const double k = 2.0 / (g - 1.0);
+    const double A = a * a + k, B = -2.0 * a * Rp, C = Rp * Rp - k * k * g * Rg * T0;
+    const double V = (-B + sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
+    const double cp = g * Rg / (g - 1.0);
+    const double Tb = T0 - V * V / (2.0 * cp);
+    pb = p0 * pow(Tb / T0, g / (g - 1.0));
+    rb = pb / (Rg * Tb);
+    for (int c3 = 0; c3 < 3; ++c3) ub[c3] = V * d[c3];
+  }
+  qi[0] = rb;
+  qi[1] = rb * ub[0];
+  qi[2] = rb * ub[1];
+  qi[3] = rb * ub[2];
+  qi[4] = pb / (g - 1.0) + 0.5 * rb * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+  for (int v = 0; v < 5; ++v) ghost[v] = qi[v];
+}
+
+template <int N>
+__global__ void k_bc_prepare(double *__restrict__ Qtr, const double *__restrict__ normals,
+                             const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
+                             int64_t first, int64_t count, DevPhys ph) {
+  constexpr int Nf = N * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count * Nf) return;
+  const int64_t I = first + t / Nf;
+  const int q = (int)(t % Nf);
+  double qm[5], n[3], gh[5], qi[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qm[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n[c] = normals[(I * 3 + c) * Nf + q];
+  boundary_states(qm, n, bcs[if_bc[I]], ph, gh, qi);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q] = 2.0 * qi[v] - qm[v];
+}
+
+template <int N>
+__global__ void k_bc_flux(const double *__restrict__ Qtr, const double *__restrict__ Gtr,
+                          const double *__restrict__ normals, const int32_t *__restrict__ if_bc,
+                          const fr_bc *__restrict__ bcs, double *__restrict__ FI, int64_t first,
+                          int64_t count, DevPhys ph) {
+  constexpr int Nf = N * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count * Nf) return;
+  const int64_t I = first + t / Nf;
+  const int q = (int)(t % Nf);
+  double qm[5], n[3], gh[5], qi[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qm[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n[c] = normals[(I * 3 + c) * Nf + q];
+  boundary_states(qm, n, bcs[if_bc[I]], ph, gh, qi);
+  double fL[5], fR[5], sL, sR;
+  normal_inviscid(qm, n, ph.gamma, fL, sL);
+  normal_inviscid(gh, n, ph.gamma, fR, sR);
+  const double lam = fmax(sL, sR);
+  double F[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]);
+  if (ph.viscous) {
+    double G[15];
+#pragma unroll
+    for (int c = 0; c < 15; ++c) G[c] = Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q];
+    double Fv[3][5];
+    viscous_flux(qi, G, ph, Fv);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * n[0] + Fv[1][v] * n[1] + Fv[2][v] * n[2];
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
+}
+
+// ------------------------------------------------------------------------------------------
 // 4. Correction by the common flux, scaling, and output / RK44 stage update.
 // ------------------------------------------------------------------------------------------
 template <int N>
@@ -441,6 +552,10 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     const int64_t n = E * 6 * Nf;
     FR_EV_BEGIN(0);
     k_interp_faces<N><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, m.ef, m.Qtr, E);
+    const int64_t nb = (m.n_if - m.n_interior) * Nf;
+    if (nb > 0)
+      k_bc_prepare<N><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(m.Qtr, m.normals, m.if_bc, m.bcs, m.n_interior,
+                                                                   m.n_if - m.n_interior, ph);
     FR_EV_END(0);
   }
   {
@@ -460,6 +575,10 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
     if (n > 0) k_iface_flux<N><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(m.Qtr, m.Gtr, m.normals, m.FI, m.n_interior, ph);
+    const int64_t nb = (m.n_if - m.n_interior) * Nf;
+    if (nb > 0)
+      k_bc_flux<N><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(m.Qtr, m.Gtr, m.normals, m.if_bc, m.bcs, m.FI,
+                                                                m.n_interior, m.n_if - m.n_interior, ph);
     FR_EV_END(2);
   }
   {

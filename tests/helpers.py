@@ -31,3 +31,26 @@ def assert_parity(got, want, rel=1e-12, floor=1e-3):
     err = parity_error(got, want, floor)
     assert np.all(err <= rel), f"per-variable max relative error {err} > {rel}"
     return err
+
+
+def assert_residual_parity(got, want, scale, rel=1e-12):
+    """Residual parity per entry: |got - want| <= rel * S, S = the entry's magnitude scale from
+    the oracle (sum of the magnitudes of the terms whose sum is the entry, Eq. 3).  Any two
+    FP64 evaluation orders differ by a few ulps of S; an entry that is small because its terms
+    cancel cannot be reproduced to 1e-12 of itself."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    scale = np.asarray(scale)
+    err = (np.abs(got - want) / scale).reshape(-1, 5).max(axis=0)
+    norm = (np.abs(got - want).reshape(-1, 5).max(axis=0) / np.abs(want).reshape(-1, 5).max(axis=0))
+    assert np.all(err <= rel), f"per-entry error / magnitude scale {err} > {rel} (normwise {norm})"
+    return err
+
+
+def assert_state_parity(got, want, scale, elapsed, rel=1e-12):
+    """State parity after RK steps: |got - want| <= rel * (|want| + elapsed * S), i.e. the
+    residual bar integrated over the elapsed time (S = magnitude scale of the initial residual)."""
+    den = np.abs(want) + elapsed * np.asarray(scale)
+    err = (np.abs(np.asarray(got) - want) / den).reshape(-1, 5).max(axis=0)
+    assert np.all(err <= rel), f"state error {err} > {rel}"
+    return err

@@ -1,15 +1,18 @@
 """GPU FP64 path vs the oracle, through the C ABI (marked gpu).
 
-Bar: |R_gpu - R_oracle| <= 1e-12 * max(|R_oracle|, 1e-3 * max_mesh|R_oracle,v|) per entry.
+Residual bar, per entry: |R_gpu - R_oracle| <= 1e-12 * S, where S is the oracle's magnitude
+scale of that entry (the sum of the magnitudes of the terms of Eq. 3 that form it).  States after
+RK steps: |Q_gpu - Q_oracle| <= 1e-12 * (|Q| + T S), T the elapsed time.
 """
 import numpy as np
 import pytest
 
 from paper_2308_06605_gb300 import fr
 from paper_2308_06605_gb300 import inputs as I
-from oracle.hexfr import HexFR
+from oracle.basis import Basis1D
+from oracle.hexfr import HexFR, trilinear_geometry
 
-from helpers import assert_parity, ensure_lib
+from helpers import assert_residual_parity, assert_state_parity, ensure_lib
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +44,7 @@ def test_residual_parity_all_orders(p):
     phys = I.tgv_physics(Ma=0.2, Re=200.0)
     ora, g, Q = _pair(d, phys, p, lambda x: I.tgv_state(x, Ma=0.2, perturb=1e-2, seed=p))
     g.set_state(Q)
-    assert_parity(g.residual(), ora.residual(Q))
+    assert_residual_parity(g.residual(), ora.residual(Q), ora.residual(Q, magnitude=True))
     g.close()
 
 
@@ -52,7 +55,7 @@ def test_residual_parity_config_8cube_p3_tgv():
     for seed in range(3):
         ora, g, Q = _pair(d, phys, 3, lambda x: I.tgv_state(x, Ma=0.1, perturb=1e-3, seed=seed))
         g.set_state(Q)
-        assert_parity(g.residual(), ora.residual(Q))
+        assert_residual_parity(g.residual(), ora.residual(Q), ora.residual(Q, magnitude=True))
         g.close()
 
 
@@ -61,7 +64,7 @@ def test_euler_parity_and_free_stream():
     phys = I.Physics(gamma=1.4, R=1.0, mu=0.0, viscous=0)
     ora, g, Q = _pair(d, phys, 4, lambda x: I.isentropic_vortex_state(x, centre=(3.0, 3.0), period=(2 * np.pi,) * 2))
     g.set_state(Q)
-    assert_parity(g.residual(), ora.residual(Q))
+    assert_residual_parity(g.residual(), ora.residual(Q), ora.residual(Q, magnitude=True))
     U = I.uniform_state(ora.x.shape[:2])
     g.set_state(np.ascontiguousarray(U))
     R = g.residual()
@@ -98,9 +101,27 @@ def test_rk44_ten_steps_config_8cube_p3():
         Qo = ora.rk44_step(Qo, t, dt_o)
         t += dt_o
     Qg = g.get_state()
-    # Compare the change over the 10 steps against the oracle's change (tighter than the state).
-    assert_parity(Qg - Q, Qo - Q, rel=1e-10)
-    assert_parity(Qg, Qo, rel=1e-13)
+    assert_state_parity(Qg, Qo, ora.residual(Q, magnitude=True), t)
+    g.close()
+
+
+@pytest.mark.parametrize("kinds", [
+    ((I.BC_WALL_ISOTHERMAL, (1.1,)), (I.BC_CHAR_OUTFLOW, (0.7,))),
+    ((I.BC_CHAR_INFLOW, (0.9, 1.05, 1.0, 0.2, 0.0)), (I.BC_WALL_ISOTHERMAL, (0.9,))),
+    ((I.BC_DIRICHLET, (1.0, 0.1, 0.0, 0.0, 1.8)), (I.BC_CHAR_OUTFLOW, (0.68,)))])
+@pytest.mark.parametrize("p", [2, 4])
+def test_boundary_conditions_parity(kinds, p):
+    """Walls, characteristic inflow/outflow and Dirichlet faces on a rotated, perturbed mesh."""
+    d = I.hex_box_mesh((3, 2, 2), hi=(2.0, 1.0, 1.0), periodic=(False, True, True),
+                       wall_tags={1: kinds[0], 2: kinds[1]}, seed=3, rotate=True, shuffle=True, perturb=0.1)
+    phys = I.Physics(gamma=1.4, R=1.0, mu=0.02, Pr=0.71, viscous=1)
+
+    def st(X):
+        return I.conserved(1 + 0.1 * np.sin(X[..., 0]), 0.2 * np.cos(X[..., 1] * 2 * np.pi),
+                           0.1 + 0 * X[..., 0], 0.05 * np.sin(2 * np.pi * X[..., 2]), 0.7 + 0.02 * X[..., 0], 1.4)
+    ora, g, Q = _pair(d, phys, p, st)
+    g.set_state(Q)
+    assert_residual_parity(g.residual(), ora.residual(Q), ora.residual(Q, magnitude=True))
     g.close()
 
 
@@ -148,8 +169,13 @@ def test_full_size_64cube_p4_sampled():
     d = I.hex_box_mesh((n, n, n))
     phys = I.tgv_physics()
     g = fr.Mesh(d, phys, p)
-    x = g.solution_points()
+    # Solution points from the oracle's own geometry (never from the library).
+    xi = Basis1D(p).nodes
+    K, Jj, Ii = np.meshgrid(xi, xi, xi, indexing="ij")
+    ref = np.stack([Ii.ravel(), Jj.ravel(), K.ravel()], axis=1)
+    x, _, _ = trilinear_geometry(d.xyz[d.hex], ref)
     Q = np.ascontiguousarray(I.tgv_state(x, Ma=0.1, perturb=1e-3, seed=4))
+    del x
     g.set_state(Q)
     R = g.residual()
     rng = np.random.default_rng(0)
@@ -166,8 +192,9 @@ def test_full_size_64cube_p4_sampled():
                     e_full = ((i - 1 + ii) % n) + n * (((j - 1 + jj) % n) + n * ((k - 1 + kk) % n))
                     Qp[ii + 3 * (jj + 3 * kk)] = Q[e_full]
         Rp = ora.residual(Qp)
+        Sp = ora.residual(Qp, magnitude=True)
         e_c = i + n * (j + n * k)
-        assert_parity(R[e_c], Rp[13])
+        assert_residual_parity(R[e_c], Rp[13], Sp[13])
     # Discrete conservation at full size: quadrature weights (library Gauss-Legendre rule) on
     # congruent affine cubes, so the constant |J| drops out.
     w = np.polynomial.legendre.leggauss(p + 1)[1]

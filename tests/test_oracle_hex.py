@@ -40,6 +40,17 @@ def test_discrete_conservation_periodic(p):
     assert np.all(s <= 1e-12 * a), s / a
 
 
+def test_magnitude_scale_bounds_residual():
+    """The tolerance scale S (sum of magnitudes of Eq. 3's terms) bounds |R| entrywise."""
+    d = I.hex_box_mesh((3, 3, 2), seed=2, rotate=True, perturb=0.1)
+    m = HexFR(d, I.tgv_physics(Ma=0.2, Re=300.0), 3)
+    Q = I.tgv_state(m.x, Ma=0.2, perturb=1e-2)
+    R = m.residual(Q)
+    S = m.residual(Q, magnitude=True)
+    assert np.all(S >= np.abs(R) * (1 - 1e-12))
+    assert np.all(S > 0)
+
+
 def _match_points(ma, mb):
     """Map solution points of mesh b onto mesh a by physical coordinates: idx with xb.flat[idx] = xa."""
     from scipy.spatial import cKDTree
