@@ -155,6 +155,28 @@ fr_status fr_rk_stage(fr_mesh *mesh, int32_t scheme, int32_t stage, double t, do
 fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
 
 /*
+ * fr_residual_static — the residual of a caller-supplied state, computed without allocating
+ * anything.  (The paper has no counterpart: this is a deployment variant of fr_residual.)
+ *
+ * For callers that cannot allocate device memory when they need a residual: code embedded in
+ * another framework that owns the device's memory pool, loops that must not hit cudaMalloc's
+ * implicit device synchronisation, or plug-ins that are only handed existing buffers.  The
+ * intermediate arrays of the residual (face traces, gradient traces, common fluxes, partial
+ * residual) live in one static device array of 32 MiB that every device loading this library
+ * holds until the process exits; no cudaMalloc, cudaFree or allocating library routine is
+ * called.  Q_device (input, [n_elem][n_pts][5] canonical layout) and R_device (output, same
+ * layout) are caller-owned device pointers; the mesh's own state is not read or changed.
+ * Meshes whose intermediates exceed 32 MiB (8 bytes x (45 n_iface_total N^2 + 5 n_elem N^3),
+ * N = p + 1) are rejected with FR_EINVAL and a message giving both sizes.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) — make that first call
+ * before any stream capture.  All calls share the one array and it keeps the last call's
+ * contents; nothing in it needs to start at zero, but calls whose work overlaps on the GPU
+ * (other streams, other meshes, other threads) race on it: serialise them.  Work is enqueued
+ * on the mesh's stream and the call returns without synchronising.
+ */
+fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
+
+/*
  * Instrumentation (not part of the method).  fr_profile(mesh, 1) makes every later residual
  * evaluation record CUDA events around each of its kernels on the mesh's stream;
  * fr_profile_read accumulates, per kernel k < n, the summed device time in milliseconds

@@ -363,3 +363,19 @@ extern "C" const char *fr_last_error(const fr_mesh *m) {
   if (m) return m->err.c_str();
   return g_create_error.c_str();
 }
+
+namespace frx {
+
+fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  *dev = m->dev;
+  *phys = m->dphys;
+  *stream = m->stream;
+  *device = m->device;
+  return FR_OK;
+}
+
+fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg) { return fail(m, st, msg); }
+
+}  // namespace frx

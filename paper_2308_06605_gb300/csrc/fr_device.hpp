@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "fr_internal.hpp"
 
@@ -43,6 +44,11 @@ cudaError_t upload_basis_tables();
 // MODE_RK applies RK44 stage `stage` with step dt.
 cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
                             double *Rout, cudaStream_t st, const PhaseEvents *ev = nullptr);
+// Accessors of the opaque mesh (fr_api.cu): a copy of its device view (fails if poisoned), and
+// recording an error on it.
+fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device);
+fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg);
+
 cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, double *d_out, cudaStream_t st);
 
 }  // namespace frx

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fr_residual": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int32]),
     "fr_rk_stage": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_double]),
     "fr_max_dt": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "fr_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "fr_probe_fma": (C.c_int32, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
@@ -184,6 +185,14 @@ class Mesh:
         p, where = _data_ptr(out)
         self._check(self._lib.fr_residual(self._h, t, p, where))
         return out
+
+    def residual_static(self, Q_device, R_device):
+        """fr_residual_static: residual of a device state into a device buffer, no allocation."""
+        q, wq = _data_ptr(Q_device)
+        r, wr = _data_ptr(R_device)
+        if wq != FR_DEVICE or wr != FR_DEVICE:
+            raise ValueError("fr_residual_static takes device tensors")
+        self._check(self._lib.fr_residual_static(self._h, q, r))
 
     def rk_stage(self, stage: int, t: float, dt: float, scheme: int = FR_RK44):
         self._check(self._lib.fr_rk_stage(self._h, scheme, stage, t, dt))
