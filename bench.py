@@ -29,12 +29,11 @@ if ROOT not in sys.path:
 METRIC = "solution-pt RK-stage updates/s at p=3..7, mixed-prec vs FP64, at stated error"
 UNIT = "updates/s"
 N_EDGE, ORDER, CFL = 64, 4, 0.3
-WORKLOAD = "tgv_64cube_p4_fp64"
 
 
 def config(precision="fp64"):
     n_pts = N_EDGE ** 3 * (ORDER + 1) ** 3
-    return {"workload": WORKLOAD, "mesh": f"{N_EDGE}^3 periodic hex [0,2pi]^3", "p": ORDER,
+    return {"workload": f"tgv_{N_EDGE}cube_p{ORDER}_{precision}", "mesh": f"{N_EDGE}^3 periodic hex [0,2pi]^3", "p": ORDER,
             "n_points": n_pts, "unknowns": 5 * n_pts, "case": "TGV Ma=0.1 Re=1600 gamma=1.4 Pr=0.71",
             "flux": "Rusanov + BR2, VCJH c=0 (DG)", "integrator": "RK44, CFL 0.3", "precision": precision,
             "l2": "no flush: working set ~18 GB >> 129 MB L2"}
@@ -264,7 +263,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-edge", type=int, default=N_EDGE, help="elements per edge (profiling of smaller cases)")
+    ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()
+    globals()["N_EDGE"], globals()["ORDER"] = args.n_edge, args.order
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
