@@ -132,8 +132,91 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU path
+SWEEP = [(64, 3), (64, 4), (48, 5), (40, 6), (32, 7)]   # (elements per edge, p): 17-33 M points
+# A double-float multiply-add (2 algorithmic flops) is 18 FP32 instructions (7 for the product,
+# 11 for the sum); the FP32 peak in FLOP/s counts an FFMA instruction as 2 flops, so the
+# double-float peak in algorithmic FLOP/s is fp32_peak / 2 instructions/s * 2 / 18 = fp32_peak / 18.
+DF_FP32_FLOPS_PER_FLOP = 18.0
+
+
+class Case:
+    """One mesh + state on the device, stepping with RK44 on the torch current stream."""
+
+    def __init__(self, n_edge, p, precision, dt=None):
+        import numpy as np
+        import torch
+        from paper_2308_06605_gb300 import fr, inputs as I
+        self.torch = torch
+        self.stream = torch.cuda.current_stream()
+        phys = I.tgv_physics()
+        phys.precision = 1 if precision == "mixed" else 0
+        self.mesh = fr.Mesh(I.hex_box_mesh((n_edge, n_edge, n_edge)), phys, p, stream=self.stream.cuda_stream)
+        x = self.mesh.solution_points()
+        self.Q0 = np.ascontiguousarray(I.tgv_state(x, Ma=0.1))
+        del x
+        self.Qd = torch.from_numpy(self.Q0).to("cuda")
+        self.mesh.set_state(self.Qd)
+        self.dt = dt if dt is not None else self.mesh.max_dt(CFL)
+        self.n_pts = self.mesh.n_elem * self.mesh.n_pts
+        self.t = 0.0
+
+    def step(self):
+        for s in range(4):
+            self.mesh.rk_stage(s, self.t, self.dt)
+        self.t += self.dt
+
+    def timed(self, steps):
+        torch = self.torch
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            self.step()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def kernels(self, steps, p):
+        from paper_2308_06605_gb300 import perfmodel
+        self.mesh.profile(True)
+        for _ in range(steps):
+            self.step()
+        kms, kcnt = self.mesh.profile_read(4)
+        self.mesh.profile(False)
+        fl, by = perfmodel.flops_per_point(p), perfmodel.bytes_per_point(p)
+        out = {}
+        for k, name in enumerate(perfmodel.KERNELS):
+            avg = kms[k] / max(1, kcnt[k])
+            out[name] = {"launches": kcnt[k], "avg_ms": avg, "share": kms[k] / max(1e-30, sum(kms)),
+                         "gflops": fl[name] * self.n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None,
+                         "gbs": by[name] * self.n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None}
+        return out
+
+    def close(self):
+        self.mesh.close()
+        del self.Qd
+
+
+def residual_error(a, b):
+    """Per-variable max-norm and L2 relative difference of two device residuals (b = reference)."""
+    torch = a.torch
+    Ra = torch.empty_like(a.Qd)
+    Rb = torch.empty_like(b.Qd)
+    a.mesh.set_state(a.Qd)
+    b.mesh.set_state(b.Qd)
+    a.mesh.residual(out=Ra)
+    b.mesh.residual(out=Rb)
+    torch.cuda.synchronize()
+    d = (Ra - Rb).reshape(-1, 5)
+    r = Rb.reshape(-1, 5)
+    linf = (d.abs().amax(0) / r.abs().amax(0)).tolist()
+    l2 = (d.norm(dim=0) / r.norm(dim=0)).tolist()
+    names = ["rho", "rho_u", "rho_v", "rho_w", "E"]
+    return {"max_rel": dict(zip(names, linf)), "l2_rel": dict(zip(names, l2))}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     rank, world, local = _env_rank()
     if world > 1:
@@ -141,36 +224,31 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    from paper_2308_06605_gb300 import fr, inputs as I, perfmodel
+    from paper_2308_06605_gb300 import fr
     if not os.path.exists(fr.LIB_PATH):
         from paper_2308_06605_gb300 import build as B
         B.build()
     fr.load()
-    stream = torch.cuda.current_stream()
-    desc = I.hex_box_mesh((N_EDGE, N_EDGE, N_EDGE))
-    phys = I.tgv_physics()
-    mesh = fr.Mesh(desc, phys, ORDER, stream=stream.cuda_stream)
-    x = mesh.solution_points()
-    Q0 = np.ascontiguousarray(I.tgv_state(x, Ma=0.1))
-    del x
-    Qd = torch.from_numpy(Q0).to(f"cuda:{dev}")
-    mesh.set_state(Qd)
-    dt = mesh.max_dt(CFL)
-    n_pts = mesh.n_elem * mesh.n_pts
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    def step(t):
-        for s in range(4):
-            mesh.rk_stage(s, t, dt)
+    def max_over_ranks(v):
+        if world > 1:
+            tt = torch.tensor([v], device=f"cuda:{dev}", dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            v = float(tt.item())
+        return v
 
-    t = 0.0
-    for _ in range(args.warmup):
-        step(t)
-        t += dt
-    torch.cuda.synchronize()
+    # Headline workload: both precisions on the same initial state and the same dt.
+    c64 = Case(N_EDGE, ORDER, "fp64")
+    cmx = Case(N_EDGE, ORDER, "mixed", dt=c64.dt)
+    err = residual_error(cmx, c64)
+    n_pts = c64.n_pts
+    for c in (c64, cmx):
+        for _ in range(args.warmup):
+            c.step()
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     gid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else str(dev))
@@ -179,73 +257,76 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(t)
-        t += dt
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_mx = max_over_ranks(cmx.timed(args.steps))
+    ms_64 = max_over_ranks(c64.timed(args.steps))
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n_pts * 4 * args.steps / (ms * 1e-3)
-
-    # Per-kernel device times over the same number of steps (events on the launching stream).
-    mesh.profile(True)
-    for _ in range(args.steps):
-        step(t)
-        t += dt
-    kms, kcnt = mesh.profile_read(4)
-    mesh.profile(False)
-    kernels = {}
+    value = world * n_pts * 4 * args.steps / (ms_mx * 1e-3)
+    value64 = world * n_pts * 4 * args.steps / (ms_64 * 1e-3)
+    k_mx = cmx.kernels(args.steps, ORDER)
+    k_64 = c64.kernels(args.steps, ORDER)
+    fp64_peak = fr.probe_fma(0, 4000)
+    fp32_peak = fr.probe_fma(1, 200000)
+    df_peak = fp32_peak / DF_FP32_FLOPS_PER_FLOP
+    dom = max(k_mx, key=lambda n_: k_mx[n_]["share"])
+    from paper_2308_06605_gb300 import perfmodel
     fl = perfmodel.flops_per_point(ORDER)
     by = perfmodel.bytes_per_point(ORDER)
-    for k, name in enumerate(perfmodel.KERNELS):
-        avg = kms[k] / max(1, kcnt[k])
-        kernels[name] = {"launches": kcnt[k], "avg_ms": avg, "share": kms[k] / max(1e-30, sum(kms)),
-                         "gflops": fl[name] * n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None,
-                         "gbs": by[name] * n_pts / (avg * 1e-3) / 1e9 if avg > 0 else None}
-    dom = max(kernels, key=lambda n_: kernels[n_]["share"])
-    fp64_peak = fr.probe_fma(0, 4000)
-    ach = kernels[dom]["gflops"] * 1e9
-    roofline = {"bound": "alu", "kernel": dom, "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "measured FP64 DFMA rate of this GPU (fr_probe_fma, 8 chains x 152x8 blocks)",
+    ach = k_mx[dom]["gflops"] * 1e9
+    roofline = {"bound": "alu", "kernel": dom, "precision": "mixed (double-float on the FP32 pipe)",
+                "achieved": ach / 1e12, "peak": df_peak / 1e12, "unit": "TFLOP/s", "frac": ach / df_peak,
+                "traffic": None,
+                "peak_source": "measured FP32 FMA rate (fr_probe_fma) / 18: a double-float multiply-add is 18 FP32 "
+                               "instructions for 2 algorithmic flops",
                 "algorithmic_flops_per_point": fl[dom], "algorithmic_bytes_per_point": by[dom]}
+    dom64 = max(k_64, key=lambda n_: k_64[n_]["share"])
+    fp64 = {"value": value64, "ms_per_step": ms_64 / args.steps, "kernels": k_64,
+            "roofline": {"bound": "alu", "kernel": dom64, "achieved": k_64[dom64]["gflops"] / 1e3,
+                         "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": k_64[dom64]["gflops"] * 1e9 / fp64_peak,
+                         "traffic": TRAFFIC.get(("fp64", ORDER, N_EDGE, dom64)),
+                         "peak_source": "measured FP64 DFMA rate (fr_probe_fma)"}}
+    c64.close()
 
-    # End to end through the public API with host buffers: set_state from pinned host memory,
-    # four stages, get_state back to pinned host memory, every step.
-    Qh = torch.from_numpy(Q0).pin_memory()
+    # End to end through the public API with host buffers (headline path): set_state from pinned
+    # host memory, four stages, get_state back to pinned host memory, every step.
+    Qh = torch.from_numpy(cmx.Q0).pin_memory()
     Out = torch.empty_like(Qh).pin_memory()
     k_e2e = max(1, args.steps)
     torch.cuda.synchronize()
     barrier()
     te0 = time.perf_counter()
     for _ in range(k_e2e):
-        mesh.set_state(Qh)
-        step(0.0)
-        mesh.get_state(out=Out)
+        cmx.mesh.set_state(Qh)
+        cmx.step()
+        cmx.mesh.get_state(out=Out)
     torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    if world > 1:
-        tt = torch.tensor([te], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt.item())
+    te = max_over_ranks(time.perf_counter() - te0)
     e2e = {"value": world * n_pts * 4 * k_e2e / te, "unit": UNIT,
            "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8)}
-    mesh.close()
+    cmx.close()
+    del Qh, Out
+
+    sweep = {}
+    if not args.no_sweep:
+        for (n, p) in SWEEP:
+            row = {"n_edge": n, "n_points": n ** 3 * (p + 1) ** 3}
+            dt = None
+            for prec in ("fp64", "mixed"):
+                c = Case(n, p, prec, dt=dt)
+                dt = c.dt
+                c.step()
+                ms = c.timed(2)
+                row[prec] = n ** 3 * (p + 1) ** 3 * 4 * 2 / (ms * 1e-3)
+                c.close()
+            sweep[f"p{p}"] = row
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(),
-            "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * 4 * args.steps, "roofline": roofline,
-            "kernels": kernels, "fp64_fma_peak_tflops": fp64_peak / 1e12}
+            "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+            "config": config("mixed"), "clocks": clocks, "e2e": e2e,
+            "gpu_launches": 2 * 4 * 4 * args.steps, "roofline": roofline, "kernels": k_mx,
+            "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
+            "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, cores = oracle_rate(budget_s=12.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -256,6 +337,12 @@ def run_ours(args):
     return 0
 
 
+# DRAM traffic per launch of the dominant kernel from ncu captures (precision, p, n_edge, kernel)
+# -> bytes; scaled from a 32^3 capture by the element count.  Only valid for the kernel version
+# that was profiled.
+TRAFFIC = {}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +350,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the p = 3..7 sweep")
     ap.add_argument("--n-edge", type=int, default=N_EDGE, help="elements per edge (profiling of smaller cases)")
     ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()

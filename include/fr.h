@@ -88,7 +88,9 @@ typedef struct {
   int32_t inviscid;     /* FR_RUSANOV | FR_ROE */
   int32_t viscous;      /* FR_VISC_NONE | FR_VISC_BR2 */
   double br2_eta;       /* BR2 penalty factor (number of faces, 6, by default) */
-  int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED */
+  int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED: element operators (traces, gradients,
+                           fluxes at solution points, divergence, correction) in double-float
+                           (FP32 hi + lo pairs); Riemann flux, boundary states and RK in FP64 */
 } fr_physics;
 
 typedef struct {
@@ -172,7 +174,8 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
  * before any stream capture.  All calls share the one array and it keeps the last call's
  * contents; nothing in it needs to start at zero, but calls whose work overlaps on the GPU
  * (other streams, other meshes, other threads) race on it: serialise them.  Work is enqueued
- * on the mesh's stream and the call returns without synchronising.
+ * on the mesh's stream and the call returns without synchronising.  FP64 meshes only
+ * (FR_EUNSUPPORTED for FR_PREC_MIXED).
  */
 fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
 

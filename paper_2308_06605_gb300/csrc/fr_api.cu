@@ -86,7 +86,7 @@ static fr_status check_mesh(fr_mesh *m) {
 
 static void release(fr_mesh *m) {
   DevMesh &d = m->dev;
-  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf};
+  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf, d.Qc};
   for (double *p : dbl)
     if (p) cudaFree(p);
   if (d.ef) cudaFree(d.ef);
@@ -130,7 +130,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   if (phys->inviscid != FR_RUSANOV) return fail(nullptr, FR_EUNSUPPORTED, "only the Rusanov flux is built");
   if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2)
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
-  if (phys->precision != FR_PREC_FP64) return fail(nullptr, FR_EUNSUPPORTED, "only FP64 is built");
+  if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED)
+    return fail(nullptr, FR_EINVAL, "unknown precision");
   for (int k = 0; k < desc->n_bc; ++k) {
     const fr_bc &b = desc->bc[k];
     if (b.kind < FR_BC_WALL_ISOTHERMAL || b.kind > FR_BC_DIRICHLET)
@@ -171,6 +172,18 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   dp.eta = phys->br2_eta;
   dp.viscous = (phys->viscous == FR_VISC_BR2 && phys->mu > 0.0) ? 1 : 0;
   dp.inviscid = phys->inviscid;
+  {
+    const double vals[10] = {dp.gamma, dp.gamma - 1.0, (dp.gamma - 1.0) / dp.R, dp.mu, -2.0 * dp.mu / 3.0,
+                             dp.kappa, dp.eta, 0.0, 0.5, 1.0};
+    double *dd[10] = {&dp.d.gamma, &dp.d.gm1, &dp.d.cT, &dp.d.mu, &dp.d.m2mu3, &dp.d.kappa, &dp.d.eta,
+                      &dp.d.zero, &dp.d.half, &dp.d.one};
+    df32 *ff[10] = {&dp.f.gamma, &dp.f.gm1, &dp.f.cT, &dp.f.mu, &dp.f.m2mu3, &dp.f.kappa, &dp.f.eta,
+                    &dp.f.zero, &dp.f.half, &dp.f.one};
+    for (int k = 0; k < 10; ++k) {
+      *dd[k] = vals[k];
+      *ff[k] = df_split_host(vals[k]);
+    }
+  }
 
   auto bail = [&](fr_status s) {
     std::string msg = m->err;
@@ -194,6 +207,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   DevMesh &d = m->dev;
   d.p = h.p; d.N = h.N; d.Np = h.Np; d.Nf = h.Nf;
   d.E = h.E; d.n_if = h.n_if; d.n_interior = h.n_interior;
+  d.mixed = (phys->precision == FR_PREC_MIXED) ? 1 : 0;
   const size_t nsol = (size_t)h.E * h.Np * 5;
   const size_t Nf = h.Nf;
   if ((st = dalloc(m, &d.Q, nsol)) || (st = dalloc(m, &d.Un, nsol)) || (st = dalloc(m, &d.acc, nsol)) ||
@@ -203,8 +217,18 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
       (st = dalloc(m, &d.Gtr, (size_t)h.n_if * 2 * 15 * Nf)) || (st = dalloc(m, &d.FI, (size_t)h.n_if * 5 * Nf)) ||
       (st = dalloc(m, &d.h, (size_t)h.E)) || (st = dalloc(m, &d.dtbuf, (size_t)h.E + 1)) ||
       (st = dalloc(m, &d.ef, h.ef.size())) || (st = dalloc(m, &d.if_bc, h.if_bc.size())) ||
-      (st = dalloc(m, &d.bcs, h.bcs.size())) || (st = dalloc(m, &d.flag, 1)))
+      (st = dalloc(m, &d.bcs, h.bcs.size())) || (st = dalloc(m, &d.flag, 1)) ||
+      (d.mixed && (st = dalloc(m, &d.Qc, nsol))))
     return bail(st);
+  if (d.mixed) {
+    // Geometry in the element arithmetic's format: each double becomes a df32 (hi, lo) pair
+    // stored in the same 8-byte slot.
+    for (std::vector<double> *v : {&h.metrics, &h.liftfac, &h.normals})
+      for (double &x : *v) {
+        df32 p = df_split_host(x);
+        std::memcpy(&x, &p, sizeof(double));
+      }
+  }
   ce = cudaMallocHost((void **)&m->h_scalar, 4 * sizeof(double));
   if (ce != cudaSuccess) { m->err = cudaGetErrorString(ce); return bail(FR_ENOMEM); }
   struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
@@ -266,6 +290,7 @@ extern "C" fr_status fr_set_state(fr_mesh *m, const double *Q, int32_t where) {
   const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
   FR_CUDA(m, cudaMemcpyAsync(m->dev.Q, Q, bytes, kind_of(where, true), m->stream));
   FR_CUDA(m, cudaMemcpyAsync(m->dev.Un, m->dev.Q, bytes, cudaMemcpyDeviceToDevice, m->stream));
+  FR_CUDA(m, launch_state_copy(m->dev, m->stream));
   if (where == FR_HOST) FR_CUDA(m, cudaStreamSynchronize(m->stream));
   return FR_OK;
 }

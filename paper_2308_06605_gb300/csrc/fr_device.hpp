@@ -6,27 +6,32 @@
 #include <cstdint>
 #include <string>
 
+#include "df32.cuh"
 #include "fr_internal.hpp"
 
 namespace frx {
 
-struct DevBasis {
-  double D[kMaxN * kMaxN];    // D[i*N + a] = l_a'(x_i)
-  double Dt[kMaxN * kMaxN];   // D - hp (x) lp + hm (x) lm: divergence with the own-flux correction
-  double lm[kMaxN], lp[kMaxN], hm[kMaxN], hp[kMaxN];
+// Physical constants in the element arithmetic's scalar type (double or df32).
+template <typename T>
+struct PhysT {
+  T gamma, gm1, cT, mu, m2mu3, kappa, eta;   // cT = (gamma-1)/R, m2mu3 = -2 mu / 3
+  T zero, half, one;
 };
 
 struct DevPhys {
   double gamma, R, mu, kappa, eta;
   int viscous;
   int inviscid;
+  PhysT<double> d;
+  PhysT<df32> f;
 };
 
 // Device buffers of one mesh (all owned by the mesh).
 struct DevMesh {
   int p, N, Np, Nf;
   int64_t E, n_if, n_interior;
-  double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf;
+  int mixed;        // 1: element arrays hold df32 pairs (same 8-byte slots), Qc holds the state as df32
+  double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc;
   int32_t *ef, *if_bc;
   fr_bc *bcs;
   int *flag;
@@ -49,6 +54,8 @@ cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int s
 fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device);
 fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg);
 
+// Mixed path: refresh the df32 copy of the state after it was set from outside.
+cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st);
 cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, double *d_out, cudaStream_t st);
 
 }  // namespace frx

@@ -1,28 +1,53 @@
-// FP64 kernels of the FR residual and the RK44 stage update (arXiv 2308.06605, section
-// "FR Algorithm", Eq. 1-3).  One residual evaluation is four launches:
+// Kernels of the FR residual and the RK44 stage update (arXiv 2308.06605, section "FR
+// Algorithm", Eq. 1-3).  One residual evaluation is four launches (plus two for boundary faces):
 //   interp_faces : Q -> solution traces at the flux points of every face (interface slots)
+//   bc_prepare   : boundary faces: common solution Q^I and ghost traces
 //   volume       : per element, BR2-corrected gradients, physical + transformed fluxes at the
 //                  solution points, gradient traces at the flux points, and the divergence of
 //                  the transformed flux including the own-flux part of the correction
-//   iface_flux   : per interface flux point, Rusanov + BR2 common normal flux
+//   iface_flux   : per interface flux point, Rusanov + BR2 common normal flux (bc_flux for
+//                  boundary faces)
 //   correct      : per solution point, adds the common-flux correction, scales by -1/|J| and
-//                  writes R or applies the RK44 stage update.
+//                  writes R or applies the RK44 stage update (always FP64).
+//
+// Every kernel is a template on the scalar type T of its element arithmetic and of the arrays it
+// exchanges: T = double is the FP64 path; T = df32 (FP32 hi + lo pairs on the FP32 pipe) is the
+// mixed path, in which the Riemann flux's pressure/energy recovery, the boundary states and the
+// RK update stay FP64.
 #include <cuda_runtime.h>
 
 #include <cmath>
 
+#include "df32.cuh"
 #include "fr_device.hpp"
 
 namespace frx {
 
-__constant__ DevBasis c_basis[kMaxN];   // index N - 1 (N = 2..8 used)
+template <typename T>
+struct BasisT {
+  T D[kMaxN * kMaxN];    // D[i*N + a] = l_a'(x_i)
+  T Dt[kMaxN * kMaxN];   // D - hp (x) lp + hm (x) lm: divergence with the own-flux correction
+  T lm[kMaxN], lp[kMaxN], hm[kMaxN], hp[kMaxN];
+};
+
+__constant__ BasisT<double> c_basis_d[kMaxN];   // index N - 1
+__constant__ BasisT<df32> c_basis_f[kMaxN];
+
+template <typename T> __device__ __forceinline__ const BasisT<T> &cbasis(int N);
+template <> __device__ __forceinline__ const BasisT<double> &cbasis<double>(int N) { return c_basis_d[N - 1]; }
+template <> __device__ __forceinline__ const BasisT<df32> &cbasis<df32>(int N) { return c_basis_f[N - 1]; }
+
+template <typename T> __device__ __forceinline__ const PhysT<T> &phys_of(const DevPhys &p);
+template <> __device__ __forceinline__ const PhysT<double> &phys_of<double>(const DevPhys &p) { return p.d; }
+template <> __device__ __forceinline__ const PhysT<df32> &phys_of<df32>(const DevPhys &p) { return p.f; }
 
 cudaError_t upload_basis_tables() {
-  DevBasis hb[kMaxN] = {};
+  BasisT<double> hd[kMaxN] = {};
+  BasisT<df32> hf[kMaxN] = {};
   for (int p = 1; p < kMaxN; ++p) {
     Basis1D b = make_basis(p);
     const int N = p + 1;
-    DevBasis &d = hb[N - 1];
+    BasisT<double> &d = hd[N - 1];
     for (int i = 0; i < N; ++i) {
       d.lm[i] = b.lm[i];
       d.lp[i] = b.lp[i];
@@ -33,8 +58,21 @@ cudaError_t upload_basis_tables() {
         d.Dt[i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
       }
     }
+    BasisT<df32> &f = hf[N - 1];
+    for (int i = 0; i < kMaxN; ++i) {
+      f.lm[i] = df_split_host(d.lm[i]);
+      f.lp[i] = df_split_host(d.lp[i]);
+      f.hm[i] = df_split_host(d.hm[i]);
+      f.hp[i] = df_split_host(d.hp[i]);
+    }
+    for (int i = 0; i < kMaxN * kMaxN; ++i) {
+      f.D[i] = df_split_host(d.D[i]);
+      f.Dt[i] = df_split_host(d.Dt[i]);
+    }
   }
-  return cudaMemcpyToSymbol(c_basis, hb, sizeof(hb));
+  cudaError_t e = cudaMemcpyToSymbol(c_basis_d, hd, sizeof(hd));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_basis_f, hf, sizeof(hf));
 }
 
 // Strides of the reference axes in the point index m = i + N j + N^2 k.
@@ -63,6 +101,7 @@ __device__ __forceinline__ int slot_of(int code, int a, int b, int N) {
 // ------------------------------------------------------------------------------------------
 // Gas dynamics (ideal gas, Stokes hypothesis, constant mu, Fourier heat flux).
 // ------------------------------------------------------------------------------------------
+// Normal inviscid flux F(q).n and (|u.n^| + c)|n|, in FP64 (pressure/energy recovery).
 __device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double g,
                                                 double out[5], double &un_abs_plus_c_n) {
   const double ri = 1.0 / q[0];
@@ -79,28 +118,30 @@ __device__ __forceinline__ void normal_inviscid(const double q[5], const double 
 }
 
 // Viscous flux F_v[j][v] (j = direction) of state q with gradient G[j*5 + v] = dQ_v/dx_j.
-__device__ __forceinline__ void viscous_flux(const double q[5], const double *G, const DevPhys &ph,
-                                             double Fv[3][5]) {
-  const double ri = 1.0 / q[0];
-  const double u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-  const double eo = q[4] * ri;
-  double du[3][3];   // du[i][j] = du_i/dx_j
+template <typename T>
+__device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const PhysT<T> &ph, T Fv[3][5]) {
+  const T ri = ph.one / q[0];
+  const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  const T eo = q[4] * ri;
+  T du[3][3];   // du[i][j] = du_i/dx_j
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) du[i][j] = (G[j * 5 + 1 + i] - u[i] * G[j * 5]) * ri;
-  double dT[3];
-  const double cT = (ph.gamma - 1.0) / ph.R;
+  T dT[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j)
-    dT[j] = cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri - (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j]));
-  const double lam = -2.0 / 3.0 * ph.mu * (du[0][0] + du[1][1] + du[2][2]);
+    dT[j] = ph.cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri - (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j]));
+  const T lam = ph.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    double t[3];
+    T t[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t[i] = ph.mu * (du[i][j] + du[j][i]) + (i == j ? lam : 0.0);
-    Fv[j][0] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      t[i] = ph.mu * (du[i][j] + du[j][i]);
+      if (i == j) t[i] = t[i] + lam;
+    }
+    Fv[j][0] = ph.zero;
     Fv[j][1] = t[0];
     Fv[j][2] = t[1];
     Fv[j][3] = t[2];
@@ -111,9 +152,9 @@ __device__ __forceinline__ void viscous_flux(const double q[5], const double *G,
 // ------------------------------------------------------------------------------------------
 // 1. Solution traces.  Thread per (element, face, flux point).
 // ------------------------------------------------------------------------------------------
-template <int N>
-__global__ void k_interp_faces(const double *__restrict__ Q, const int32_t *__restrict__ ef,
-                               double *__restrict__ Qtr, int64_t E) {
+template <int N, typename T>
+__global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restrict__ ef,
+                               T *__restrict__ Qtr, int64_t E) {
   constexpr int Np = N * N * N, Nf = N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * 6 * Nf) return;
@@ -121,16 +162,18 @@ __global__ void k_interp_faces(const double *__restrict__ Q, const int32_t *__re
   const int64_t eff = t / Nf;
   const int f = (int)(eff % 6);
   const int64_t e = eff / 6;
-  const DevBasis &B = c_basis[N - 1];
-  const double *l = (f & 1) ? B.lp : B.lm;
+  const BasisT<T> &B = cbasis<T>(N);
+  const T *l = (f & 1) ? B.lp : B.lm;
   int base, sd;
   face_line<N>(f, r, base, sd);
-  const double *q = Q + e * Np * 5;
-  double acc[5] = {0, 0, 0, 0, 0};
+  const T *q = Q + e * Np * 5;
+  T acc[5];
 #pragma unroll
-  for (int c = 0; c < N; ++c) {
-    const double lc = l[c];
-    const double *qc = q + (base + c * sd) * 5;
+  for (int v = 0; v < 5; ++v) acc[v] = l[0] * q[base * 5 + v];
+#pragma unroll
+  for (int c = 1; c < N; ++c) {
+    const T lc = l[c];
+    const T *qc = q + (base + c * sd) * 5;
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += lc * qc[v];
   }
@@ -138,7 +181,7 @@ __global__ void k_interp_faces(const double *__restrict__ Q, const int32_t *__re
   const int64_t I = packed >> 4;
   const int side = (packed >> 3) & 1;
   const int slot = slot_of(packed & 7, r % N, r / N, N);
-  double *dst = Qtr + (I * 2 + side) * 5 * Nf + slot;
+  T *dst = Qtr + (I * 2 + side) * 5 * Nf + slot;
 #pragma unroll
   for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v];
 }
@@ -147,20 +190,25 @@ __global__ void k_interp_faces(const double *__restrict__ Q, const int32_t *__re
 // 2. Volume kernel.  One block per element, one thread per solution point.
 // ------------------------------------------------------------------------------------------
 template <int N>
-__global__ void k_volume(const double *__restrict__ Q, const double *__restrict__ metrics,
-                         const int32_t *__restrict__ ef, const double *__restrict__ Qtr,
-                         const double *__restrict__ liftfac, double *__restrict__ Gtr,
-                         double *__restrict__ Rpart, DevPhys ph) {
+constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
+
+template <int N, typename T>
+__global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restrict__ Q, const T *__restrict__ metrics,
+                         const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
+                         const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
+                         DevPhys dph) {
   constexpr int Np = N * N * N, Nf = N * N;
-  extern __shared__ double sm[];
-  double *sQ = sm;                 // [5][Np]
-  double *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
-  double *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
-  double *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
+  extern __shared__ double sm_raw[];
+  T *sm = reinterpret_cast<T *>(sm_raw);
+  T *sQ = sm;                 // [5][Np]
+  T *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
+  T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
+  T *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
+  const PhysT<T> &ph = phys_of<T>(dph);
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
-  const DevBasis &B = c_basis[N - 1];
-  const bool viscous = ph.viscous != 0;
+  const BasisT<T> &B = cbasis<T>(N);
+  const bool viscous = dph.viscous != 0;
   for (int t = tid; t < 5 * Np; t += blockDim.x) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
   if (viscous) {
     for (int t = tid; t < 6 * Nf; t += blockDim.x) {
@@ -169,46 +217,49 @@ __global__ void k_volume(const double *__restrict__ Q, const double *__restrict_
       const int64_t I = packed >> 4;
       const int side = (packed >> 3) & 1;
       const int slot = slot_of(packed & 7, r % N, r / N, N);
-      const double *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
-      const double *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
+      const T *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
+      const T *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = 0.5 * (oth[v * Nf] - own[v * Nf]);
+      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = ph.half * (oth[v * Nf] - own[v * Nf]);
     }
   }
   __syncthreads();
   if (tid < Np) {
     const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
-    double S[9];
-    const double *met = metrics + e * 10 * Np + m;
+    T S[9];
+    const T *met = metrics + e * 10 * Np + m;
 #pragma unroll
     for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
-    const double invJ = met[9 * Np];
-    double q[5];
+    const T invJ = met[9 * Np];
+    T q[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v] = sQ[v * Np + m];
-    double H[3][5];
+    T H[3][5];
     {
       // Inviscid flux F_j.
-      const double ri = 1.0 / q[0];
-      const double u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-      const double p = (ph.gamma - 1.0) * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+      const T ri = ph.one / q[0];
+      const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+      const T p = ph.gm1 * (q[4] - ph.half * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
         H[jj][0] = q[1 + jj];
-        H[jj][1] = q[1] * u[jj] + (jj == 0 ? p : 0.0);
-        H[jj][2] = q[2] * u[jj] + (jj == 1 ? p : 0.0);
-        H[jj][3] = q[3] * u[jj] + (jj == 2 ? p : 0.0);
+        H[jj][1] = q[1] * u[jj];
+        H[jj][2] = q[2] * u[jj];
+        H[jj][3] = q[3] * u[jj];
+        H[jj][1 + jj] = H[jj][1 + jj] + p;
         H[jj][4] = (q[4] + p) * u[jj];
       }
     }
     if (viscous) {
-      double gu[3][5], gc[3][5];
+      T gu[3][5], gc[3][5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double *sq = sQ + v * Np;
-        double a0 = 0, a1 = 0, a2 = 0;
+        const T *sq = sQ + v * Np;
+        T a0 = B.D[i * N] * sq[N * j + N * N * k];
+        T a1 = B.D[j * N] * sq[i + N * N * k];
+        T a2 = B.D[k * N] * sq[i + N * j];
 #pragma unroll
-        for (int a = 0; a < N; ++a) {
+        for (int a = 1; a < N; ++a) {
           a0 += B.D[i * N + a] * sq[a + N * j + N * N * k];
           a1 += B.D[j * N + a] * sq[i + N * a + N * N * k];
           a2 += B.D[k * N + a] * sq[i + N * j + N * N * a];
@@ -220,17 +271,18 @@ __global__ void k_volume(const double *__restrict__ Q, const double *__restrict_
         gc[1][v] = a1 - B.hm[j] * sdQ[(2 * 5 + v) * Nf + i + N * k] + B.hp[j] * sdQ[(3 * 5 + v) * Nf + i + N * k];
         gc[2][v] = a2 - B.hm[k] * sdQ[(4 * 5 + v) * Nf + i + N * j] + B.hp[k] * sdQ[(5 * 5 + v) * Nf + i + N * j];
       }
-      double G[15];
+      T G[15];
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj)
+      for (int jj = 0; jj < 3; ++jj) {
+        const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const double s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
           sG[(jj * 5 + v) * Np + m] = s0 * gu[0][v] + s1 * gu[1][v] + s2 * gu[2][v];
           G[jj * 5 + v] = s0 * gc[0][v] + s1 * gc[1][v] + s2 * gc[2][v];
         }
-      double Fv[3][5];
-      viscous_flux(q, G, ph, Fv);
+      }
+      T Fv[3][5];
+      viscous_flux<T>(q, G, ph, Fv);
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
@@ -247,24 +299,24 @@ __global__ void k_volume(const double *__restrict__ Q, const double *__restrict_
     // Gradient traces: uncorrected gradient interpolated to the face + eta * own lifting.
     for (int t = tid; t < 6 * Nf; t += blockDim.x) {
       const int f = t / Nf, r = t % Nf;
-      const double *l = (f & 1) ? B.lp : B.lm;
+      const T *l = (f & 1) ? B.lp : B.lm;
       int base, sd;
       face_line<N>(f, r, base, sd);
       const int packed = ef[e * 6 + f];
       const int64_t I = packed >> 4;
       const int side = (packed >> 3) & 1;
       const int slot = slot_of(packed & 7, r % N, r / N, N);
-      double *dst = Gtr + (I * 2 + side) * 15 * Nf + slot;
-      const double *lf = liftfac + (e * 6 + f) * 3 * Nf + r;
+      T *dst = Gtr + (I * 2 + side) * 15 * Nf + slot;
+      const T *lf = liftfac + (e * 6 + f) * 3 * Nf + r;
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
-        const double lj = ph.eta * lf[jj * Nf];
+        const T lj = ph.eta * lf[jj * Nf];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const double *sg = sG + (jj * 5 + v) * Np + base;
-          double acc = 0.0;
+          const T *sg = sG + (jj * 5 + v) * Np + base;
+          T acc = l[0] * sg[0];
 #pragma unroll
-          for (int c = 0; c < N; ++c) acc += l[c] * sg[c * sd];
+          for (int c = 1; c < N; ++c) acc += l[c] * sg[c * sd];
           dst[(jj * 5 + v) * Nf] = acc + lj * sdQ[(f * 5 + v) * Nf + r];
         }
       }
@@ -272,13 +324,15 @@ __global__ void k_volume(const double *__restrict__ Q, const double *__restrict_
   }
   if (tid < Np) {
     const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
-    double *out = Rpart + (e * Np + m) * 5;
+    T *out = Rpart + (e * Np + m) * 5;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double *h0 = sH + (0 * 5 + v) * Np, *h1 = sH + (1 * 5 + v) * Np, *h2 = sH + (2 * 5 + v) * Np;
-      double acc = 0.0;
+      const T *h0 = sH + (0 * 5 + v) * Np, *h1 = sH + (1 * 5 + v) * Np, *h2 = sH + (2 * 5 + v) * Np;
+      T acc = B.Dt[i * N] * h0[N * j + N * N * k];
+      acc += B.Dt[j * N] * h1[i + N * N * k];
+      acc += B.Dt[k * N] * h2[i + N * j];
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
+      for (int a = 1; a < N; ++a) {
         acc += B.Dt[i * N + a] * h0[a + N * j + N * N * k];
         acc += B.Dt[j * N + a] * h1[i + N * a + N * N * k];
         acc += B.Dt[k * N + a] * h2[i + N * j + N * N * a];
@@ -289,43 +343,50 @@ __global__ void k_volume(const double *__restrict__ Q, const double *__restrict_
 }
 
 // ------------------------------------------------------------------------------------------
-// 3. Common normal flux at the flux points of two-sided interfaces (Rusanov + BR2).
+// 3. Common normal flux at the flux points of two-sided interfaces (Rusanov + BR2).  The
+// inviscid part (pressure/energy recovery) is FP64 in both paths.
 // ------------------------------------------------------------------------------------------
-template <int N>
-__global__ void k_iface_flux(const double *__restrict__ Qtr, const double *__restrict__ Gtr,
-                             const double *__restrict__ normals, double *__restrict__ FI,
-                             int64_t n_if, DevPhys ph) {
+template <int N, typename T>
+__global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
+                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph) {
   constexpr int Nf = N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_if * Nf) return;
   const int64_t I = t / Nf;
   const int q = (int)(t % Nf);
-  double qL[5], qR[5], n[3];
+  T qL[5], qR[5], nT[3];
+  double qLd[5], qRd[5], n[3];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qL[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
     qR[v] = Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q];
+    qLd[v] = to_double(qL[v]);
+    qRd[v] = to_double(qR[v]);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) n[c] = normals[(I * 3 + c) * Nf + q];
+  for (int c = 0; c < 3; ++c) {
+    nT[c] = normals[(I * 3 + c) * Nf + q];
+    n[c] = to_double(nT[c]);
+  }
   double fL[5], fR[5], sL, sR;
-  normal_inviscid(qL, n, ph.gamma, fL, sL);
-  normal_inviscid(qR, n, ph.gamma, fR, sR);
+  normal_inviscid(qLd, n, dph.gamma, fL, sL);
+  normal_inviscid(qRd, n, dph.gamma, fR, sR);
   const double lam = fmax(sL, sR);
-  double F[5];
+  T F[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (qR[v] - qL[v]);
-  if (ph.viscous) {
-    double qc[5], G[15];
+  for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (qRd[v] - qLd[v]));
+  if (dph.viscous) {
+    const PhysT<T> &ph = phys_of<T>(dph);
+    T qc[5], G[15];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qc[v] = 0.5 * (qL[v] + qR[v]);
+    for (int v = 0; v < 5; ++v) qc[v] = ph.half * (qL[v] + qR[v]);
 #pragma unroll
     for (int c = 0; c < 15; ++c)
-      G[c] = 0.5 * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
-    double Fv[3][5];
-    viscous_flux(qc, G, ph, Fv);
+      G[c] = ph.half * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
+    T Fv[3][5];
+    viscous_flux<T>(qc, G, ph, Fv);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * n[0] + Fv[1][v] * n[1] + Fv[2][v] * n[2];
+    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
@@ -334,6 +395,7 @@ __global__ void k_iface_flux(const double *__restrict__ Qtr, const double *__res
 // ------------------------------------------------------------------------------------------
 // 3b. Boundary faces.  Side 0 of a boundary interface is the element; its side-1 slot holds
 // 2 Q^I - Q- so that the volume kernel's (other - own)/2 equals Q^I - Q- for the BR2 jump.
+// Boundary states are FP64 in both paths.
 // ------------------------------------------------------------------------------------------
 // Ghost state (for the Rusanov flux) and boundary common solution Q^I from the interior trace.
 __device__ void boundary_states(const double qm[5], const double n[3], const fr_bc &bc, const DevPhys &ph,
@@ -387,8 +449,8 @@ __device__ void boundary_states(const double qm[5], const double n[3], const fr_
   for (int v = 0; v < 5; ++v) ghost[v] = qi[v];
 }
 
-template <int N>
-__global__ void k_bc_prepare(double *__restrict__ Qtr, const double *__restrict__ normals,
+template <int N, typename T>
+__global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
                              const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
                              int64_t first, int64_t count, DevPhys ph) {
   constexpr int Nf = N * N;
@@ -398,89 +460,95 @@ __global__ void k_bc_prepare(double *__restrict__ Qtr, const double *__restrict_
   const int q = (int)(t % Nf);
   double qm[5], n[3], gh[5], qi[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) qm[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
+  for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) n[c] = normals[(I * 3 + c) * Nf + q];
+  for (int c = 0; c < 3; ++c) n[c] = to_double(normals[(I * 3 + c) * Nf + q]);
   boundary_states(qm, n, bcs[if_bc[I]], ph, gh, qi);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q] = 2.0 * qi[v] - qm[v];
+  for (int v = 0; v < 5; ++v) Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q] = from_double<T>(2.0 * qi[v] - qm[v]);
 }
 
-template <int N>
-__global__ void k_bc_flux(const double *__restrict__ Qtr, const double *__restrict__ Gtr,
-                          const double *__restrict__ normals, const int32_t *__restrict__ if_bc,
-                          const fr_bc *__restrict__ bcs, double *__restrict__ FI, int64_t first,
-                          int64_t count, DevPhys ph) {
+template <int N, typename T>
+__global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
+                          const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs, T *__restrict__ FI,
+                          int64_t first, int64_t count, DevPhys dph) {
   constexpr int Nf = N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count * Nf) return;
   const int64_t I = first + t / Nf;
   const int q = (int)(t % Nf);
   double qm[5], n[3], gh[5], qi[5];
+  T nT[3];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) qm[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
+  for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) n[c] = normals[(I * 3 + c) * Nf + q];
-  boundary_states(qm, n, bcs[if_bc[I]], ph, gh, qi);
+  for (int c = 0; c < 3; ++c) {
+    nT[c] = normals[(I * 3 + c) * Nf + q];
+    n[c] = to_double(nT[c]);
+  }
+  boundary_states(qm, n, bcs[if_bc[I]], dph, gh, qi);
   double fL[5], fR[5], sL, sR;
-  normal_inviscid(qm, n, ph.gamma, fL, sL);
-  normal_inviscid(gh, n, ph.gamma, fR, sR);
+  normal_inviscid(qm, n, dph.gamma, fL, sL);
+  normal_inviscid(gh, n, dph.gamma, fR, sR);
   const double lam = fmax(sL, sR);
-  double F[5];
+  T F[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]);
-  if (ph.viscous) {
-    double G[15];
+  for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]));
+  if (dph.viscous) {
+    const PhysT<T> &ph = phys_of<T>(dph);
+    T G[15], qiT[5];
 #pragma unroll
     for (int c = 0; c < 15; ++c) G[c] = Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q];
-    double Fv[3][5];
-    viscous_flux(qi, G, ph, Fv);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * n[0] + Fv[1][v] * n[1] + Fv[2][v] * n[2];
+    for (int v = 0; v < 5; ++v) qiT[v] = from_double<T>(qi[v]);
+    T Fv[3][5];
+    viscous_flux<T>(qiT, G, ph, Fv);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
 }
 
 // ------------------------------------------------------------------------------------------
-// 4. Correction by the common flux, scaling, and output / RK44 stage update.
+// 4. Correction by the common flux, scaling, and output / RK44 stage update (FP64).
 // ------------------------------------------------------------------------------------------
-template <int N>
-__global__ void k_correct(const double *__restrict__ Rpart, const double *__restrict__ FI,
-                          const int32_t *__restrict__ ef, const double *__restrict__ metrics,
-                          int64_t E, int mode, int stage, double dt, double *__restrict__ Rout,
-                          double *__restrict__ Q, double *__restrict__ Un, double *__restrict__ acc,
-                          int *__restrict__ flag) {
+template <int N, typename T>
+__global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef,
+                          const T *__restrict__ metrics, int64_t E, int mode, int stage, double dt,
+                          double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
+                          double *__restrict__ Un, double *__restrict__ acc, int *__restrict__ flag) {
   constexpr int Np = N * N * N, Nf = N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * Np) return;
   const int64_t e = t / Np;
   const int m = (int)(t % Np), i = m % N, j = (m / N) % N, k = m / (N * N);
-  const DevBasis &B = c_basis[N - 1];
-  double r[5];
+  const BasisT<T> &B = cbasis<T>(N);
+  T r[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) r[v] = Rpart[t * 5 + v];
-  // Faces: (f, weight, local flux point (a, b)).
+  // Faces: (weight, local flux point (a, b)).
   const int fa[6] = {j, j, i, i, i, i};
   const int fb[6] = {k, k, k, k, j, j};
-  const double wts[6] = {B.hm[i], B.hp[i], B.hm[j], B.hp[j], B.hm[k], B.hp[k]};
+  const T wts[6] = {B.hm[i], B.hp[i], B.hm[j], B.hp[j], B.hm[k], B.hp[k]};
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const int packed = ef[e * 6 + f];
     const int64_t I = packed >> 4;
     const int side = (packed >> 3) & 1;
     const int slot = slot_of(packed & 7, fa[f], fb[f], N);
-    const double w = side ? -wts[f] : wts[f];
-    const double *src = FI + I * 5 * Nf + slot;
+    const T w = side ? -wts[f] : wts[f];
+    const T *src = FI + I * 5 * Nf + slot;
 #pragma unroll
     for (int v = 0; v < 5; ++v) r[v] += w * src[v * Nf];
   }
-  const double s = -metrics[(e * 10 + 9) * Np + m];
+  const T s = -metrics[(e * 10 + 9) * Np + m];
+  double rd[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) r[v] *= s;
+  for (int v = 0; v < 5; ++v) rd[v] = to_double(r[v] * s);
   if (mode == MODE_RESIDUAL) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = r[v];
+    for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];
     return;
   }
   const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -490,18 +558,27 @@ __global__ void k_correct(const double *__restrict__ Rpart, const double *__rest
   for (int v = 0; v < 5; ++v) {
     const int64_t o = t * 5 + v;
     const double un = Un[o];
+    double nv;
     if (stage < 3) {
-      const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * r[v];
+      const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
       acc[o] = a_;
-      Q[o] = un + anext[stage] * dt * r[v];
+      nv = un + anext[stage] * dt * rd[v];
+      Q[o] = nv;
     } else {
-      const double nv = un + acc[o] + bcoef[3] * dt * r[v];
+      nv = un + acc[o] + bcoef[3] * dt * rd[v];
       Un[o] = nv;
       Q[o] = nv;
       bad |= !isfinite(nv);
     }
+    if (Qc) Qc[o] = from_double<T>(nv);
   }
   if (bad) atomicOr(flag, 1);
+}
+
+// Copy of the FP64 state in the compute type (mixed path).
+__global__ void k_state_to_df(const double *__restrict__ Q, df32 *__restrict__ Qc, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) Qc[t] = df_from(Q[t]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -543,66 +620,82 @@ __global__ void k_min_reduce(const double *__restrict__ x, int64_t n, double *__
 #define FR_EV_END(k) \
   if (ev) cudaEventRecord(ev->stop[k], st)
 
-template <int N>
+template <int N, typename T>
 static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
                                  double *Rout, cudaStream_t st, const PhaseEvents *ev) {
   constexpr int Np = N * N * N, Nf = N * N;
   const int64_t E = m.E;
+  const T *Qin = reinterpret_cast<const T *>(m.mixed ? m.Qc : m.Q);
+  T *Qtr = reinterpret_cast<T *>(m.Qtr), *Gtr = reinterpret_cast<T *>(m.Gtr), *FI = reinterpret_cast<T *>(m.FI);
+  T *Rpart = reinterpret_cast<T *>(m.Rpart);
+  const T *met = reinterpret_cast<const T *>(m.metrics), *lift = reinterpret_cast<const T *>(m.liftfac);
+  const T *nrm = reinterpret_cast<const T *>(m.normals);
+  T *Qc = m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr;
   {
     const int64_t n = E * 6 * Nf;
     FR_EV_BEGIN(0);
-    k_interp_faces<N><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, m.ef, m.Qtr, E);
+    k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
     if (nb > 0)
-      k_bc_prepare<N><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(m.Qtr, m.normals, m.if_bc, m.bcs, m.n_interior,
-                                                                   m.n_if - m.n_interior, ph);
+      k_bc_prepare<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, nrm, m.if_bc, m.bcs, m.n_interior,
+                                                                      m.n_if - m.n_interior, ph);
     FR_EV_END(0);
   }
   {
-    const int threads = ((Np + 31) / 32) * 32;
-    const size_t smem = sizeof(double) * (35 * Np + 30 * Nf);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t err = cudaFuncSetAttribute(k_volume<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err != cudaSuccess) return err;
-      attr_set = true;
-    }
+    const int threads = volume_threads<N>();
+    const size_t smem = sizeof(T) * (35 * Np + 30 * Nf);
+    cudaError_t err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
-    k_volume<N><<<(unsigned)E, threads, smem, st>>>(m.Q, m.metrics, m.ef, m.Qtr, m.liftfac, m.Gtr, m.Rpart, ph);
+    k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph);
     FR_EV_END(1);
   }
   {
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
-    if (n > 0) k_iface_flux<N><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(m.Qtr, m.Gtr, m.normals, m.FI, m.n_interior, ph);
+    if (n > 0) k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph);
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
     if (nb > 0)
-      k_bc_flux<N><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(m.Qtr, m.Gtr, m.normals, m.if_bc, m.bcs, m.FI,
-                                                                m.n_interior, m.n_if - m.n_interior, ph);
+      k_bc_flux<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, m.if_bc, m.bcs, FI, m.n_interior,
+                                                                   m.n_if - m.n_interior, ph);
     FR_EV_END(2);
   }
   {
     const int64_t n = E * Np;
     FR_EV_BEGIN(3);
-    k_correct<N><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Rpart, m.FI, m.ef, m.metrics, E, mode, stage, dt,
-                                                              Rout, m.Q, m.Un, m.acc, m.flag);
+    k_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Rpart, FI, m.ef, met, E, mode, stage, dt, Rout, m.Q,
+                                                                 Qc, m.Un, m.acc, m.flag);
     FR_EV_END(3);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt, double *Rout,
-                            cudaStream_t st, const PhaseEvents *ev) {
+template <typename T>
+static cudaError_t dispatch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
+                                     double *Rout, cudaStream_t st, const PhaseEvents *ev) {
   switch (m.N) {
-    case 2: return residual_impl<2>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 3: return residual_impl<3>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 4: return residual_impl<4>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 5: return residual_impl<5>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 6: return residual_impl<6>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 7: return residual_impl<7>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 8: return residual_impl<8>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 2: return residual_impl<2, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 3: return residual_impl<3, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 4: return residual_impl<4, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 5: return residual_impl<5, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 6: return residual_impl<6, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 7: return residual_impl<7, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 8: return residual_impl<8, T>(m, ph, mode, stage, dt, Rout, st, ev);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt, double *Rout,
+                            cudaStream_t st, const PhaseEvents *ev) {
+  if (m.mixed) return dispatch_residual<df32>(m, ph, mode, stage, dt, Rout, st, ev);
+  return dispatch_residual<double>(m, ph, mode, stage, dt, Rout, st, ev);
+}
+
+cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st) {
+  if (!m.mixed) return cudaSuccess;
+  const int64_t n = m.E * m.Np * 5;
+  k_state_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, reinterpret_cast<df32 *>(m.Qc), n);
+  return cudaGetLastError();
 }
 
 template <int N>
