@@ -144,7 +144,10 @@ fr_status fr_residual(fr_mesh *mesh, double t, double *R, int32_t where);
  * residual of the current stage state at time t + c_k dt and updates, in FP64,
  *   acc += b_k dt R,  U = U_n + a_{k+1} dt R       (k < 3)
  *   U_n = U_n + acc + b_3 dt R,  U = U_n           (k = 3)
- * with a = (1/2, 1/2, 1), b = (1/6, 1/3, 1/3, 1/6).  Stages must be called in order 0,1,2,3;
+ * with a = (1/2, 1/2, 1), b = (1/6, 1/3, 1/3, 1/6).  acc and U_n are FP64 in both precisions;
+ * with FR_PREC_MIXED the intermediate stage state U is held only as double-float for the element
+ * kernels, so fr_get_state between stages returns U_n (the state of the last completed step).
+ * Stages must be called in order 0,1,2,3;
  * `t` is the time at the start of the step.  Returns FR_ENONFINITE (checked at stage 3 only) if
  * a non-finite value was written.
  */

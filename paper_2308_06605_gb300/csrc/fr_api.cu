@@ -86,7 +86,7 @@ static fr_status check_mesh(fr_mesh *m) {
 
 static void release(fr_mesh *m) {
   DevMesh &d = m->dev;
-  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf, d.Qc};
+  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf, d.Qc, d.Unc};
   for (double *p : dbl)
     if (p) cudaFree(p);
   if (d.ef) cudaFree(d.ef);
@@ -218,7 +218,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
       (st = dalloc(m, &d.h, (size_t)h.E)) || (st = dalloc(m, &d.dtbuf, (size_t)h.E + 1)) ||
       (st = dalloc(m, &d.ef, h.ef.size())) || (st = dalloc(m, &d.if_bc, h.if_bc.size())) ||
       (st = dalloc(m, &d.bcs, h.bcs.size())) || (st = dalloc(m, &d.flag, 1)) ||
-      (d.mixed && (st = dalloc(m, &d.Qc, nsol))))
+      (d.mixed && ((st = dalloc(m, &d.Qc, nsol)) || (st = dalloc(m, &d.Unc, nsol)))))
     return bail(st);
   if (d.mixed) {
     // Geometry in the element arithmetic's format: each double becomes a df32 (hi, lo) pair

@@ -31,7 +31,7 @@ struct DevMesh {
   int p, N, Np, Nf;
   int64_t E, n_if, n_interior;
   int mixed;        // 1: element arrays hold df32 pairs (same 8-byte slots), Qc holds the state as df32
-  double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc;
+  double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc, *Unc;
   int32_t *ef, *if_bc;
   fr_bc *bcs;
   int *flag;

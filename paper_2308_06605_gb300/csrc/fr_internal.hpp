@@ -32,7 +32,7 @@ struct HostMesh {
   std::vector<int32_t> if_bc;     // [n_if] -1 two-sided, else index into bcs
   std::vector<double> metrics;    // [E][10][Np]: S (row-major d, j) then 1/|J|
   std::vector<double> liftfac;    // [E][6][3][Nf]
-  std::vector<double> normals;    // [n_if][3][Nf] outward area-scaled normal of side 0
+  std::vector<double> normals;    // [n_if][4][Nf] outward area-scaled normal of side 0, then |n|
   std::vector<double> xsol;       // [E][Np][3]
   std::vector<double> h;          // [E] volume^(1/3)
   std::vector<fr_bc> bcs;

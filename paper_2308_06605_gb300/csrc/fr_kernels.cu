@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "df32.cuh"
 #include "fr_device.hpp"
@@ -101,8 +102,8 @@ __device__ __forceinline__ int slot_of(int code, int a, int b, int N) {
 // ------------------------------------------------------------------------------------------
 // Gas dynamics (ideal gas, Stokes hypothesis, constant mu, Fourier heat flux).
 // ------------------------------------------------------------------------------------------
-// Normal inviscid flux F(q).n and (|u.n^| + c)|n|, in FP64 (pressure/energy recovery).
-__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double g,
+// Normal inviscid flux F(q).n and (|u.n^| + c)|n|, in FP64 (pressure/energy recovery); nn = |n|.
+__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, double g,
                                                 double out[5], double &un_abs_plus_c_n) {
   const double ri = 1.0 / q[0];
   const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
@@ -113,8 +114,40 @@ __device__ __forceinline__ void normal_inviscid(const double q[5], const double 
   out[2] = q[2] * un + p * n[1];
   out[3] = q[3] * un + p * n[2];
   out[4] = (q[4] + p) * un;
-  const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   un_abs_plus_c_n = fabs(un) + sqrt(g * p * ri) * nn;      // (|u.n^| + c) |n|
+}
+
+// Double-float normal flux with the pressure recovery p = (gamma-1)(E - m.u/2) in FP64.
+__device__ __forceinline__ void normal_inviscid(const df32 q[5], const df32 n[3], df32 nn, const DevPhys &dph,
+                                                df32 out[5], df32 &un_abs_plus_c_n) {
+  const PhysT<df32> &ph = dph.f;
+  const df32 ri = ph.one / q[0];
+  const df32 u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  Dot<df32> mu, unn;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mu.add(q[1 + c], u[c]);
+    unn.add(u[c], n[c]);
+  }
+  const double pd = (dph.gamma - 1.0) * (to_double(q[4]) - 0.5 * to_double(mu.get()));
+  const df32 p = df_from(pd);
+  const df32 un = unn.get();
+  out[0] = q[0] * un;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Dot<df32> f;
+    f.add(q[1 + c], un);
+    f.add(p, n[c]);
+    out[1 + c] = f.get();
+  }
+  out[4] = (q[4] + p) * un;
+  un_abs_plus_c_n = fabs(un) + sqrt(ph.gamma * p * ri) * nn;
+}
+
+// FP64 overload with the same signature shape (the FP64 path's arithmetic).
+__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, const DevPhys &dph,
+                                                double out[5], double &s) {
+  normal_inviscid(q, n, nn, dph.gamma, out, s);
 }
 
 // Viscous flux F_v[j][v] (j = direction) of state q with gradient G[j*5 + v] = dQ_v/dx_j.
@@ -167,15 +200,13 @@ __global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restric
   int base, sd;
   face_line<N>(f, r, base, sd);
   const T *q = Q + e * Np * 5;
-  T acc[5];
+  Dot<T> acc[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) acc[v] = l[0] * q[base * 5 + v];
-#pragma unroll
-  for (int c = 1; c < N; ++c) {
+  for (int c = 0; c < N; ++c) {
     const T lc = l[c];
     const T *qc = q + (base + c * sd) * 5;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] += lc * qc[v];
+    for (int v = 0; v < 5; ++v) acc[v].add(lc, qc[v]);
   }
   const int packed = ef[eff];
   const int64_t I = packed >> 4;
@@ -183,7 +214,7 @@ __global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restric
   const int slot = slot_of(packed & 7, r % N, r / N, N);
   T *dst = Qtr + (I * 2 + side) * 5 * Nf + slot;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v];
+  for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v].get();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -191,9 +222,12 @@ __global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restric
 // ------------------------------------------------------------------------------------------
 template <int N>
 constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
+// Resident blocks the register budget must allow (smem allows at least this many).
+template <int N>
+constexpr int volume_min_blocks() { return volume_threads<N>() <= 128 ? 3 : (volume_threads<N>() <= 256 ? 2 : 1); }
 
 template <int N, typename T>
-__global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restrict__ Q, const T *__restrict__ metrics,
+__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k_volume(const T *__restrict__ Q, const T *__restrict__ metrics,
                          const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
                          const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
                          DevPhys dph) {
@@ -252,24 +286,29 @@ __global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restr
     }
     if (viscous) {
       T gu[3][5], gc[3][5];
+      const T nhm[3] = {-B.hm[i], -B.hm[j], -B.hm[k]};
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const T *sq = sQ + v * Np;
-        T a0 = B.D[i * N] * sq[N * j + N * N * k];
-        T a1 = B.D[j * N] * sq[i + N * N * k];
-        T a2 = B.D[k * N] * sq[i + N * j];
+        Dot<T> a0, a1, a2;
 #pragma unroll
-        for (int a = 1; a < N; ++a) {
-          a0 += B.D[i * N + a] * sq[a + N * j + N * N * k];
-          a1 += B.D[j * N + a] * sq[i + N * a + N * N * k];
-          a2 += B.D[k * N + a] * sq[i + N * j + N * N * a];
+        for (int a = 0; a < N; ++a) {
+          a0.add(B.D[i * N + a], sq[a + N * j + N * N * k]);
+          a1.add(B.D[j * N + a], sq[i + N * a + N * N * k]);
+          a2.add(B.D[k * N + a], sq[i + N * j + N * N * a]);
         }
-        gu[0][v] = a0;
-        gu[1][v] = a1;
-        gu[2][v] = a2;
-        gc[0][v] = a0 - B.hm[i] * sdQ[(0 * 5 + v) * Nf + j + N * k] + B.hp[i] * sdQ[(1 * 5 + v) * Nf + j + N * k];
-        gc[1][v] = a1 - B.hm[j] * sdQ[(2 * 5 + v) * Nf + i + N * k] + B.hp[j] * sdQ[(3 * 5 + v) * Nf + i + N * k];
-        gc[2][v] = a2 - B.hm[k] * sdQ[(4 * 5 + v) * Nf + i + N * j] + B.hp[k] * sdQ[(5 * 5 + v) * Nf + i + N * j];
+        gu[0][v] = a0.get();
+        gu[1][v] = a1.get();
+        gu[2][v] = a2.get();
+        a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
+        a0.add(B.hp[i], sdQ[(1 * 5 + v) * Nf + j + N * k]);
+        a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
+        a1.add(B.hp[j], sdQ[(3 * 5 + v) * Nf + i + N * k]);
+        a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
+        a2.add(B.hp[k], sdQ[(5 * 5 + v) * Nf + i + N * j]);
+        gc[0][v] = a0.get();
+        gc[1][v] = a1.get();
+        gc[2][v] = a2.get();
       }
       T G[15];
 #pragma unroll
@@ -277,8 +316,15 @@ __global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restr
         const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          sG[(jj * 5 + v) * Np + m] = s0 * gu[0][v] + s1 * gu[1][v] + s2 * gu[2][v];
-          G[jj * 5 + v] = s0 * gc[0][v] + s1 * gc[1][v] + s2 * gc[2][v];
+          Dot<T> du, dc;
+          du.add(s0, gu[0][v]);
+          du.add(s1, gu[1][v]);
+          du.add(s2, gu[2][v]);
+          dc.add(s0, gc[0][v]);
+          dc.add(s1, gc[1][v]);
+          dc.add(s2, gc[2][v]);
+          sG[(jj * 5 + v) * Np + m] = du.get();
+          G[jj * 5 + v] = dc.get();
         }
       }
       T Fv[3][5];
@@ -291,8 +337,13 @@ __global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restr
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int v = 0; v < 5; ++v)
-        sH[(d * 5 + v) * Np + m] = S[d * 3 + 0] * H[0][v] + S[d * 3 + 1] * H[1][v] + S[d * 3 + 2] * H[2][v];
+      for (int v = 0; v < 5; ++v) {
+        Dot<T> h;
+        h.add(S[d * 3 + 0], H[0][v]);
+        h.add(S[d * 3 + 1], H[1][v]);
+        h.add(S[d * 3 + 2], H[2][v]);
+        sH[(d * 5 + v) * Np + m] = h.get();
+      }
   }
   __syncthreads();
   if (viscous) {
@@ -314,10 +365,11 @@ __global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restr
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const T *sg = sG + (jj * 5 + v) * Np + base;
-          T acc = l[0] * sg[0];
+          Dot<T> acc;
 #pragma unroll
-          for (int c = 1; c < N; ++c) acc += l[c] * sg[c * sd];
-          dst[(jj * 5 + v) * Nf] = acc + lj * sdQ[(f * 5 + v) * Nf + r];
+          for (int c = 0; c < N; ++c) acc.add(l[c], sg[c * sd]);
+          acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
+          dst[(jj * 5 + v) * Nf] = acc.get();
         }
       }
     }
@@ -328,16 +380,14 @@ __global__ void __launch_bounds__(volume_threads<N>()) k_volume(const T *__restr
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const T *h0 = sH + (0 * 5 + v) * Np, *h1 = sH + (1 * 5 + v) * Np, *h2 = sH + (2 * 5 + v) * Np;
-      T acc = B.Dt[i * N] * h0[N * j + N * N * k];
-      acc += B.Dt[j * N] * h1[i + N * N * k];
-      acc += B.Dt[k * N] * h2[i + N * j];
+      Dot<T> acc;
 #pragma unroll
-      for (int a = 1; a < N; ++a) {
-        acc += B.Dt[i * N + a] * h0[a + N * j + N * N * k];
-        acc += B.Dt[j * N + a] * h1[i + N * a + N * N * k];
-        acc += B.Dt[k * N + a] * h2[i + N * j + N * N * a];
+      for (int a = 0; a < N; ++a) {
+        acc.add(B.Dt[i * N + a], h0[a + N * j + N * N * k]);
+        acc.add(B.Dt[j * N + a], h1[i + N * a + N * N * k]);
+        acc.add(B.Dt[k * N + a], h2[i + N * j + N * N * a]);
       }
-      out[v] = acc;
+      out[v] = acc.get();
     }
   }
 }
@@ -354,29 +404,24 @@ __global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gt
   if (t >= n_if * Nf) return;
   const int64_t I = t / Nf;
   const int q = (int)(t % Nf);
+  const PhysT<T> &ph = phys_of<T>(dph);
   T qL[5], qR[5], nT[3];
-  double qLd[5], qRd[5], n[3];
+  const T nn = normals[(I * 4 + 3) * Nf + q];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qL[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
     qR[v] = Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q];
-    qLd[v] = to_double(qL[v]);
-    qRd[v] = to_double(qR[v]);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    nT[c] = normals[(I * 3 + c) * Nf + q];
-    n[c] = to_double(nT[c]);
-  }
-  double fL[5], fR[5], sL, sR;
-  normal_inviscid(qLd, n, dph.gamma, fL, sL);
-  normal_inviscid(qRd, n, dph.gamma, fR, sR);
-  const double lam = fmax(sL, sR);
+  for (int c = 0; c < 3; ++c) nT[c] = normals[(I * 4 + c) * Nf + q];
+  T fL[5], fR[5], sL, sR;
+  normal_inviscid(qL, nT, nn, dph, fL, sL);
+  normal_inviscid(qR, nT, nn, dph, fR, sR);
+  const T hl = ph.half * fmax(sL, sR);
   T F[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (qRd[v] - qLd[v]));
+  for (int v = 0; v < 5; ++v) F[v] = ph.half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
   if (dph.viscous) {
-    const PhysT<T> &ph = phys_of<T>(dph);
     T qc[5], G[15];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qc[v] = ph.half * (qL[v] + qR[v]);
@@ -398,8 +443,8 @@ __global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gt
 // Boundary states are FP64 in both paths.
 // ------------------------------------------------------------------------------------------
 // Ghost state (for the Rusanov flux) and boundary common solution Q^I from the interior trace.
-__device__ void boundary_states(const double qm[5], const double n[3], const fr_bc &bc, const DevPhys &ph,
-                                double ghost[5], double qi[5]) {
+__device__ void boundary_states(const double qm[5], const double n[3], double nn, const fr_bc &bc,
+                                const DevPhys &ph, double ghost[5], double qi[5]) {
   const double g = ph.gamma, Rg = ph.R;
   const double ri = 1.0 / qm[0];
   const double u[3] = {qm[1] * ri, qm[2] * ri, qm[3] * ri};
@@ -414,7 +459,6 @@ __device__ void boundary_states(const double qm[5], const double n[3], const fr_
     qi[4] = qm[0] * Rg * bc.params[0] / (g - 1.0);
     return;
   }
-  const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   const double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
   const double un = u[0] * nh[0] + u[1] * nh[1] + u[2] * nh[2];
   const double c = sqrt(g * p * ri);
@@ -462,8 +506,8 @@ __global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
 #pragma unroll
   for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) n[c] = to_double(normals[(I * 3 + c) * Nf + q]);
-  boundary_states(qm, n, bcs[if_bc[I]], ph, gh, qi);
+  for (int c = 0; c < 3; ++c) n[c] = to_double(normals[(I * 4 + c) * Nf + q]);
+  boundary_states(qm, n, to_double(normals[(I * 4 + 3) * Nf + q]), bcs[if_bc[I]], ph, gh, qi);
 #pragma unroll
   for (int v = 0; v < 5; ++v) Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q] = from_double<T>(2.0 * qi[v] - qm[v]);
 }
@@ -483,13 +527,14 @@ __global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, 
   for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    nT[c] = normals[(I * 3 + c) * Nf + q];
+    nT[c] = normals[(I * 4 + c) * Nf + q];
     n[c] = to_double(nT[c]);
   }
-  boundary_states(qm, n, bcs[if_bc[I]], dph, gh, qi);
+  const double nn = to_double(normals[(I * 4 + 3) * Nf + q]);
+  boundary_states(qm, n, nn, bcs[if_bc[I]], dph, gh, qi);
   double fL[5], fR[5], sL, sR;
-  normal_inviscid(qm, n, dph.gamma, fL, sL);
-  normal_inviscid(gh, n, dph.gamma, fR, sR);
+  normal_inviscid(qm, n, nn, dph.gamma, fL, sL);
+  normal_inviscid(gh, n, nn, dph.gamma, fR, sR);
   const double lam = fmax(sL, sR);
   T F[5];
 #pragma unroll
@@ -517,16 +562,18 @@ template <int N, typename T>
 __global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef,
                           const T *__restrict__ metrics, int64_t E, int mode, int stage, double dt,
                           double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
-                          double *__restrict__ Un, double *__restrict__ acc, int *__restrict__ flag) {
+                          double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
+                          int *__restrict__ flag, DevPhys dph) {
   constexpr int Np = N * N * N, Nf = N * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * Np) return;
   const int64_t e = t / Np;
   const int m = (int)(t % Np), i = m % N, j = (m / N) % N, k = m / (N * N);
   const BasisT<T> &B = cbasis<T>(N);
-  T r[5];
+  const PhysT<T> &ph = phys_of<T>(dph);
+  Dot<T> r[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) r[v] = Rpart[t * 5 + v];
+  for (int v = 0; v < 5; ++v) r[v].add(ph.one, Rpart[t * 5 + v]);
   // Faces: (weight, local flux point (a, b)).
   const int fa[6] = {j, j, i, i, i, i};
   const int fb[6] = {k, k, k, k, j, j};
@@ -540,12 +587,12 @@ __global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI,
     const T w = side ? -wts[f] : wts[f];
     const T *src = FI + I * 5 * Nf + slot;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) r[v] += w * src[v * Nf];
+    for (int v = 0; v < 5; ++v) r[v].add(w, src[v * Nf]);
   }
   const T s = -metrics[(e * 10 + 9) * Np + m];
   double rd[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) rd[v] = to_double(r[v] * s);
+  for (int v = 0; v < 5; ++v) rd[v] = to_double(r[v].get() * s);
   if (mode == MODE_RESIDUAL) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];
@@ -554,31 +601,51 @@ __global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI,
   const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double anext[3] = {0.5, 0.5, 1.0};
   bool bad = false;
+  if constexpr (std::is_same<T, df32>::value) {
+    // Mixed path: acc and U_n are FP64; the next stage state, read only by the element
+    // kernels, is formed in double-float from the df32 copy of U_n.
+    const T adt = from_double<T>(stage < 3 ? anext[stage] * dt : 0.0);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const int64_t o = t * 5 + v;
-    const double un = Un[o];
-    double nv;
-    if (stage < 3) {
-      const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
-      acc[o] = a_;
-      nv = un + anext[stage] * dt * rd[v];
-      Q[o] = nv;
-    } else {
-      nv = un + acc[o] + bcoef[3] * dt * rd[v];
-      Un[o] = nv;
-      Q[o] = nv;
-      bad |= !isfinite(nv);
+    for (int v = 0; v < 5; ++v) {
+      const int64_t o = t * 5 + v;
+      if (stage < 3) {
+        acc[o] = fma(bcoef[stage] * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
+        Qc[o] = Unc[o] + adt * (r[v].get() * s);
+      } else {
+        const double nv = fma(bcoef[3] * dt, rd[v], Un[o] + acc[o]);
+        Un[o] = nv;
+        Q[o] = nv;
+        const T nc = from_double<T>(nv);
+        Unc[o] = nc;
+        Qc[o] = nc;
+        bad |= !isfinite(nv);
+      }
     }
-    if (Qc) Qc[o] = from_double<T>(nv);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t o = t * 5 + v;
+      const double un = Un[o];
+      if (stage < 3) {
+        const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
+        acc[o] = a_;
+        Q[o] = un + anext[stage] * dt * rd[v];
+      } else {
+        const double nv = un + acc[o] + bcoef[3] * dt * rd[v];
+        Un[o] = nv;
+        Q[o] = nv;
+        bad |= !isfinite(nv);
+      }
+    }
   }
   if (bad) atomicOr(flag, 1);
 }
 
-// Copy of the FP64 state in the compute type (mixed path).
-__global__ void k_state_to_df(const double *__restrict__ Q, df32 *__restrict__ Qc, int64_t n) {
+// Copies of the FP64 state in the compute type (mixed path): the stage state and U_n.
+__global__ void k_state_to_df(const double *__restrict__ Q, df32 *__restrict__ Qc, df32 *__restrict__ Unc,
+                              int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) Qc[t] = df_from(Q[t]);
+  if (t < n) Qc[t] = Unc[t] = df_from(Q[t]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -664,7 +731,8 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     const int64_t n = E * Np;
     FR_EV_BEGIN(3);
     k_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Rpart, FI, m.ef, met, E, mode, stage, dt, Rout, m.Q,
-                                                                 Qc, m.Un, m.acc, m.flag);
+                                                                 Qc, m.Un, reinterpret_cast<T *>(m.Unc), m.acc,
+                                                                 m.flag, ph);
     FR_EV_END(3);
   }
   return cudaGetLastError();
@@ -694,7 +762,8 @@ cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int s
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st) {
   if (!m.mixed) return cudaSuccess;
   const int64_t n = m.E * m.Np * 5;
-  k_state_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, reinterpret_cast<df32 *>(m.Qc), n);
+  k_state_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, reinterpret_cast<df32 *>(m.Qc),
+                                                             reinterpret_cast<df32 *>(m.Unc), n);
   return cudaGetLastError();
 }
 

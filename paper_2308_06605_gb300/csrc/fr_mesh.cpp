@@ -439,7 +439,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   Basis1D b = make_basis(p);
   m.metrics.assign((size_t)E * 10 * Np, 0.0);
   m.liftfac.assign((size_t)E * 6 * 3 * Nf, 0.0);
-  m.normals.assign((size_t)m.n_if * 3 * Nf, 0.0);
+  m.normals.assign((size_t)m.n_if * 4 * Nf, 0.0);
   m.xsol.assign((size_t)E * Np * 3, 0.0);
   m.h.assign(E, 0.0);
   std::vector<double> fx((size_t)E * 6 * Nf * 3);     // flux-point coordinates for the match check
@@ -495,8 +495,14 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
           double S[3][3], det;
           adjugate_rows(g.J, S, det);
           for (int c = 0; c < 3; ++c) fx[(((size_t)e * 6 + f) * Nf + r) * 3 + c] = g.x[c];
-          if (side == 0)
-            for (int jj = 0; jj < 3; ++jj) m.normals[((size_t)I * 3 + jj) * Nf + r] = s * S[d][jj];
+          if (side == 0) {
+            double nn = 0.0;
+            for (int jj = 0; jj < 3; ++jj) {
+              m.normals[((size_t)I * 4 + jj) * Nf + r] = s * S[d][jj];
+              nn += S[d][jj] * S[d][jj];
+            }
+            m.normals[((size_t)I * 4 + 3) * Nf + r] = std::sqrt(nn);
+          }
         }
     }
   }
