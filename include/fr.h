@@ -183,6 +183,37 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
 fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
 
 /*
+ * Batched stages for ensembles of independent cases (the paper runs one mesh per MPI
+ * decomposition; on one GPU an ensemble of unevenly sized cases, with different orders, is
+ * advanced together).  fr_batch_create borrows the meshes (they must outlive the batch, share
+ * precision, device and stream).  fr_batch_rk_stage runs stage `stage` (RK44, same update as
+ * fr_rk_stage) of every case in ONE cooperative persistent kernel: phases (face interpolation,
+ * boundary states, volume, interface fluxes, correction + update) are separated by grid
+ * barriers whose waits are bounded; if a wait gives up, the call returns FR_ETIMEOUT and the
+ * batch and its meshes are poisoned.  On a non-default stream each stage is captured once into
+ * a CUDA graph and replayed.  Errors (timeout, non-finite values) are read back at stage 3.
+ * fr_batch_set_dt sets each case's step size (host array, one per case).  fr_batch_tune times
+ * the kernel's block size (256/512 threads, which fixes the elements-per-block tile of every
+ * order) and resident blocks per SM on this batch, keeps the fastest, and restores every case to
+ * its U_n.  fr_batch_debug (tests only) makes block `skip_block` leave before its first barrier,
+ * with a barrier wait limit of `spin_limit` iterations, to exercise the timeout path.
+ */
+typedef struct fr_batch fr_batch;
+typedef struct {
+  int32_t n_cases, block, grid, blocks_per_sm;
+  int64_t n_points, smem_bytes;
+  int32_t n_tasks;
+} fr_batch_info;
+fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch **out);
+fr_status fr_batch_set_dt(fr_batch *batch, const double *dt_host);
+fr_status fr_batch_rk_stage(fr_batch *batch, int32_t stage, double t);
+fr_status fr_batch_tune(fr_batch *batch);
+fr_status fr_batch_query(const fr_batch *batch, fr_batch_info *info);
+fr_status fr_batch_debug(fr_batch *batch, int32_t skip_block, int64_t spin_limit);
+void fr_batch_free(fr_batch *batch);
+const char *fr_batch_last_error(const fr_batch *batch);
+
+/*
  * Instrumentation (not part of the method).  fr_profile(mesh, 1) makes every later residual
  * evaluation record CUDA events around each of its kernels on the mesh's stream;
  * fr_profile_read accumulates, per kernel k < n, the summed device time in milliseconds

@@ -49,6 +49,54 @@ cudaError_t upload_basis_tables();
 // MODE_RK applies RK44 stage `stage` with step dt.
 cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
                             double *Rout, cudaStream_t st, const PhaseEvents *ev = nullptr);
+// ---------------------------------------------------------------- batched persistent stage
+// One case of a batch: its device view, physics and precision (all cases share the precision).
+struct BatchCase {
+  DevMesh m;
+  DevPhys ph;
+};
+
+// Work item of a phase: case `cs`, kind, and an item range [begin, end) -- flux/solution
+// points for the pointwise kinds, elements for the volume kind.
+enum { TASK_INTERP = 0, TASK_BC_PREPARE = 1, TASK_VOLUME = 2, TASK_IFACE = 3, TASK_BC_FLUX = 4, TASK_CORRECT = 5 };
+struct BatchTask {
+  int32_t cs, kind;
+  int64_t begin, end;
+};
+
+// Device state of one stage launch: task counters per phase, grid-barrier count/generation,
+// error word (1 = a barrier wait gave up), non-finite flag.
+struct BatchSync {
+  unsigned counters[8];
+  unsigned bar_count, bar_gen;
+  int err;
+  int nonfinite;
+};
+
+struct BatchLaunch {
+  const BatchCase *cases;
+  const BatchTask *tasks;
+  int phase_begin[6];    // tasks of phase k are [phase_begin[k], phase_begin[k+1])
+  int n_phases;
+  int stage;
+  const double *dts;     // [n_cases] device
+  BatchSync *sync;
+  long long spin_limit;  // iterations of a barrier wait before giving up
+  int debug_skip_block;  // >= 0: that block leaves before the first barrier (timeout test)
+};
+
+// Launch one cooperative persistent stage over all cases (block size 256 or 512).
+cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st);
+// Largest dynamic shared memory one block needs for the given orders and block size.
+size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed);
+// Resident blocks per SM of the batch kernel for the given configuration.
+cudaError_t batch_occupancy(int mixed, int block, size_t smem, int *blocks_per_sm);
+// Elements a block of `block` threads processes at once in the volume phase for order N.
+inline int batch_elems_per_block(int N, int block) {
+  const int tpe = ((N * N * N + 31) / 32) * 32;
+  return tpe >= block ? 1 : block / tpe;
+}
+
 // Accessors of the opaque mesh (fr_api.cu): a copy of its device view (fails if poisoned), and
 // recording an error on it.
 fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device);

@@ -186,10 +186,9 @@ __device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const Phy
 // 1. Solution traces.  Thread per (element, face, flux point).
 // ------------------------------------------------------------------------------------------
 template <int N, typename T>
-__global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restrict__ ef,
-                               T *__restrict__ Qtr, int64_t E) {
+__device__ __forceinline__ void interp_body(int64_t t, const T *__restrict__ Q, const int32_t *__restrict__ ef,
+                                            T *__restrict__ Qtr, int64_t E) {
   constexpr int Np = N * N * N, Nf = N * N;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * 6 * Nf) return;
   const int r = (int)(t % Nf);
   const int64_t eff = t / Nf;
@@ -217,6 +216,12 @@ __global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restric
   for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v].get();
 }
 
+template <int N, typename T>
+__global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restrict__ ef,
+                               T *__restrict__ Qtr, int64_t E) {
+  interp_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Q, ef, Qtr, E);
+}
+
 // ------------------------------------------------------------------------------------------
 // 2. Volume kernel.  One block per element, one thread per solution point.
 // ------------------------------------------------------------------------------------------
@@ -226,26 +231,32 @@ constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
 template <int N>
 constexpr int volume_min_blocks() { return volume_threads<N>() <= 128 ? 3 : (volume_threads<N>() <= 256 ? 2 : 1); }
 
+// Shared-memory values (of T) one element needs in the volume kernel.
+template <int N>
+__host__ __device__ constexpr int volume_smem_values() { return 35 * N * N * N + 30 * N * N; }
+
+// One element e handled by `nth` threads of the block (thread index tid in [0, nth)); every
+// thread of the block calls this together (it contains block barriers); inactive sub-blocks
+// (active = false) only take part in the barriers.
 template <int N, typename T>
-__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k_volume(const T *__restrict__ Q, const T *__restrict__ metrics,
-                         const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
-                         const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
-                         DevPhys dph) {
+__device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool active, double *sm_raw,
+                                            const T *__restrict__ Q, const T *__restrict__ metrics,
+                                            const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
+                                            const T *__restrict__ liftfac, T *__restrict__ Gtr,
+                                            T *__restrict__ Rpart, const DevPhys &dph) {
   constexpr int Np = N * N * N, Nf = N * N;
-  extern __shared__ double sm_raw[];
   T *sm = reinterpret_cast<T *>(sm_raw);
   T *sQ = sm;                 // [5][Np]
   T *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
   T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
   T *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
   const PhysT<T> &ph = phys_of<T>(dph);
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x;
   const BasisT<T> &B = cbasis<T>(N);
   const bool viscous = dph.viscous != 0;
-  for (int t = tid; t < 5 * Np; t += blockDim.x) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
-  if (viscous) {
-    for (int t = tid; t < 6 * Nf; t += blockDim.x) {
+  if (active)
+    for (int t = tid; t < 5 * Np; t += nth) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
+  if (viscous && active) {
+    for (int t = tid; t < 6 * Nf; t += nth) {
       const int f = t / Nf, r = t % Nf;
       const int packed = ef[e * 6 + f];
       const int64_t I = packed >> 4;
@@ -258,7 +269,7 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k
     }
   }
   __syncthreads();
-  if (tid < Np) {
+  if (active && tid < Np) {
     const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
     T S[9];
     const T *met = metrics + e * 10 * Np + m;
@@ -346,9 +357,9 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k
       }
   }
   __syncthreads();
-  if (viscous) {
+  if (viscous && active) {
     // Gradient traces: uncorrected gradient interpolated to the face + eta * own lifting.
-    for (int t = tid; t < 6 * Nf; t += blockDim.x) {
+    for (int t = tid; t < 6 * Nf; t += nth) {
       const int f = t / Nf, r = t % Nf;
       const T *l = (f & 1) ? B.lp : B.lm;
       int base, sd;
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k
       }
     }
   }
-  if (tid < Np) {
+  if (active && tid < Np) {
     const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
     T *out = Rpart + (e * Np + m) * 5;
 #pragma unroll
@@ -392,15 +403,25 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>()) k
   }
 }
 
+template <int N, typename T>
+__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
+    k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
+             const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
+             DevPhys dph) {
+  extern __shared__ double sm_raw[];
+  volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr, Rpart,
+                    dph);
+}
+
 // ------------------------------------------------------------------------------------------
 // 3. Common normal flux at the flux points of two-sided interfaces (Rusanov + BR2).  The
 // inviscid part (pressure/energy recovery) is FP64 in both paths.
 // ------------------------------------------------------------------------------------------
 template <int N, typename T>
-__global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
-                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph) {
+__device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
+                                           const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if,
+                                           const DevPhys &dph) {
   constexpr int Nf = N * N;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_if * Nf) return;
   const int64_t I = t / Nf;
   const int q = (int)(t % Nf);
@@ -435,6 +456,12 @@ __global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gt
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
+}
+
+template <int N, typename T>
+__global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
+                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph) {
+  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -494,11 +521,10 @@ __device__ void boundary_states(const double qm[5], const double n[3], double nn
 }
 
 template <int N, typename T>
-__global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
-                             const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
-                             int64_t first, int64_t count, DevPhys ph) {
+__device__ __forceinline__ void bc_prepare_body(int64_t t, T *__restrict__ Qtr, const T *__restrict__ normals,
+                                                const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
+                                                int64_t first, int64_t count, const DevPhys &ph) {
   constexpr int Nf = N * N;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count * Nf) return;
   const int64_t I = first + t / Nf;
   const int q = (int)(t % Nf);
@@ -513,11 +539,18 @@ __global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
 }
 
 template <int N, typename T>
-__global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
-                          const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs, T *__restrict__ FI,
-                          int64_t first, int64_t count, DevPhys dph) {
+__global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
+                             const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
+                             int64_t first, int64_t count, DevPhys ph) {
+  bc_prepare_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, normals, if_bc, bcs, first, count, ph);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
+                                             const T *__restrict__ normals, const int32_t *__restrict__ if_bc,
+                                             const fr_bc *__restrict__ bcs, T *__restrict__ FI, int64_t first,
+                                             int64_t count, const DevPhys &dph) {
   constexpr int Nf = N * N;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count * Nf) return;
   const int64_t I = first + t / Nf;
   const int q = (int)(t % Nf);
@@ -555,17 +588,25 @@ __global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, 
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
 }
 
+template <int N, typename T>
+__global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
+                          const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs, T *__restrict__ FI,
+                          int64_t first, int64_t count, DevPhys dph) {
+  bc_flux_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, if_bc, bcs, FI, first, count,
+                     dph);
+}
+
 // ------------------------------------------------------------------------------------------
 // 4. Correction by the common flux, scaling, and output / RK44 stage update (FP64).
 // ------------------------------------------------------------------------------------------
 template <int N, typename T>
-__global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef,
-                          const T *__restrict__ metrics, int64_t E, int mode, int stage, double dt,
-                          double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
-                          double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
-                          int *__restrict__ flag, DevPhys dph) {
+__device__ __forceinline__ void correct_body(int64_t t, const T *__restrict__ Rpart, const T *__restrict__ FI,
+                                             const int32_t *__restrict__ ef, const T *__restrict__ metrics,
+                                             int64_t E, int mode, int stage, double dt, double *__restrict__ Rout,
+                                             double *__restrict__ Q, T *__restrict__ Qc, double *__restrict__ Un,
+                                             T *__restrict__ Unc, double *__restrict__ acc, int *__restrict__ flag,
+                                             const DevPhys &dph) {
   constexpr int Np = N * N * N, Nf = N * N;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * Np) return;
   const int64_t e = t / Np;
   const int m = (int)(t % Np), i = m % N, j = (m / N) % N, k = m / (N * N);
@@ -639,6 +680,16 @@ __global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI,
     }
   }
   if (bad) atomicOr(flag, 1);
+}
+
+template <int N, typename T>
+__global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef,
+                          const T *__restrict__ metrics, int64_t E, int mode, int stage, double dt,
+                          double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
+                          double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
+                          int *__restrict__ flag, DevPhys dph) {
+  correct_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Rpart, FI, ef, metrics, E, mode, stage, dt, Rout,
+                     Q, Qc, Un, Unc, acc, flag, dph);
 }
 
 // Copies of the FP64 state in the compute type (mixed path): the stage state and U_n.
@@ -785,6 +836,157 @@ cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, doubl
     case 8: return max_dt_impl<8>(m, ph, cfl, d_out, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched persistent stage: one cooperative launch runs every phase of one RK stage for all
+// cases of a ragged ensemble.  Phases are separated by a grid barrier whose waits are bounded:
+// a wait that exceeds the spin limit sets the error word and every block returns.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool batch_grid_sync(BatchSync *sy, long long limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &sy->bar_gen;
+    volatile int *err = &sy->err;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(&sy->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&sy->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&sy->bar_gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (*err) break;
+        if (++it > limit) {
+          atomicExch(&sy->err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)&sy->err == 0;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase &c, const BatchLaunch &L,
+                                           double *smem) {
+  const DevMesh &m = c.m;
+  const T *Qin = reinterpret_cast<const T *>(m.mixed ? m.Qc : m.Q);
+  T *Qtr = reinterpret_cast<T *>(m.Qtr), *Gtr = reinterpret_cast<T *>(m.Gtr), *FI = reinterpret_cast<T *>(m.FI);
+  T *Rpart = reinterpret_cast<T *>(m.Rpart);
+  const T *met = reinterpret_cast<const T *>(m.metrics), *lift = reinterpret_cast<const T *>(m.liftfac);
+  const T *nrm = reinterpret_cast<const T *>(m.normals);
+  switch (tk.kind) {
+    case TASK_INTERP:
+      interp_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qin, m.ef, Qtr,
+                        m.E);
+      break;
+    case TASK_BC_PREPARE:
+      bc_prepare_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, nrm,
+                            m.if_bc, m.bcs, m.n_interior, m.n_if - m.n_interior, c.ph);
+      break;
+    case TASK_VOLUME: {
+      // Sub-blocks of nth threads, one element each; threads past the last full sub-block idle.
+      const int tpe = ((N * N * N + 31) / 32) * 32;
+      const int nth = tpe >= (int)blockDim.x ? (int)blockDim.x : tpe;
+      const int epb = (int)blockDim.x / nth;
+      const int le = (int)threadIdx.x / nth;
+      const int tid = (int)threadIdx.x % nth;
+      const int64_t e = tk.begin + le;
+      const bool active = le < epb && e < tk.end;
+      volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * volume_smem_values<N>(), Qin, met,
+                        m.ef, Qtr, lift, Gtr, Rpart, c.ph);
+      break;
+    }
+    case TASK_IFACE:
+      iface_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm, FI,
+                       m.n_interior, c.ph);
+      break;
+    case TASK_BC_FLUX:
+      bc_flux_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm,
+                         m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph);
+      break;
+    case TASK_CORRECT:
+      correct_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Rpart, FI, m.ef,
+                         met, m.E, MODE_RK, L.stage, L.dts[tk.cs], nullptr, m.Q,
+                         m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr, m.Un, reinterpret_cast<T *>(m.Unc), m.acc,
+                         &L.sync->nonfinite, c.ph);
+      break;
+  }
+}
+
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) k_batch_stage(BatchLaunch L) {
+  extern __shared__ double smem[];
+  __shared__ int s_task;
+  if (L.debug_skip_block == (int)blockIdx.x) return;     // never arrives: the others time out
+  for (int ph = 0; ph < L.n_phases; ++ph) {
+    if (ph > 0 && !batch_grid_sync(L.sync, L.spin_limit)) return;
+    const int t0 = L.phase_begin[ph], t1 = L.phase_begin[ph + 1];
+    while (true) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_task = t0 + (int)atomicAdd(&L.sync->counters[ph], 1u);
+      __syncthreads();
+      const int ti = s_task;
+      if (ti >= t1) break;
+      const BatchTask tk = L.tasks[ti];
+      const BatchCase &c = L.cases[tk.cs];
+      switch (c.m.N) {
+        case 2: batch_task<T, 2>(tk, c, L, smem); break;
+        case 3: batch_task<T, 3>(tk, c, L, smem); break;
+        case 4: batch_task<T, 4>(tk, c, L, smem); break;
+        case 5: batch_task<T, 5>(tk, c, L, smem); break;
+        case 6: batch_task<T, 6>(tk, c, L, smem); break;
+        case 7: if (BLOCK >= 352) batch_task<T, 7>(tk, c, L, smem); break;
+        case 8: if (BLOCK >= 512) batch_task<T, 8>(tk, c, L, smem); break;
+      }
+    }
+  }
+}
+
+size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed) {
+  (void)mixed;
+  size_t best = 0;
+  for (int k = 0; k < n; ++k) {
+    const int N = Ns[k];
+    const int tpe = ((N * N * N + 31) / 32) * 32;
+    const size_t per = (size_t)(35 * N * N * N + 30 * N * N) * sizeof(double);
+    const size_t need = per * (size_t)(tpe >= block ? 1 : block / tpe);
+    if (need > best) best = need;
+  }
+  return best;
+}
+
+template <typename T, int BLOCK>
+static cudaError_t batch_launch_impl(const BatchLaunch &L, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_stage<T, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BatchLaunch arg = L;
+  void *args[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void *)k_batch_stage<T, BLOCK>, dim3(grid), dim3(BLOCK), args, smem, st);
+}
+
+cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st) {
+  if (block == 256) return mixed ? batch_launch_impl<df32, 256>(L, grid, smem, st) : batch_launch_impl<double, 256>(L, grid, smem, st);
+  if (block == 512) return mixed ? batch_launch_impl<df32, 512>(L, grid, smem, st) : batch_launch_impl<double, 512>(L, grid, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int BLOCK>
+static cudaError_t batch_occ_impl(size_t smem, int *nb) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_stage<T, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_batch_stage<T, BLOCK>, BLOCK, smem);
+}
+
+cudaError_t batch_occupancy(int mixed, int block, size_t smem, int *nb) {
+  if (block == 256) return mixed ? batch_occ_impl<df32, 256>(smem, nb) : batch_occ_impl<double, 256>(smem, nb);
+  if (block == 512) return mixed ? batch_occ_impl<df32, 512>(smem, nb) : batch_occ_impl<double, 512>(smem, nb);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace frx

@@ -54,6 +54,11 @@ class fr_physics(C.Structure):
                 ("precision", C.c_int32)]
 
 
+class fr_batch_info(C.Structure):
+    _fields_ = [("n_cases", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("n_points", C.c_int64), ("smem_bytes", C.c_int64), ("n_tasks", C.c_int32)]
+
+
 class fr_mesh_info(C.Structure):
     _fields_ = [("n_elem", C.c_int64), ("p", C.c_int32), ("n_pts", C.c_int32),
                 ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("device_bytes", C.c_int64)]
@@ -73,6 +78,14 @@ SIGNATURES = {
     "fr_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "fr_probe_fma": (C.c_int32, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "fr_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "fr_batch_set_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "fr_batch_rk_stage": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
+    "fr_batch_tune": (C.c_int, [C.c_void_p]),
+    "fr_batch_query": (C.c_int, [C.c_void_p, C.POINTER(fr_batch_info)]),
+    "fr_batch_debug": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fr_batch_free": (None, [C.c_void_p]),
+    "fr_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_free": (None, [C.c_void_p]),
     "fr_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -218,6 +231,64 @@ class Mesh:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.fr_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Ensemble of meshes advanced together by one persistent launch per RK stage."""
+
+    def __init__(self, meshes):
+        lib = load()
+        self._lib = lib
+        self.meshes = list(meshes)          # keep the borrowed meshes alive
+        arr = (C.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = C.c_void_p()
+        st = lib.fr_batch_create(arr, len(self.meshes), C.byref(h))
+        if st != FR_OK:
+            raise FRError(st, lib.fr_batch_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != FR_OK:
+            raise FRError(st, self._lib.fr_batch_last_error(self._h).decode())
+
+    def set_dt(self, dts):
+        a = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self._lib.fr_batch_set_dt(self._h, a.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def rk_stage(self, stage: int, t: float = 0.0):
+        self._check(self._lib.fr_batch_rk_stage(self._h, stage, t))
+
+    def rk_step(self, t: float = 0.0):
+        for s in range(4):
+            self.rk_stage(s, t)
+
+    def tune(self):
+        self._check(self._lib.fr_batch_tune(self._h))
+
+    def info(self) -> dict:
+        i = fr_batch_info()
+        self._check(self._lib.fr_batch_query(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in fr_batch_info._fields_}
+
+    def debug(self, skip_block: int, spin_limit: int):
+        self._check(self._lib.fr_batch_debug(self._h, skip_block, spin_limit))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fr_batch_free(self._h)
             self._h = None
 
     def __del__(self):
