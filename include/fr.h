@@ -193,9 +193,10 @@ fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_de
  * batch and its meshes are poisoned.  On a non-default stream each stage is captured once into
  * a CUDA graph and replayed.  Errors (timeout, non-finite values) are read back at stage 3.
  * fr_batch_set_dt sets each case's step size (host array, one per case).  fr_batch_tune times
- * the kernel's block size (256/512 threads, which fixes the elements-per-block tile of every
- * order) and resident blocks per SM on this batch, keeps the fastest, and restores every case to
- * its U_n.  fr_batch_debug (tests only) makes block `skip_block` leave before its first barrier,
+ * the persistent kernel's block size (256/512 threads, which fixes the elements-per-block tile of
+ * every order) and resident blocks per SM, and the alternative executor -- every case's own
+ * order-specialised kernels captured back to back in one graph per stage -- keeps the fastest
+ * (fr_batch_info.mode: 0 persistent, 1 per-case kernels), and restores every case to its U_n.  fr_batch_debug (tests only) makes block `skip_block` leave before its first barrier,
  * with a barrier wait limit of `spin_limit` iterations, to exercise the timeout path.
  */
 typedef struct fr_batch fr_batch;
@@ -203,12 +204,15 @@ typedef struct {
   int32_t n_cases, block, grid, blocks_per_sm;
   int64_t n_points, smem_bytes;
   int32_t n_tasks;
+  int32_t mode;          /* 0: one persistent cooperative kernel per stage; 1: per-case kernels */
 } fr_batch_info;
 fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch **out);
 fr_status fr_batch_set_dt(fr_batch *batch, const double *dt_host);
 fr_status fr_batch_rk_stage(fr_batch *batch, int32_t stage, double t);
 fr_status fr_batch_tune(fr_batch *batch);
 fr_status fr_batch_query(const fr_batch *batch, fr_batch_info *info);
+/* fr_batch_select — force the executor: 0 persistent cooperative kernel, 1 per-case kernels. */
+fr_status fr_batch_select(fr_batch *batch, int32_t mode);
 fr_status fr_batch_debug(fr_batch *batch, int32_t skip_block, int64_t spin_limit);
 void fr_batch_free(fr_batch *batch);
 const char *fr_batch_last_error(const fr_batch *batch);

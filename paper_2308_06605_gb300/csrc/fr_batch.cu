@@ -28,6 +28,8 @@ struct fr_batch {
   double *d_dts = nullptr;
   BatchSync *d_sync = nullptr;
   int *h_status = nullptr;   // pinned: err, nonfinite
+  int mode = 0;    // 0: one cooperative persistent kernel per stage; 1: per-case kernels in one graph
+  std::vector<double> h_dts;
   int block = 256, blocks_per_sm = 1, grid = 0;
   size_t smem = 0;
   int phase_begin[6] = {0};
@@ -137,6 +139,14 @@ static fr_status configure(fr_batch *b, int block, int bps) {
 }
 
 static cudaError_t enqueue_stage(fr_batch *b, int stage) {
+  if (b->mode == 1) {
+    // Every case's own specialised kernels, back to back on the stream.
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+      cudaError_t e = launch_residual(b->cases[i].m, b->cases[i].ph, MODE_RK, stage, b->h_dts[i], nullptr, b->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return stage == 3 ? launch_gather_flags(b->d_cases, (int)b->cases.size(), b->d_sync, b->stream) : cudaSuccess;
+  }
   BatchLaunch L;
   L.cases = b->d_cases;
   L.tasks = b->d_tasks;
@@ -223,6 +233,8 @@ extern "C" fr_status fr_batch_set_dt(fr_batch *b, const double *dt_host) {
   cudaError_t e = cudaMemcpyAsync(b->d_dts, dt_host, sizeof(double) * b->cases.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, FR_ECUDA, std::string("dt upload: ") + cudaGetErrorString(e));
+  b->h_dts.assign(dt_host, dt_host + b->cases.size());
+  drop_graphs(b);   // the per-case mode bakes dt into its graph
   return FR_OK;
 }
 
@@ -249,6 +261,7 @@ extern "C" fr_status fr_batch_rk_stage(fr_batch *b, int32_t stage, double t) {
   if (st) return st;
   if (stage < 0 || stage > 3) return bfail(b, FR_EINVAL, "stage must be 0..3");
   cudaError_t e;
+  if (b->mode == 1 && b->h_dts.size() != b->cases.size()) return bfail(b, FR_EINVAL, "call fr_batch_set_dt first");
   if (b->stream != nullptr && b->debug_skip < 0) {
     // One graph per stage on a capturable (non-default) stream.
     if (!b->graph[stage]) {
@@ -322,11 +335,37 @@ extern "C" fr_status fr_batch_tune(fr_batch *b) {
       }
     }
   }
+  // Per-case kernels (the same work as separate launches; captured into one graph per stage).
+  int best_mode = 0;
+  {
+    std::vector<double> saved = b->h_dts;
+    if (b->h_dts.size() != b->cases.size()) b->h_dts.assign(b->cases.size(), 0.0);
+    b->mode = 1;
+    cudaError_t e = enqueue_stage(b, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = enqueue_stage(b, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    b->mode = 0;
+    b->h_dts = saved;
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return bfail(b, FR_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_mode = 1;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   fr_status s = read_status(b);
   if (s != FR_OK) return s;
   s = configure(b, best_block, best_bps);
+  b->mode = best_mode;
   if (s != FR_OK) return s;
   cudaError_t e = restore_states(b);
   if (e != cudaSuccess) return bfail(b, FR_ECUDA, std::string("batch restore: ") + cudaGetErrorString(e));
@@ -342,6 +381,16 @@ extern "C" fr_status fr_batch_query(const fr_batch *b, fr_batch_info *info) {
   info->n_points = b->n_points;
   info->smem_bytes = (int64_t)b->smem;
   info->n_tasks = b->phase_begin[b->n_phases];
+  info->mode = b->mode;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_batch_select(fr_batch *b, int32_t mode) {
+  fr_status st = check_batch(b);
+  if (st) return st;
+  if (mode != 0 && mode != 1) return bfail(b, FR_EINVAL, "mode must be 0 or 1");
+  b->mode = mode;
+  drop_graphs(b);
   return FR_OK;
 }
 
@@ -351,6 +400,7 @@ extern "C" fr_status fr_batch_debug(fr_batch *b, int32_t skip_block, int64_t spi
   if (spin_limit < 1) return bfail(b, FR_EINVAL, "spin limit must be positive");
   b->debug_skip = skip_block;
   b->spin_limit = spin_limit;
+  b->mode = 0;
   drop_graphs(b);
   return FR_OK;
 }

@@ -87,6 +87,7 @@ struct BatchLaunch {
 
 // Launch one cooperative persistent stage over all cases (block size 256 or 512).
 cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cudaStream_t st);
 // Largest dynamic shared memory one block needs for the given orders and block size.
 size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed);
 // Resident blocks per SM of the batch kernel for the given configuration.

@@ -948,6 +948,22 @@ __global__ void __launch_bounds__(BLOCK, 1) k_batch_stage(BatchLaunch L) {
   }
 }
 
+// OR the per-case non-finite flags into the batch word and clear them (graph-of-kernels mode).
+__global__ void k_gather_flags(const BatchCase *cases, int n, BatchSync *sy) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int *f = cases[i].m.flag;
+    if (*f) {
+      atomicOr(&sy->nonfinite, 1);
+      *f = 0;
+    }
+  }
+}
+
+cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cudaStream_t st) {
+  k_gather_flags<<<1, 128, 0, st>>>(cases, n, sy);
+  return cudaGetLastError();
+}
+
 size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed) {
   (void)mixed;
   size_t best = 0;

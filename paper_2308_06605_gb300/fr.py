@@ -56,7 +56,7 @@ class fr_physics(C.Structure):
 
 class fr_batch_info(C.Structure):
     _fields_ = [("n_cases", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("n_points", C.c_int64), ("smem_bytes", C.c_int64), ("n_tasks", C.c_int32)]
+                ("n_points", C.c_int64), ("smem_bytes", C.c_int64), ("n_tasks", C.c_int32), ("mode", C.c_int32)]
 
 
 class fr_mesh_info(C.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = {
     "fr_batch_tune": (C.c_int, [C.c_void_p]),
     "fr_batch_query": (C.c_int, [C.c_void_p, C.POINTER(fr_batch_info)]),
     "fr_batch_debug": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fr_batch_select": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_batch_free": (None, [C.c_void_p]),
     "fr_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_free": (None, [C.c_void_p]),
@@ -282,6 +283,9 @@ class Batch:
         i = fr_batch_info()
         self._check(self._lib.fr_batch_query(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in fr_batch_info._fields_}
+
+    def select(self, mode: int):
+        self._check(self._lib.fr_batch_select(self._h, mode))
 
     def debug(self, skip_block: int, spin_limit: int):
         self._check(self._lib.fr_batch_debug(self._h, skip_block, spin_limit))

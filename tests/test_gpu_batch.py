@@ -74,6 +74,20 @@ def test_batch_step_equals_per_mesh_steps(precision):
         _close(c.get_state(), a.get_state())
 
 
+def test_batch_per_case_executor_equals_per_mesh():
+    specs = _cases(1)
+    _, single, Qs, dts = _build(specs)
+    _, batched, _, _ = _build(specs)
+    for m, dt in zip(single, dts):
+        m.rk_step(0.0, dt)
+    with fr.Batch(batched) as b:
+        b.select(1)
+        b.set_dt(dts)
+        b.rk_step(0.0)
+    for a, c in zip(single, batched):
+        np.testing.assert_array_equal(c.get_state(), a.get_state())
+
+
 def test_batch_matches_oracle():
     specs = _cases(0)[:3]
     oras, meshes, Qs, dts = _build(specs)
