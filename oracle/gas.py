@@ -31,16 +31,18 @@ def inviscid_flux(Q, gamma):
     return F
 
 
-def viscous_flux(Q, gradQ, gamma, R, mu, Pr):
+def viscous_flux(Q, gradQ, gamma, R, mu, Pr, kappa=None):
     """F_v[..., j, :] = (0, tau_xj, tau_yj, tau_zj, u_i tau_ij + kappa dT/dx_j).
 
     gradQ[..., j, v] = dQ_v/dx_j.  Velocity and temperature gradients follow from the chain
     rule: du_i/dx_j = (d(rho u_i)/dx_j - u_i drho/dx_j)/rho and, with T = (gamma-1)/R (E/rho -
     |u|^2/2), dT/dx_j = (gamma-1)/R [ (dE/dx_j - (E/rho) drho/dx_j)/rho - u_i du_i/dx_j ].
+    mu (and kappa, default mu cp / Pr) may be arrays broadcasting against Q[..., 0].
     """
     rho, u, _ = primitives(Q, gamma)
     E = Q[..., 4]
-    kappa = mu * gamma * R / ((gamma - 1.0) * Pr)
+    if kappa is None:
+        kappa = mu * gamma * R / ((gamma - 1.0) * Pr)
     gu = np.empty(Q.shape[:-1] + (3, 3))           # gu[..., i, j] = du_i/dx_j
     for i in range(3):
         for j in range(3):

@@ -33,6 +33,7 @@ import numpy as np
 from scipy.spatial import cKDTree
 
 from . import gas
+from . import mlp
 from .basis import Basis1D
 
 FACE_AXIS = (0, 0, 1, 1, 2, 2)
@@ -45,6 +46,7 @@ BC_WALL_ISOTHERMAL = 1
 BC_CHAR_INFLOW = 2
 BC_CHAR_OUTFLOW = 3
 BC_DIRICHLET = 4
+PR_TURB = 0.9      # turbulent Prandtl number of the eddy-viscosity closure
 
 
 def trilinear_geometry(X, ref):
@@ -110,6 +112,23 @@ class HexFR:
             self.ref_face.append(pts)
         self._geometry(desc)
         self._connect(desc)
+        self.closure = None
+
+    def set_closure(self, params, scales):
+        """Enable the eddy-viscosity closure (oracle.mlp): per element nu_t from the element-mean
+        corrected velocity gradient; mu -> mu + rho nu_t, kappa -> kappa + rho nu_t cp / Pr_t in the
+        volume flux, and with the average of the two elements' nu_t at interfaces."""
+        self.closure = (np.asarray(params, dtype=np.float64), scales)
+
+    def _closure_nu(self, Q, grad):
+        rho = Q[..., 0]
+        u = Q[..., 1:4] / rho[..., None]
+        gu = (grad[..., :, 1:4] - grad[..., :, 0:1] * u[..., None, :]) / rho[..., None, None]   # [e][m][j][i]
+        gu = np.swapaxes(gu, -1, -2)                                                            # du_i/dx_j
+        wJ = self.W[None, :] * self.detJ
+        mean = np.einsum('em,emij->eij', wJ, gu) / wJ.sum(axis=1)[:, None, None]
+        X = mlp.features(mean, self.h, self.p)
+        return mlp.eddy_viscosity(self.closure[0], self.closure[1], X)
 
     # ------------------------------------------------------------------ geometry (Eq. 1)
     def _geometry(self, desc):
@@ -312,7 +331,15 @@ class HexFR:
             for f in range(6):
                 r_f = np.einsum('emj,emv->emjv', Sinv[:, :, FACE_AXIS[f], :], lifts[f])
                 gface[:, f] = np.einsum('qm,emjv->eqjv', self.Lf[f], grad_unc + ph.br2_eta * r_f)
-            Fv = gas.viscous_flux(Q, grad, gam, ph.R, ph.mu, ph.Pr)
+            kappa0 = ph.mu * gam * ph.R / ((gam - 1.0) * ph.Pr)
+            cp = gam * ph.R / (gam - 1.0)
+            nu_el = np.zeros(E)
+            if self.closure is not None:
+                nu_el = self._closure_nu(Q, grad)
+            self.last_nu = nu_el
+            rho_v = Q[..., 0]
+            Fv = gas.viscous_flux(Q, grad, gam, ph.R, ph.mu + rho_v * nu_el[:, None], ph.Pr,
+                                  kappa=kappa0 + rho_v * nu_el[:, None] * cp / PR_TURB)
         # Physical and transformed flux at solution points.
         H = gas.inviscid_flux(Q, gam)                              # [E][Np][j][5]
         if viscous:
@@ -328,7 +355,9 @@ class HexFR:
             gL = gface[self.eL, self.fL]
             gR = gface[self.eR, self.fR][rows, self.perm]
             gc = 0.5 * (gL + gR)
-            FI = FI - np.einsum('pqjv,pqj->pqv', gas.viscous_flux(QI, gc, gam, ph.R, ph.mu, ph.Pr), self.nL)
+            nu_if = 0.5 * (nu_el[self.eL] + nu_el[self.eR])[:, None] * QI[..., 0]
+            FI = FI - np.einsum('pqjv,pqj->pqv', gas.viscous_flux(QI, gc, gam, ph.R, ph.mu + nu_if, ph.Pr,
+                                                                  kappa=kappa0 + nu_if * cp / PR_TURB), self.nL)
         Fc = np.empty_like(Fperp)
         Fc[self.eL, self.fL] = FI
         Fc[self.eR, self.fR] = -FI[rows, self.invperm]
@@ -339,7 +368,9 @@ class HexFR:
             Fb = gas.rusanov(Qm, ghosts[k], n, gam)
             if viscous:
                 # Common gradient at a boundary: the interior side's face gradient.
-                Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(bstates[k], gface[e, f], gam, ph.R, ph.mu, ph.Pr), n)
+                nb = nu_el[e] * bstates[k][..., 0]
+                Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(bstates[k], gface[e, f], gam, ph.R, ph.mu + nb, ph.Pr,
+                                                                   kappa=kappa0 + nb * cp / PR_TURB), n)
             Fc[e, f] = Fb
         if magnitude:
             A = np.abs(Hhat)
