@@ -183,6 +183,40 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
 fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
 
 /*
+ * Eddy-viscosity closure (the paper lists LES sub-grid-scale models among its physical models;
+ * this is a learned one).  Per element, a network of 11 -> 64 -> 64 -> 64 -> 1 (GELU, softplus
+ * output) maps the features x = (element-mean corrected velocity gradient du_i/dx_j, 9 values
+ * row-major; |S| = sqrt(2 S_ij S_ij); Delta = h/(p+1)) to nu_t = s_out Delta^2 softplus(z); the
+ * viscous fluxes use mu + rho nu_t and kappa + rho nu_t cp / Pr_t (Pr_t = 0.9), with the mean of the
+ * two elements' nu_t at interfaces.  params: FR_CLOSURE_NPARAMS floats, layout W1[64][11], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4[1]; stored on the device as bfloat16 (round to
+ * nearest even) and evaluated with FP32 accumulation inside the volume kernel.  scales: 23 floats
+ * (input mean[11], input std[11], s_out).  enable = 0 switches it off.  Needs the viscous path;
+ * not available in batches.  fr_closure_nu copies the last evaluated nu_t per element to the host.
+ */
+#define FR_CLOSURE_NPARAMS 9153
+#define FR_CLOSURE_PRT 0.9
+fr_status fr_set_closure(fr_mesh *mesh, const float *params, const float *scales, int32_t enable);
+fr_status fr_closure_nu(fr_mesh *mesh, float *nu_host);
+
+/*
+ * Training kernels of the closure network (FP32; all pointers are device pointers, work is
+ * enqueued on `stream` and the calls return without synchronising).  X: [n][11] raw features,
+ * scales as in fr_set_closure (only mean/std are used), y: [n] targets of softplus(z) (that is
+ * nu_t / (s_out Delta^2)).  work: fr_mlp_workspace_floats(n) floats owned by the caller.
+ * fr_mlp_forward writes softplus(z) to out[n].  fr_mlp_loss_grad writes the mean squared error to
+ * *loss and its gradient with respect to every parameter to grad[FR_CLOSURE_NPARAMS].
+ * fr_mlp_adam applies one Adam update (Kingma & Ba 2015) with bias correction for step >= 1.
+ */
+int64_t fr_mlp_workspace_floats(int64_t n);
+fr_status fr_mlp_forward(const float *params, const float *scales, const float *X, int64_t n, float *out, float *work,
+                         uintptr_t stream);
+fr_status fr_mlp_loss_grad(const float *params, const float *scales, const float *X, const float *y, int64_t n,
+                           float *grad, float *loss, float *work, uintptr_t stream);
+fr_status fr_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t n_params, float lr, float beta1,
+                      float beta2, float eps, int32_t step, uintptr_t stream);
+
+/*
  * Batched stages for ensembles of independent cases (the paper runs one mesh per MPI
  * decomposition; on one GPU an ensemble of unevenly sized cases, with different orders, is
  * advanced together).  fr_batch_create borrows the meshes (they must outlive the batch, share

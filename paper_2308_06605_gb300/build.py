@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfr.so")
-SOURCES = ["fr_mesh.cpp", "fr_kernels.cu", "fr_api.cu", "fr_probe.cu", "fr_static.cu", "fr_batch.cu"]
+SOURCES = ["fr_mesh.cpp", "fr_kernels.cu", "fr_api.cu", "fr_probe.cu", "fr_static.cu", "fr_batch.cu", "fr_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

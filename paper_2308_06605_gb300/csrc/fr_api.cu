@@ -24,6 +24,9 @@ struct fr_mesh {
   std::string err;
   int64_t bytes = 0;
   double *h_scalar = nullptr;   // pinned host scalar for dt / flags
+  // Eddy-viscosity closure (allocated by fr_set_closure).
+  void *d_cw = nullptr;
+  float *d_cscale = nullptr;
   // Instrumentation: one event set per recorded residual evaluation.
   bool profiling = false;
   std::vector<PhaseEvents> ev_pool;
@@ -93,6 +96,12 @@ static void release(fr_mesh *m) {
   if (d.if_bc) cudaFree(d.if_bc);
   if (d.bcs) cudaFree(d.bcs);
   if (d.flag) cudaFree(d.flag);
+  if (d.nu) cudaFree(d.nu);
+  if (d.if_elem) cudaFree(d.if_elem);
+  if (m->d_cw) cudaFree(m->d_cw);
+  if (m->d_cscale) cudaFree(m->d_cscale);
+  m->d_cw = nullptr;
+  m->d_cscale = nullptr;
   if (m->h_scalar) cudaFreeHost(m->h_scalar);
   d = DevMesh{};
   m->h_scalar = nullptr;
@@ -348,6 +357,59 @@ extern "C" fr_status fr_max_dt(fr_mesh *m, double cfl, double *dt) {
   FR_CUDA(m, cudaMemcpyAsync(m->h_scalar, d_out, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   FR_CUDA(m, cudaStreamSynchronize(m->stream));
   *dt = m->h_scalar[0];
+  return FR_OK;
+}
+
+// float -> bfloat16 bits, round to nearest even (NaN kept quiet).
+static uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+extern "C" fr_status fr_set_closure(fr_mesh *m, const float *params, const float *scales, int32_t enable) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!enable) {
+    m->dphys.closure = 0;
+    return FR_OK;
+  }
+  if (!params || !scales) return fail(m, FR_EINVAL, "closure parameters or scales are NULL");
+  if (!m->dphys.viscous) return fail(m, FR_EINVAL, "the closure needs the viscous (BR2) path");
+  for (int k = 0; k < 11; ++k)
+    if (!(scales[11 + k] > 0.f)) return fail(m, FR_EINVAL, "closure input scales must be positive");
+  const int n = FR_CLOSURE_NPARAMS;
+  std::vector<uint16_t> w(n);
+  for (int k = 0; k < n; ++k) w[k] = bf16_bits(params[k]);
+  DevMesh &d = m->dev;
+  if (!m->d_cw) {
+    fr_status s;
+    if ((s = dalloc(m, reinterpret_cast<uint16_t **>(&m->d_cw), (size_t)n)) || (s = dalloc(m, &m->d_cscale, 23)) ||
+        (s = dalloc(m, &d.nu, (size_t)d.E)) || (s = dalloc(m, &d.if_elem, m->host.if_elem.size())))
+      return s;
+    FR_CUDA(m, cudaMemcpyAsync(d.if_elem, m->host.if_elem.data(), m->host.if_elem.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, m->stream));
+    FR_CUDA(m, cudaMemsetAsync(d.nu, 0, sizeof(float) * d.E, m->stream));
+  }
+  FR_CUDA(m, cudaMemcpyAsync(m->d_cw, w.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice, m->stream));
+  FR_CUDA(m, cudaMemcpyAsync(m->d_cscale, scales, sizeof(float) * 23, cudaMemcpyHostToDevice, m->stream));
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  m->dphys.closure = 1;
+  m->dphys.cw = m->d_cw;
+  m->dphys.cscale = m->d_cscale;
+  m->dphys.cp_prt = m->phys.gamma * m->phys.R / (m->phys.gamma - 1.0) / FR_CLOSURE_PRT;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_closure_nu(fr_mesh *m, float *nu_host) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (!nu_host) return fail(m, FR_EINVAL, "nu is NULL");
+  if (!m->dev.nu) return fail(m, FR_EINVAL, "no closure set");
+  FR_CUDA(m, cudaMemcpyAsync(nu_host, m->dev.nu, sizeof(float) * m->dev.E, cudaMemcpyDeviceToHost, m->stream));
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
   return FR_OK;
 }
 

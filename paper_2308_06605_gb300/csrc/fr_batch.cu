@@ -184,6 +184,10 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, s == FR_EINVAL ? FR_EINVAL : s, "a mesh is NULL or poisoned");
     }
+    if (c.ph.closure) {
+      delete b;
+      return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
+    }
     if (i == 0) {
       b->mixed = c.m.mixed;
       b->stream = st;

@@ -22,6 +22,10 @@ struct DevPhys {
   double gamma, R, mu, kappa, eta;
   int viscous;
   int inviscid;
+  int closure;             // eddy-viscosity network on (weights below)
+  double cp_prt;           // cp / Pr_t
+  const void *cw;          // [9153] bf16 network parameters (device)
+  const float *cscale;     // [23] input mean (11), input std (11), output scale (device)
   PhysT<double> d;
   PhysT<df32> f;
 };
@@ -33,6 +37,8 @@ struct DevMesh {
   int mixed;        // 1: element arrays hold df32 pairs (same 8-byte slots), Qc holds the state as df32
   double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc, *Unc;
   int32_t *ef, *if_bc;
+  int32_t *if_elem;        // [n_if][2] element of each side (-1: boundary), closure only
+  float *nu;               // [E] eddy viscosity of each element, closure only
   fr_bc *bcs;
   int *flag;
 };

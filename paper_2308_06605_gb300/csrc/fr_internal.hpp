@@ -30,6 +30,7 @@ struct HostMesh {
   int64_t n_interior = 0;         // first n_interior entries are two-sided
   std::vector<int32_t> ef;        // [E][6] packed: (iface << 4) | (side << 3) | orient
   std::vector<int32_t> if_bc;     // [n_if] -1 two-sided, else index into bcs
+  std::vector<int32_t> if_elem;   // [n_if][2] element of side 0 and side 1 (-1 for a boundary)
   std::vector<double> metrics;    // [E][10][Np]: S (row-major d, j) then 1/|J|
   std::vector<double> liftfac;    // [E][6][3][Nf]
   std::vector<double> normals;    // [n_if][4][Nf] outward area-scaled normal of side 0, then |n|

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "df32.cuh"
 #include "fr_device.hpp"
 
@@ -29,6 +31,7 @@ struct BasisT {
   T D[kMaxN * kMaxN];    // D[i*N + a] = l_a'(x_i)
   T Dt[kMaxN * kMaxN];   // D - hp (x) lp + hm (x) lm: divergence with the own-flux correction
   T lm[kMaxN], lp[kMaxN], hm[kMaxN], hp[kMaxN];
+  double w[kMaxN];       // Gauss-Legendre weights (closure's element means)
 };
 
 __constant__ BasisT<double> c_basis_d[kMaxN];   // index N - 1
@@ -54,6 +57,7 @@ cudaError_t upload_basis_tables() {
       d.lp[i] = b.lp[i];
       d.hm[i] = b.hm[i];
       d.hp[i] = b.hp[i];
+      d.w[i] = b.w[i];
       for (int a = 0; a < N; ++a) {
         d.D[i * N + a] = b.D[i * N + a];
         d.Dt[i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
@@ -65,6 +69,7 @@ cudaError_t upload_basis_tables() {
       f.lp[i] = df_split_host(d.lp[i]);
       f.hm[i] = df_split_host(d.hm[i]);
       f.hp[i] = df_split_host(d.hp[i]);
+      f.w[i] = d.w[i];
     }
     for (int i = 0; i < kMaxN * kMaxN; ++i) {
       f.D[i] = df_split_host(d.D[i]);
@@ -150,9 +155,75 @@ __device__ __forceinline__ void normal_inviscid(const double q[5], const double 
   normal_inviscid(q, n, nn, dph.gamma, out, s);
 }
 
+// Transport coefficients of one viscous-flux evaluation (molecular, or with an eddy viscosity).
+template <typename T>
+struct Visc {
+  T mu, m2mu3, kappa;   // mu, -2 mu / 3, kappa
+};
+
+template <typename T>
+__device__ __forceinline__ Visc<T> visc_of(const PhysT<T> &ph) {
+  return Visc<T>{ph.mu, ph.m2mu3, ph.kappa};
+}
+
+// Closure: mu + rho nu_t, kappa + rho nu_t cp / Pr_t (nu_t = 0 gives the molecular values exactly).
+template <typename T>
+__device__ __forceinline__ Visc<T> visc_with(const PhysT<T> &ph, T rho_nu, const DevPhys &dph) {
+  if (!dph.closure) return visc_of(ph);
+  const T mu = ph.mu + rho_nu;
+  return Visc<T>{mu, ph.m2mu3 + from_double<T>(-2.0 / 3.0) * rho_nu, ph.kappa + from_double<T>(dph.cp_prt) * rho_nu};
+}
+
+// Eddy-viscosity network for one element, evaluated by one warp (lane = 0..31): BF16 weights,
+// FP32 activations and accumulation.  x: the 11 raw features; buf: 128 floats of shared memory.
+// Returns nu_t = s_out Delta^2 softplus(z) (Delta = x[10]).
+__device__ __forceinline__ float closure_mlp(const DevPhys &dph, const float x_raw[11], float *buf, int lane) {
+  const __nv_bfloat16 *W = static_cast<const __nv_bfloat16 *>(dph.cw);
+  const float *sc = dph.cscale;
+  float x[11];
+#pragma unroll
+  for (int c = 0; c < 11; ++c) x[c] = (x_raw[c] - sc[c]) / sc[11 + c];
+  const __nv_bfloat16 *W1 = W, *b1 = W1 + 64 * 11, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+                      *b3 = W3 + 64 * 64, *w4 = b3 + 64, *b4 = w4 + 64;
+  float *hA = buf, *hB = buf + 64;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int n = lane + 32 * r;
+    float a = __bfloat162float(b1[n]);
+#pragma unroll
+    for (int c = 0; c < 11; ++c) a = fmaf(__bfloat162float(W1[n * 11 + c]), x[c], a);
+    hA[n] = 0.5f * a * (1.f + erff(a * 0.70710678118654752f));
+  }
+  __syncwarp();
+  const __nv_bfloat16 *Ws[2] = {W2, W3}, *bs[2] = {b2, b3};
+  float *hin = hA, *hout = hB;
+#pragma unroll
+  for (int layer = 0; layer < 2; ++layer) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int n = lane + 32 * r;
+      float a = __bfloat162float(bs[layer][n]);
+      for (int c = 0; c < 64; ++c) a = fmaf(__bfloat162float(Ws[layer][n * 64 + c]), hin[c], a);
+      hout[n] = 0.5f * a * (1.f + erff(a * 0.70710678118654752f));
+    }
+    __syncwarp();
+    float *t = hin;
+    hin = hout;
+    hout = t;
+  }
+  float z = __bfloat162float(w4[lane]) * hin[lane] + __bfloat162float(w4[lane + 32]) * hin[lane + 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+  z += __bfloat162float(b4[0]);
+  const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
+  __syncwarp();
+  return sc[22] * x_raw[10] * x_raw[10] * sp;
+}
+
 // Viscous flux F_v[j][v] (j = direction) of state q with gradient G[j*5 + v] = dQ_v/dx_j.
 template <typename T>
-__device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const PhysT<T> &ph, T Fv[3][5]) {
+__device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const PhysT<T> &ph, const Visc<T> &vc,
+                                             T Fv[3][5]) {
   const T ri = ph.one / q[0];
   const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
   const T eo = q[4] * ri;
@@ -165,20 +236,20 @@ __device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const Phy
 #pragma unroll
   for (int j = 0; j < 3; ++j)
     dT[j] = ph.cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri - (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j]));
-  const T lam = ph.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
+  const T lam = vc.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     T t[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      t[i] = ph.mu * (du[i][j] + du[j][i]);
+      t[i] = vc.mu * (du[i][j] + du[j][i]);
       if (i == j) t[i] = t[i] + lam;
     }
     Fv[j][0] = ph.zero;
     Fv[j][1] = t[0];
     Fv[j][2] = t[1];
     Fv[j][3] = t[2];
-    Fv[j][4] = u[0] * t[0] + u[1] * t[1] + u[2] * t[2] + ph.kappa * dT[j];
+    Fv[j][4] = u[0] * t[0] + u[1] * t[1] + u[2] * t[2] + vc.kappa * dT[j];
   }
 }
 
@@ -243,7 +314,8 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
                                             const T *__restrict__ Q, const T *__restrict__ metrics,
                                             const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
                                             const T *__restrict__ liftfac, T *__restrict__ Gtr,
-                                            T *__restrict__ Rpart, const DevPhys &dph) {
+                                            T *__restrict__ Rpart, const DevPhys &dph,
+                                            const double *__restrict__ hel, float *__restrict__ nu_out) {
   constexpr int Np = N * N * N, Nf = N * N;
   T *sm = reinterpret_cast<T *>(sm_raw);
   T *sQ = sm;                 // [5][Np]
@@ -269,17 +341,16 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     }
   }
   __syncthreads();
-  if (active && tid < Np) {
-    const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
-    T S[9];
+  const bool pt = active && tid < Np;
+  const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
+  T S[9], invJ, q[5], H[3][5], G[15];
+  if (pt) {
     const T *met = metrics + e * 10 * Np + m;
 #pragma unroll
     for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
-    const T invJ = met[9 * Np];
-    T q[5];
+    invJ = met[9 * Np];
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v] = sQ[v * Np + m];
-    T H[3][5];
     {
       // Inviscid flux F_j.
       const T ri = ph.one / q[0];
@@ -321,7 +392,6 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
         gc[1][v] = a1.get();
         gc[2][v] = a2.get();
       }
-      T G[15];
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
         const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
@@ -338,8 +408,62 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
           G[jj * 5 + v] = dc.get();
         }
       }
+    }
+  }
+  T rho_nu = ph.zero;
+  if (viscous && dph.closure) {
+    // Eddy-viscosity closure: quadrature-weighted element mean of the corrected velocity
+    // gradient, then one warp evaluates the network (BF16 weights, FP32 accumulation).
+    float *red = reinterpret_cast<float *>(sm + volume_smem_values<N>());   // [10][Np] + 129
+    if (pt) {
+      const double ri = 1.0 / to_double(q[0]);
+      const double w = (double)B.w[i] * B.w[j] * B.w[k] / to_double(invJ);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const double dudx = (to_double(G[b * 5 + 1 + a]) - to_double(q[1 + a]) * ri * to_double(G[b * 5])) * ri;
+          red[(a * 3 + b) * Np + m] = (float)(w * dudx);
+        }
+      red[9 * Np + m] = (float)w;
+    }
+    __syncthreads();
+    if (active && tid < 32) {
+      float acc[10];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) {
+        float sacc = 0.f;
+        for (int mm = tid; mm < Np; mm += 32) sacc += red[c * Np + mm];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        acc[c] = sacc;
+      }
+      float x[11];
+      float ss = 0.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) x[c] = acc[c] / acc[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const float sab = 0.5f * (x[a * 3 + b] + x[b * 3 + a]);
+          ss += sab * sab;
+        }
+      x[9] = sqrtf(2.f * ss);
+      x[10] = (float)(hel[e] / N);
+      const float nu = closure_mlp(dph, x, red + 10 * Np + 1, tid);
+      if (tid == 0) {
+        red[10 * Np] = nu;
+        if (nu_out) nu_out[e] = nu;
+      }
+    }
+    __syncthreads();
+    if (pt) rho_nu = q[0] * from_double<T>((double)red[10 * Np]);
+  }
+  if (pt) {
+    if (viscous) {
       T Fv[3][5];
-      viscous_flux<T>(q, G, ph, Fv);
+      viscous_flux<T>(q, G, ph, visc_with(ph, rho_nu, dph), Fv);
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
@@ -407,10 +531,10 @@ template <int N, typename T>
 __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
     k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
              const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
-             DevPhys dph) {
+             DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out) {
   extern __shared__ double sm_raw[];
   volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr, Rpart,
-                    dph);
+                    dph, hel, nu_out);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -420,7 +544,8 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
 template <int N, typename T>
 __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                                            const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if,
-                                           const DevPhys &dph) {
+                                           const DevPhys &dph, const int32_t *__restrict__ if_elem,
+                                           const float *__restrict__ nu) {
   constexpr int Nf = N * N;
   if (t >= n_if * Nf) return;
   const int64_t I = t / Nf;
@@ -449,8 +574,10 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
 #pragma unroll
     for (int c = 0; c < 15; ++c)
       G[c] = ph.half * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
+    T rho_nu = ph.zero;
+    if (dph.closure) rho_nu = qc[0] * from_double<T>(0.5 * ((double)nu[if_elem[2 * I]] + (double)nu[if_elem[2 * I + 1]]));
     T Fv[3][5];
-    viscous_flux<T>(qc, G, ph, Fv);
+    viscous_flux<T>(qc, G, ph, visc_with(ph, rho_nu, dph), Fv);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
   }
@@ -460,8 +587,9 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
 
 template <int N, typename T>
 __global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
-                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph) {
-  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph);
+                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph,
+                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu) {
+  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -549,7 +677,8 @@ template <int N, typename T>
 __device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                                              const T *__restrict__ normals, const int32_t *__restrict__ if_bc,
                                              const fr_bc *__restrict__ bcs, T *__restrict__ FI, int64_t first,
-                                             int64_t count, const DevPhys &dph) {
+                                             int64_t count, const DevPhys &dph,
+                                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu) {
   constexpr int Nf = N * N;
   if (t >= count * Nf) return;
   const int64_t I = first + t / Nf;
@@ -579,8 +708,10 @@ __device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qt
     for (int c = 0; c < 15; ++c) G[c] = Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qiT[v] = from_double<T>(qi[v]);
+    T rho_nu = ph.zero;
+    if (dph.closure) rho_nu = qiT[0] * from_double<T>((double)nu[if_elem[2 * I]]);
     T Fv[3][5];
-    viscous_flux<T>(qiT, G, ph, Fv);
+    viscous_flux<T>(qiT, G, ph, visc_with(ph, rho_nu, dph), Fv);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
   }
@@ -591,9 +722,10 @@ __device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qt
 template <int N, typename T>
 __global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
                           const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs, T *__restrict__ FI,
-                          int64_t first, int64_t count, DevPhys dph) {
+                          int64_t first, int64_t count, DevPhys dph, const int32_t *__restrict__ if_elem,
+                          const float *__restrict__ nu) {
   bc_flux_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, if_bc, bcs, FI, first, count,
-                     dph);
+                     dph, if_elem, nu);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -761,21 +893,22 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   }
   {
     const int threads = volume_threads<N>();
-    const size_t smem = sizeof(T) * (35 * Np + 30 * Nf);
+    const size_t smem = sizeof(T) * (35 * Np + 30 * Nf) + (ph.closure ? sizeof(float) * (10 * Np + 1 + 128) : 0);
     cudaError_t err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
-    k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph);
+    k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu);
     FR_EV_END(1);
   }
   {
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
-    if (n > 0) k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph);
+    if (n > 0)
+      k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu);
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
     if (nb > 0)
       k_bc_flux<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, m.if_bc, m.bcs, FI, m.n_interior,
-                                                                   m.n_if - m.n_interior, ph);
+                                                                   m.n_if - m.n_interior, ph, m.if_elem, m.nu);
     FR_EV_END(2);
   }
   {
@@ -899,16 +1032,16 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
       const int64_t e = tk.begin + le;
       const bool active = le < epb && e < tk.end;
       volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * volume_smem_values<N>(), Qin, met,
-                        m.ef, Qtr, lift, Gtr, Rpart, c.ph);
+                        m.ef, Qtr, lift, Gtr, Rpart, c.ph, m.h, nullptr);
       break;
     }
     case TASK_IFACE:
       iface_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm, FI,
-                       m.n_interior, c.ph);
+                       m.n_interior, c.ph, m.if_elem, m.nu);
       break;
     case TASK_BC_FLUX:
       bc_flux_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm,
-                         m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph);
+                         m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph, m.if_elem, m.nu);
       break;
     case TASK_CORRECT:
       correct_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Rpart, FI, m.ef,

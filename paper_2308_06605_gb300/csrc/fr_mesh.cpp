@@ -397,6 +397,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   }
   m.ef.assign(E * 6, -1);
   m.if_bc.assign(m.n_if, -1);
+  m.if_elem.assign(2 * m.n_if, -1);
   std::vector<int> orient(n_int, 0);
   // Orientation of side 1 relative to side 0.
   auto corner_xyz = [&](Side s, double c[4][3], int r[4][2]) {
@@ -421,12 +422,15 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
       return FR_EMESH;
     }
     orient[I] = code;
+    m.if_elem[2 * I] = (int32_t)pr.first.e;
+    m.if_elem[2 * I + 1] = (int32_t)pr.second.e;
     m.ef[pr.first.e * 6 + pr.first.f] = (int32_t)((I << 4) | (0 << 3) | 0);
     m.ef[pr.second.e * 6 + pr.second.f] = (int32_t)((I << 4) | (1 << 3) | code);
   }
   for (size_t k = 0; k < bfaces.size(); ++k) {
     int64_t I = n_int + (int64_t)k;
     m.if_bc[I] = bfaces[k].second;
+    m.if_elem[2 * I] = (int32_t)bfaces[k].first.e;
     m.ef[bfaces[k].first.e * 6 + bfaces[k].first.f] = (int32_t)(I << 4);
   }
   for (int64_t i = 0; i < E * 6; ++i)

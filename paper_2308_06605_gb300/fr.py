@@ -75,6 +75,14 @@ SIGNATURES = {
     "fr_rk_stage": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_double]),
     "fr_max_dt": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "fr_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_set_closure": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32]),
+    "fr_closure_nu": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "fr_mlp_workspace_floats": (C.c_int64, [C.c_int64]),
+    "fr_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fr_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_size_t]),
+    "fr_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_float,
+                              C.c_float, C.c_int32, C.c_size_t]),
     "fr_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "fr_probe_fma": (C.c_int32, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
@@ -220,6 +228,19 @@ class Mesh:
         self._check(self._lib.fr_max_dt(self._h, cfl, C.byref(v)))
         return v.value
 
+    def set_closure(self, params, scales, enable: bool = True):
+        """Eddy-viscosity network: params (9153 floats), scales (mean[11], std[11], s_out)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        sc = np.ascontiguousarray(scales, dtype=np.float32)
+        self._keep_closure = (p, sc)
+        self._check(self._lib.fr_set_closure(self._h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                             sc.ctypes.data_as(C.POINTER(C.c_float)), 1 if enable else 0))
+
+    def closure_nu(self):
+        out = np.empty(self.n_elem, dtype=np.float32)
+        self._check(self._lib.fr_closure_nu(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
     def profile(self, enable: bool):
         self._check(self._lib.fr_profile(self._h, 1 if enable else 0))
 
@@ -306,3 +327,55 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+N_CLOSURE_PARAMS = 9153
+
+
+class MLPTrainer:
+    """Device-side training of the closure network through fr_mlp_* (torch tensors for memory)."""
+
+    def __init__(self, params, scales, max_batch: int, stream: int = 0):
+        import torch
+        self._lib = load()
+        self.torch = torch
+        self.stream = stream
+        self.P = torch.as_tensor(np.asarray(params, dtype=np.float32)).cuda().contiguous()
+        self.sc = torch.as_tensor(np.asarray(scales, dtype=np.float32)).cuda().contiguous()
+        self.g = torch.zeros_like(self.P)
+        self.m = torch.zeros_like(self.P)
+        self.v = torch.zeros_like(self.P)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.work = torch.empty(int(self._lib.fr_mlp_workspace_floats(max_batch)), dtype=torch.float32, device="cuda")
+        self.max_batch = max_batch
+        self.step_count = 0
+
+    @staticmethod
+    def _p(t):
+        return C.c_void_p(t.data_ptr())
+
+    def loss_grad(self, X, y):
+        n = X.shape[0]
+        assert n <= self.max_batch
+        st = self._lib.fr_mlp_loss_grad(self._p(self.P), self._p(self.sc), self._p(X), self._p(y), n, self._p(self.g),
+                                        self._p(self.loss), self._p(self.work), self.stream)
+        if st != FR_OK:
+            raise FRError(st, "fr_mlp_loss_grad")
+        return self.loss, self.g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step_count += 1
+        st = self._lib.fr_mlp_adam(self._p(self.P), self._p(self.g), self._p(self.m), self._p(self.v), self.P.numel(),
+                                   lr, beta1, beta2, eps, self.step_count, self.stream)
+        if st != FR_OK:
+            raise FRError(st, "fr_mlp_adam")
+
+    def forward(self, X):
+        n = X.shape[0]
+        assert n <= self.max_batch
+        out = self.torch.empty(n, dtype=self.torch.float32, device="cuda")
+        st = self._lib.fr_mlp_forward(self._p(self.P), self._p(self.sc), self._p(X), n, self._p(out), self._p(self.work),
+                                      self.stream)
+        if st != FR_OK:
+            raise FRError(st, "fr_mlp_forward")
+        return out
