@@ -66,10 +66,11 @@ class Periodic:
 class MeshDesc:
     xyz: np.ndarray                     # [n_nodes][3] float64
     hex: np.ndarray                     # [E][8] int64 node ids, VTK order
-    bface_nodes: np.ndarray             # [nb][4] int64 node ids of each boundary quad
+    bface_nodes: np.ndarray             # [nb][4] int64 node ids of each boundary face (-1 pads a triangle)
     bface_tag: np.ndarray               # [nb] int32
     periodic: List[Periodic] = field(default_factory=list)
     bcs: List[BC] = field(default_factory=list)
+    prism: np.ndarray = field(default_factory=lambda: np.zeros((0, 6), dtype=np.int64))   # [Ep][6] VTK order
 
     @property
     def n_elem(self) -> int:
@@ -105,10 +106,16 @@ def rotation_vertex_permutations() -> np.ndarray:
     return np.array(perms, dtype=np.int64)
 
 
+# Proper relabelings of a prism's vertices (VTK order): the three rotations of the triangle and
+# the three top/bottom exchanges combined with a reflection of the triangle.
+PRISM_PERMUTATIONS = np.array([[0, 1, 2, 3, 4, 5], [1, 2, 0, 4, 5, 3], [2, 0, 1, 5, 3, 4],
+                               [3, 5, 4, 0, 2, 1], [4, 3, 5, 1, 0, 2], [5, 4, 3, 2, 1, 0]], dtype=np.int64)
+
+
 def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
                  periodic=(True, True, True), seed: int | None = None,
                  shuffle: bool = False, rotate: bool = False, perturb: float = 0.0,
-                 wall_tags: dict | None = None, affine=None) -> MeshDesc:
+                 wall_tags: dict | None = None, affine=None, prisms=None) -> MeshDesc:
     """Structured box of nx*ny*nz hexahedra stored as an unstructured mesh.
 
     Boundary faces are tagged 1..6 for x-, x+, y-, y+, z-, z+.  Periodic axes pair (1,2), (3,4),
@@ -117,7 +124,9 @@ def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
     elements).  `shuffle` permutes the element order and `rotate` applies a random one of the
     24 cube rotations to each element's local vertex order; both are seeded.  `affine` (3x3)
     maps the box about `lo` (x -> lo + A (x - lo)), giving a sheared lattice of parallelepipeds;
-    periodic translations are mapped with it.
+    periodic translations are mapped with it.  `prisms` = "all" or "checker" splits every (or every
+    other) column of hexahedra along z into two prisms each (cut through the diagonal from corner
+    0 to corner 2 of every bottom face); z-boundary faces of split columns are triangles.
     """
     nx, ny, nz = (int(v) for v in n)
     lo = np.asarray(lo, dtype=np.float64)
@@ -144,6 +153,18 @@ def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
                               nid[i, j, k + 1], nid[i + 1, j, k + 1], nid[i + 1, j + 1, k + 1],
                               nid[i, j + 1, k + 1]])
     hexes = np.array(hexes, dtype=np.int64)
+    split = np.zeros((nx, ny), dtype=bool)
+    if prisms == "all":
+        split[:] = True
+    elif prisms == "checker":
+        split[(np.add.outer(np.arange(nx), np.arange(ny)) % 2) == 0] = True
+    is_split = np.array([split[i, j] for k in range(nz) for j in range(ny) for i in range(nx)], dtype=bool)
+    prism_list = []
+    for hv in hexes[is_split]:
+        prism_list.append([hv[0], hv[1], hv[2], hv[4], hv[5], hv[6]])
+        prism_list.append([hv[0], hv[2], hv[3], hv[4], hv[6], hv[7]])
+    prism_arr = np.array(prism_list, dtype=np.int64).reshape(-1, 6)
+    hexes = hexes[~is_split]
     # Boundary quads with tags.
     bnodes, btags = [], []
     for j in range(ny):
@@ -156,8 +177,13 @@ def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
             bnodes.append([nid[i, ny, k], nid[i + 1, ny, k], nid[i + 1, ny, k + 1], nid[i, ny, k + 1]]); btags.append(4)
     for i in range(nx):
         for j in range(ny):
-            bnodes.append([nid[i, j, 0], nid[i + 1, j, 0], nid[i + 1, j + 1, 0], nid[i, j + 1, 0]]); btags.append(5)
-            bnodes.append([nid[i, j, nz], nid[i + 1, j, nz], nid[i + 1, j + 1, nz], nid[i, j + 1, nz]]); btags.append(6)
+            for kk, tag in ((0, 5), (nz, 6)):
+                c = [nid[i, j, kk], nid[i + 1, j, kk], nid[i + 1, j + 1, kk], nid[i, j + 1, kk]]
+                if split[i, j]:
+                    bnodes.append([c[0], c[1], c[2], -1]); btags.append(tag)
+                    bnodes.append([c[0], c[2], c[3], -1]); btags.append(tag)
+                else:
+                    bnodes.append(c); btags.append(tag)
     per = []
     L = hi - lo
     for a in range(3):
@@ -173,13 +199,17 @@ def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
         perms = rotation_vertex_permutations()
         r = rng.integers(0, 24, size=hexes.shape[0])
         hexes = np.take_along_axis(hexes, perms[r], axis=1)
+        if len(prism_arr):
+            r = rng.integers(0, 6, size=prism_arr.shape[0])
+            prism_arr = np.take_along_axis(prism_arr, PRISM_PERMUTATIONS[r], axis=1)
     if shuffle:
         hexes = hexes[rng.permutation(hexes.shape[0])]
+        prism_arr = prism_arr[rng.permutation(prism_arr.shape[0])]
     return MeshDesc(xyz=np.ascontiguousarray(xyz, dtype=np.float64),
                     hex=np.ascontiguousarray(hexes, dtype=np.int64),
                     bface_nodes=np.array(bnodes, dtype=np.int64).reshape(-1, 4),
                     bface_tag=np.array(btags, dtype=np.int32),
-                    periodic=per, bcs=bcs)
+                    periodic=per, bcs=bcs, prism=np.ascontiguousarray(prism_arr, dtype=np.int64))
 
 
 # ---------------------------------------------------------------------------------------------
