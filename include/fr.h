@@ -2,7 +2,8 @@
  * fr.h — C ABI of the GB300 flux-reconstruction (FR) library.
  *
  * The library evaluates the semi-discrete FR residual of the compressible Navier–Stokes
- * equations on unstructured hexahedral meshes at orders p = 1..7 and advances it with explicit
+ * equations on unstructured hexahedral and mixed hexahedral/prismatic meshes at orders p = 1..7
+ * and advances it with explicit
  * Runge–Kutta stages, all on one CUDA device (arXiv 2308.06605, section "FR Algorithm",
  * Eq. 1–3).  Plain C types only; device pointers are raw CUDA pointers, host pointers are plain
  * host memory.  Every call returns an fr_status; nothing aborts.
@@ -12,6 +13,11 @@
  *    m = i + N j + N^2 k (N = p + 1) on ascending Gauss–Legendre nodes along the element's
  *    reference axes xi, eta, zeta, variables (rho, rho u, rho v, rho w, E).  Reference vertex
  *    order of a hexahedron follows VTK/CGNS (bottom face counter-clockwise, then top face).
+ *    On meshes with prisms the prism points follow all hexahedral points: prism by prism in
+ *    input order, points m = q + Nt k (Nt = N(N+1)/2) with q the triangle node (warp-and-blend
+ *    nodes of Warburton 2006 on the reference triangle (-1,-1), (1,-1), (-1,1), enumerated by
+ *    barycentric lattice index n = 0..p outer, m = 0..p-n inner) and k the Gauss–Legendre node
+ *    along the prism's axis.
  *  - The library copies every host array it is given at create time; pointers passed to other
  *    calls are borrowed for the duration of the call only.
  *  - All device work is enqueued on the stream given to fr_mesh_create (0 = legacy default
@@ -72,12 +78,16 @@ typedef struct {
   const int64_t *hex;           /* [n_hex][8] vertex ids, VTK order (host) */
   int32_t p;                    /* polynomial order, 1..7, uniform over the mesh */
   int64_t n_bface;
-  const int64_t *bface_nodes;   /* [n_bface][4] vertex ids of each boundary quadrilateral */
+  const int64_t *bface_nodes;   /* [n_bface][4] vertex ids of each boundary face (a triangle
+                                   lists three ids and -1) */
   const int32_t *bface_tag;     /* [n_bface] */
   int32_t n_bc;
   const fr_bc *bc;              /* [n_bc] tag -> condition */
   int32_t n_periodic;
   const fr_periodic *periodic;  /* [n_periodic] */
+  int64_t n_prism;              /* 0 for a hexahedral mesh */
+  const int64_t *prism;         /* [n_prism][6] vertex ids, VTK wedge order: (v0, v1, v2) one
+                                   triangle, (v3, v4, v5) the opposite one, v_k+3 above v_k (host) */
 } fr_mesh_desc;
 
 typedef struct {
@@ -99,6 +109,9 @@ typedef struct {
   int64_t n_iface;      /* interior + periodic interfaces */
   int64_t n_bface;      /* boundary-condition faces */
   int64_t device_bytes; /* device memory held by the mesh */
+  int64_t n_prism;      /* prisms (after the n_elem hexahedra in every per-point array) */
+  int32_t n_pts_prism;  /* solution points per prism: (p+1)(p+2)/2 triangle nodes x (p+1) */
+  int64_t n_points;     /* all solution points: n_elem n_pts + n_prism n_pts_prism */
 } fr_mesh_info;
 
 /*
@@ -117,13 +130,13 @@ fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintp
 fr_status fr_mesh_query(const fr_mesh *mesh, fr_mesh_info *info);
 
 /*
- * fr_solution_points — physical coordinates of the solution points, [n_elem][n_pts][3] in the
+ * fr_solution_points — physical coordinates of the solution points, [n_points][3] in the
  * canonical order, written to host memory (Eq. 2: the nodal points of the element map).
  */
 fr_status fr_solution_points(fr_mesh *mesh, double *xyz_host);
 
 /*
- * fr_set_state / fr_get_state — copy the solution Q (canonical layout, n_elem*n_pts*5 doubles)
+ * fr_set_state / fr_get_state — copy the solution Q (canonical layout, n_points*5 doubles)
  * into / out of the mesh.  `where` = FR_HOST or FR_DEVICE.  fr_set_state also resets the
  * Runge–Kutta registers (the solution becomes the start of a new step).
  */
@@ -177,8 +190,8 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
  * before any stream capture.  All calls share the one array and it keeps the last call's
  * contents; nothing in it needs to start at zero, but calls whose work overlaps on the GPU
  * (other streams, other meshes, other threads) race on it: serialise them.  Work is enqueued
- * on the mesh's stream and the call returns without synchronising.  FP64 meshes only
- * (FR_EUNSUPPORTED for FR_PREC_MIXED).
+ * on the mesh's stream and the call returns without synchronising.  FP64 hexahedral meshes only
+ * (FR_EUNSUPPORTED for FR_PREC_MIXED or a mesh with prisms).
  */
 fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
 
@@ -192,7 +205,7 @@ fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_de
  * W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4[1]; stored on the device as bfloat16 (round to
  * nearest even) and evaluated with FP32 accumulation inside the volume kernel.  scales: 23 floats
  * (input mean[11], input std[11], s_out).  enable = 0 switches it off.  Needs the viscous path;
- * not available in batches.  fr_closure_nu copies the last evaluated nu_t per element to the host.
+ * hexahedral meshes only (FR_EUNSUPPORTED on a mesh with prisms); not available in batches.  fr_closure_nu copies the last evaluated nu_t per element to the host.
  */
 #define FR_CLOSURE_NPARAMS 9153
 #define FR_CLOSURE_PRT 0.9
@@ -220,7 +233,7 @@ fr_status fr_mlp_adam(float *params, const float *grad, float *m, float *v, int3
  * Batched stages for ensembles of independent cases (the paper runs one mesh per MPI
  * decomposition; on one GPU an ensemble of unevenly sized cases, with different orders, is
  * advanced together).  fr_batch_create borrows the meshes (they must outlive the batch, share
- * precision, device and stream).  fr_batch_rk_stage runs stage `stage` (RK44, same update as
+ * precision, device and stream; hexahedral meshes only, FR_EUNSUPPORTED for one with prisms).  fr_batch_rk_stage runs stage `stage` (RK44, same update as
  * fr_rk_stage) of every case in ONE cooperative persistent kernel: phases (face interpolation,
  * boundary states, volume, interface fluxes, correction + update) are separated by grid
  * barriers whose waits are bounded; if a wait gives up, the call returns FR_ETIMEOUT and the

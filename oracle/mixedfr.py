@@ -201,8 +201,13 @@ class MixedFR:
     def solution_points(self):
         return [x.copy() for x in self.x]
 
-    def residual(self, Qs):
-        """Qs: [Q_hex [E_h][Np_h][5], Q_prism [E_p][Np_p][5]] -> residuals in the same layout."""
+    def residual(self, Qs, magnitude=False):
+        """Qs: [Q_hex [E_h][Np_h][5], Q_prism [E_p][Np_p][5]] -> residuals in the same layout.
+
+        With magnitude=True it returns instead the entrywise magnitude of the final sum,
+        |J|^-1 [sum_d |D_d| |F^_d| + sum_f |C_f| (|F^I_perp| + |L_f| sum_d |N_f,d| |F^_d|)], the scale
+        of the rounding error of any evaluation order (used for tolerances).
+        """
         ph = self.phys
         gam = ph.gamma
         visc = ph.viscous != 0 and ph.mu != 0.0
@@ -262,6 +267,15 @@ class MixedFR:
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(bst[k], gfaces[ti][fi][e], gam, ph.R, ph.mu, ph.Pr), n)
             Fc[ti][fi][e] = F
         out = []
+        if magnitude:
+            for ti, t in enumerate(T):
+                A = np.abs(Hhat[ti])
+                mag = sum(np.einsum('mn,env->emv', np.abs(t.Dop[d]), A[:, :, d, :]) for d in range(3))
+                for fi, f in enumerate(t.faces):
+                    own = np.einsum('qm,emv->eqv', np.abs(f["L"]), np.einsum('d,emdv->emv', np.abs(f["N"]), A))
+                    mag = mag + np.einsum('mq,eqv->emv', np.abs(f["C"]), np.abs(Fc[ti][fi]) + own)
+                out.append(mag / self.detJ[ti][..., None])
+            return out
         for ti, t in enumerate(T):
             R = sum(np.einsum('mn,env->emv', t.Dop[d], Hhat[ti][:, :, d, :]) for d in range(3))
             for fi, f in enumerate(t.faces):

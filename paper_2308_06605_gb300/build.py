@@ -16,7 +16,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfr.so")
-SOURCES = ["fr_mesh.cpp", "fr_kernels.cu", "fr_api.cu", "fr_probe.cu", "fr_static.cu", "fr_batch.cu", "fr_mlp.cu"]
+SOURCES = ["fr_mesh.cpp", "fr_tri.cpp", "fr_kernels.cu", "fr_prism.cu", "fr_api.cu", "fr_probe.cu", "fr_static.cu",
+           "fr_batch.cu", "fr_mlp.cu"]
+# The batched stage kernel is compiled once per (precision, block size) so the variants build in parallel.
+VARIANTS = [("fr_batch_kernel.cu", f"m{m}_b{b}", [f"-DFRX_BATCH_MIXED={m}", f"-DFRX_BATCH_BLOCK={b}"])
+            for m in (0, 1) for b in (256, 512)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,9 +42,10 @@ def build(verbose: bool = False, extra=()) -> str:
     common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
-    def compile_one(src):
-        obj = os.path.join(objdir, src + ".o")
-        cmd = common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, tag, flags = unit if isinstance(unit, tuple) else (unit, "", [])
+        obj = os.path.join(objdir, src + (("." + tag) if tag else "") + ".o")
+        cmd = common + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -50,8 +55,9 @@ def build(verbose: bool = False, extra=()) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    units = VARIANTS + SOURCES          # slowest first
+    with ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath," + cuda_libdir()]

@@ -89,7 +89,8 @@ static fr_status check_mesh(fr_mesh *m) {
 
 static void release(fr_mesh *m) {
   DevMesh &d = m->dev;
-  double *dbl[] = {d.Q, d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr, d.Gtr, d.FI, d.h, d.dtbuf, d.Qc, d.Unc};
+  double *dbl[] = {d.Q,  d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr,
+                   d.Gtr, d.FI, d.h,   d.dtbuf, d.Qc,      d.Unc,     d.metrics_p, d.ptab};
   for (double *p : dbl)
     if (p) cudaFree(p);
   if (d.ef) cudaFree(d.ef);
@@ -98,6 +99,9 @@ static void release(fr_mesh *m) {
   if (d.flag) cudaFree(d.flag);
   if (d.nu) cudaFree(d.nu);
   if (d.if_elem) cudaFree(d.if_elem);
+  if (d.ef_p) cudaFree(d.ef_p);
+  if (d.tri_slot) cudaFree(d.tri_slot);
+  if (d.if_tri) cudaFree(d.if_tri);
   if (m->d_cw) cudaFree(m->d_cw);
   if (m->d_cscale) cudaFree(m->d_cscale);
   m->d_cw = nullptr;
@@ -126,7 +130,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   *out = nullptr;
   if (!desc || !phys) return fail(nullptr, FR_EINVAL, "desc or phys is NULL");
   if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
-  if (desc->n_hex <= 0 || !desc->hex || desc->n_nodes <= 0 || !desc->xyz)
+  if (desc->n_hex < 0 || desc->n_prism < 0 || desc->n_hex + desc->n_prism <= 0 || (desc->n_hex > 0 && !desc->hex) ||
+      (desc->n_prism > 0 && !desc->prism) || desc->n_nodes <= 0 || !desc->xyz)
     return fail(nullptr, FR_EINVAL, "empty mesh or NULL arrays");
   if (desc->n_bface < 0 || (desc->n_bface > 0 && (!desc->bface_nodes || !desc->bface_tag)))
     return fail(nullptr, FR_EINVAL, "bad boundary-face arrays");
@@ -216,23 +221,29 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   DevMesh &d = m->dev;
   d.p = h.p; d.N = h.N; d.Np = h.Np; d.Nf = h.Nf;
   d.E = h.E; d.n_if = h.n_if; d.n_interior = h.n_interior;
+  d.Ep = h.Ep; d.Nt = h.Nt; d.Npp = h.Npp;
   d.mixed = (phys->precision == FR_PREC_MIXED) ? 1 : 0;
-  const size_t nsol = (size_t)h.E * h.Np * 5;
+  const size_t nsol = ((size_t)h.E * h.Np + (size_t)h.Ep * h.Npp) * 5;
+  const size_t G = (size_t)(h.E + h.Ep);
   const size_t Nf = h.Nf;
   if ((st = dalloc(m, &d.Q, nsol)) || (st = dalloc(m, &d.Un, nsol)) || (st = dalloc(m, &d.acc, nsol)) ||
       (st = dalloc(m, &d.Rpart, nsol)) || (st = dalloc(m, &d.metrics, h.metrics.size())) ||
       (st = dalloc(m, &d.liftfac, h.liftfac.size())) || (st = dalloc(m, &d.normals, h.normals.size())) ||
       (st = dalloc(m, &d.Qtr, (size_t)h.n_if * 2 * 5 * Nf)) ||
       (st = dalloc(m, &d.Gtr, (size_t)h.n_if * 2 * 15 * Nf)) || (st = dalloc(m, &d.FI, (size_t)h.n_if * 5 * Nf)) ||
-      (st = dalloc(m, &d.h, (size_t)h.E)) || (st = dalloc(m, &d.dtbuf, (size_t)h.E + 1)) ||
+      (st = dalloc(m, &d.h, G)) || (st = dalloc(m, &d.dtbuf, G + 1)) ||
       (st = dalloc(m, &d.ef, h.ef.size())) || (st = dalloc(m, &d.if_bc, h.if_bc.size())) ||
       (st = dalloc(m, &d.bcs, h.bcs.size())) || (st = dalloc(m, &d.flag, 1)) ||
       (d.mixed && ((st = dalloc(m, &d.Qc, nsol)) || (st = dalloc(m, &d.Unc, nsol)))))
     return bail(st);
+  if (h.Ep > 0 && ((st = dalloc(m, &d.ef_p, h.ef_p.size())) || (st = dalloc(m, &d.metrics_p, h.metrics_p.size())) ||
+                   (st = dalloc(m, &d.ptab, h.ptab.size())) || (st = dalloc(m, &d.tri_slot, h.tri_slot.size())) ||
+                   (st = dalloc(m, &d.if_tri, h.if_tri.size()))))
+    return bail(st);
   if (d.mixed) {
     // Geometry in the element arithmetic's format: each double becomes a df32 (hi, lo) pair
     // stored in the same 8-byte slot.
-    for (std::vector<double> *v : {&h.metrics, &h.liftfac, &h.normals})
+    for (std::vector<double> *v : {&h.metrics, &h.liftfac, &h.normals, &h.metrics_p, &h.ptab})
       for (double &x : *v) {
         df32 p = df_split_host(x);
         std::memcpy(&x, &p, sizeof(double));
@@ -248,6 +259,11 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
       {d.ef, h.ef.data(), h.ef.size() * sizeof(int32_t)},
       {d.if_bc, h.if_bc.data(), h.if_bc.size() * sizeof(int32_t)},
       {d.bcs, h.bcs.data(), h.bcs.size() * sizeof(fr_bc)},
+      {d.ef_p, h.ef_p.data(), h.ef_p.size() * sizeof(int32_t)},
+      {d.metrics_p, h.metrics_p.data(), h.metrics_p.size() * sizeof(double)},
+      {d.ptab, h.ptab.data(), h.ptab.size() * sizeof(double)},
+      {d.tri_slot, h.tri_slot.data(), h.tri_slot.size() * sizeof(int32_t)},
+      {d.if_tri, h.if_tri.data(), h.if_tri.size() * sizeof(int8_t)},
   };
   for (const Up &u : ups) {
     if (u.bytes == 0) continue;
@@ -264,6 +280,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   std::vector<double>().swap(h.metrics);
   std::vector<double>().swap(h.liftfac);
   std::vector<double>().swap(h.normals);
+  std::vector<double>().swap(h.metrics_p);
   *out = m;
   return FR_OK;
 }
@@ -276,6 +293,9 @@ extern "C" fr_status fr_mesh_query(const fr_mesh *m, fr_mesh_info *info) {
   info->n_iface = m->host.n_interior;
   info->n_bface = m->host.n_if - m->host.n_interior;
   info->device_bytes = m->bytes;
+  info->n_prism = m->host.Ep;
+  info->n_pts_prism = m->host.Npp;
+  info->n_points = m->host.E * m->host.Np + m->host.Ep * m->host.Npp;
   return FR_OK;
 }
 
@@ -287,6 +307,11 @@ extern "C" fr_status fr_solution_points(fr_mesh *m, double *xyz) {
   return FR_OK;
 }
 
+// Bytes of a state or residual in the canonical layout (hexahedral points, then prism points).
+static size_t state_bytes(const DevMesh &d) {
+  return ((size_t)d.E * d.Np + (size_t)d.Ep * d.Npp) * 5 * sizeof(double);
+}
+
 static cudaMemcpyKind kind_of(int where, bool to_device) {
   if (where == FR_DEVICE) return cudaMemcpyDeviceToDevice;
   return to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
@@ -296,7 +321,7 @@ extern "C" fr_status fr_set_state(fr_mesh *m, const double *Q, int32_t where) {
   fr_status st = check_mesh(m);
   if (st) return st;
   if (!Q || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad state pointer or where");
-  const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+  const size_t bytes = state_bytes(m->dev);
   FR_CUDA(m, cudaMemcpyAsync(m->dev.Q, Q, bytes, kind_of(where, true), m->stream));
   FR_CUDA(m, cudaMemcpyAsync(m->dev.Un, m->dev.Q, bytes, cudaMemcpyDeviceToDevice, m->stream));
   FR_CUDA(m, launch_state_copy(m->dev, m->stream));
@@ -308,7 +333,7 @@ extern "C" fr_status fr_get_state(fr_mesh *m, double *Q, int32_t where) {
   fr_status st = check_mesh(m);
   if (st) return st;
   if (!Q || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad state pointer or where");
-  const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+  const size_t bytes = state_bytes(m->dev);
   FR_CUDA(m, cudaMemcpyAsync(Q, m->dev.Q, bytes, kind_of(where, false), m->stream));
   if (where == FR_HOST) FR_CUDA(m, cudaStreamSynchronize(m->stream));
   return FR_OK;
@@ -322,7 +347,7 @@ extern "C" fr_status fr_residual(fr_mesh *m, double t, double *R, int32_t where)
   double *dst = (where == FR_DEVICE) ? R : m->dev.acc;   // acc is free outside an RK step
   FR_CUDA(m, launch_residual(m->dev, m->dphys, MODE_RESIDUAL, 0, 0.0, dst, m->stream, next_events(m)));
   if (where == FR_HOST) {
-    const size_t bytes = (size_t)m->dev.E * m->dev.Np * 5 * sizeof(double);
+    const size_t bytes = state_bytes(m->dev);
     FR_CUDA(m, cudaMemcpyAsync(R, dst, bytes, cudaMemcpyDeviceToHost, m->stream));
     FR_CUDA(m, cudaStreamSynchronize(m->stream));
   }
@@ -352,7 +377,7 @@ extern "C" fr_status fr_max_dt(fr_mesh *m, double cfl, double *dt) {
   fr_status st = check_mesh(m);
   if (st) return st;
   if (!dt || !(cfl > 0.0)) return fail(m, FR_EINVAL, "bad dt pointer or cfl");
-  double *d_out = m->dev.dtbuf + m->dev.E;
+  double *d_out = m->dev.dtbuf + m->dev.E + m->dev.Ep;
   FR_CUDA(m, launch_max_dt(m->dev, m->dphys, cfl, d_out, m->stream));
   FR_CUDA(m, cudaMemcpyAsync(m->h_scalar, d_out, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   FR_CUDA(m, cudaStreamSynchronize(m->stream));
@@ -378,6 +403,7 @@ extern "C" fr_status fr_set_closure(fr_mesh *m, const float *params, const float
   }
   if (!params || !scales) return fail(m, FR_EINVAL, "closure parameters or scales are NULL");
   if (!m->dphys.viscous) return fail(m, FR_EINVAL, "the closure needs the viscous (BR2) path");
+  if (m->dev.Ep > 0) return fail(m, FR_EUNSUPPORTED, "the closure is built for hexahedral meshes only");
   for (int k = 0; k < 11; ++k)
     if (!(scales[11 + k] > 0.f)) return fail(m, FR_EINVAL, "closure input scales must be positive");
   const int n = FR_CLOSURE_NPARAMS;

@@ -188,6 +188,10 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
     }
+    if (c.m.Ep > 0) {
+      delete b;
+      return bfail(nullptr, FR_EUNSUPPORTED, "meshes with prisms cannot be batched");
+    }
     if (i == 0) {
       b->mixed = c.m.mixed;
       b->stream = st;

@@ -41,6 +41,14 @@ struct DevMesh {
   float *nu;               // [E] eddy viscosity of each element, closure only
   fr_bc *bcs;
   int *flag;
+  // Prisms (after the E hexahedra in Q, Un, acc, Rpart, Qc, Unc, h); zero / null on hexahedral meshes.
+  int64_t Ep;
+  int Nt, Npp;             // triangle nodes, points per prism
+  int32_t *ef_p;           // [Ep][5] packed like ef (triangular faces: kTriPerm code)
+  double *metrics_p;       // [Ep][10][Npp] S then 1/|J|, in the element type
+  double *ptab;            // prism operator table (prism_tab layout), in the element type
+  int32_t *tri_slot;       // [6][Nt] side-0 slot of a side-1 triangle node per code
+  int8_t *if_tri;          // [n_if] 1: triangular interface (only its first Nt slots are used)
 };
 
 enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
@@ -91,6 +99,18 @@ struct BatchLaunch {
   int debug_skip_block;  // >= 0: that block leaves before the first barrier (timeout test)
 };
 
+// Variants of the batched stage kernel (fr_batch_kernel.cu, compiled once per precision m = 0 FP64,
+// 1 double-float and block size b): launch, resident blocks per SM, upload of the unit's basis.
+#define FRX_BATCH_VARIANT_DECL(m, b)                                                                    \
+  cudaError_t batch_launch_m##m##_b##b(const BatchLaunch &L, int grid, size_t smem, cudaStream_t st); \
+  cudaError_t batch_occupancy_m##m##_b##b(size_t smem, int *nb);                                       \
+  cudaError_t batch_upload_m##m##_b##b();
+FRX_BATCH_VARIANT_DECL(0, 256)
+FRX_BATCH_VARIANT_DECL(0, 512)
+FRX_BATCH_VARIANT_DECL(1, 256)
+FRX_BATCH_VARIANT_DECL(1, 512)
+#undef FRX_BATCH_VARIANT_DECL
+
 // Launch one cooperative persistent stage over all cases (block size 256 or 512).
 cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cudaStream_t st);
@@ -108,6 +128,13 @@ inline int batch_elems_per_block(int N, int block) {
 // recording an error on it.
 fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device);
 fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg);
+
+// Prism phases of one residual evaluation (fr_prism.cu): 0 face traces, 1 volume, 3 correction
+// and output / RK update; a no-op on hexahedral meshes.
+cudaError_t launch_prism_phase(const DevMesh &m, const DevPhys &ph, int phase, int mode, int stage, double dt,
+                               double *Rout, cudaStream_t st);
+// Per-prism time-step bound into m.dtbuf[E + ep] (same formula as the hexahedra).
+cudaError_t launch_prism_dt(const DevMesh &m, const DevPhys &ph, double cfl, cudaStream_t st);
 
 // Mixed path: refresh the df32 copy of the state after it was set from outside.
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st);

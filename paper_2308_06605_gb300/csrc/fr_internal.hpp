@@ -7,6 +7,12 @@
 
 #include "fr.h"
 
+#ifdef __CUDACC__
+#define FRX_HD __host__ __device__
+#else
+#define FRX_HD
+#endif
+
 namespace frx {
 
 constexpr int kMaxN = 8;      // p <= 7
@@ -22,6 +28,48 @@ struct Basis1D {
 };
 Basis1D make_basis(int p);
 
+// Nodal triangle basis of order p (prism elements): warp-and-blend nodes, operators from the
+// orthonormal Proriol-Koornwinder-Dubiner modes, all computed in long double.
+struct TriBasis {
+  int p = 0, N = 0, Nt = 0;
+  std::vector<double> r, s;        // [Nt] nodes, enumerated n = 0..p (outer), m = 0..p-n (inner)
+  std::vector<double> Dr, Ds;      // [Nt][Nt] derivative matrices
+  std::vector<double> Minv;        // [Nt][Nt] inverse mass matrix
+  std::vector<double> wT;          // [Nt] integral of each nodal function over the triangle
+  std::vector<double> E[3];        // [N][Nt] interpolation to the Gauss-Legendre points of edge e
+  std::vector<double> LQ[3];       // [Nt][N] DG lifting of edge e: M^-1 E^T diag(w)
+  std::vector<int32_t> perm;       // [6][Nt] image node under the vertex permutation kTriPerm[c]
+};
+extern const int kTriPerm[6][3];
+// Point of edge e (0: s = -1, 1: r + s = 0, 2: r = -1) at parameter sigma in [-1, 1].
+void tri_edge_point(int edge, double sigma, double &r, double &s);
+bool make_tri_basis(int p, TriBasis &T);
+
+// Offsets (in values) of the per-mesh prism operator table for line order N (Nt = N(N+1)/2):
+// Dr, Ds (triangle derivatives), Drt, Dst (with the own-flux correction of the quadrilateral
+// faces folded in), E [3][N][Nt], LQ [3][Nt][N], D1, D1t [N][N] (line derivative, plain and with
+// the own-flux correction of the triangular faces), then l(-1), l(+1), h-, h+ [N] each.
+struct PrismTab {
+  int Nt, Dr, Ds, Drt, Dst, E, LQ, D1, D1t, lm, lp, hm, hp, size;
+};
+FRX_HD constexpr PrismTab prism_tab(int N) {
+  const int Nt = N * (N + 1) / 2, T2 = Nt * Nt;
+  return PrismTab{Nt,
+                  0,
+                  T2,
+                  2 * T2,
+                  3 * T2,
+                  4 * T2,
+                  4 * T2 + 3 * N * Nt,
+                  4 * T2 + 6 * N * Nt,
+                  4 * T2 + 6 * N * Nt + N * N,
+                  4 * T2 + 6 * N * Nt + 2 * N * N,
+                  4 * T2 + 6 * N * Nt + 2 * N * N + N,
+                  4 * T2 + 6 * N * Nt + 2 * N * N + 2 * N,
+                  4 * T2 + 6 * N * Nt + 2 * N * N + 3 * N,
+                  4 * T2 + 6 * N * Nt + 2 * N * N + 4 * N};
+}
+
 // Connectivity + geometry, host side, before upload.
 struct HostMesh {
   int p = 0, N = 0, Np = 0, Nf = 0;
@@ -34,15 +82,23 @@ struct HostMesh {
   std::vector<double> metrics;    // [E][10][Np]: S (row-major d, j) then 1/|J|
   std::vector<double> liftfac;    // [E][6][3][Nf]
   std::vector<double> normals;    // [n_if][4][Nf] outward area-scaled normal of side 0, then |n|
-  std::vector<double> xsol;       // [E][Np][3]
-  std::vector<double> h;          // [E] volume^(1/3)
+  std::vector<double> xsol;       // [E][Np][3] then [Ep][Npp][3]
+  std::vector<double> h;          // [E + Ep] volume^(1/3)
   std::vector<fr_bc> bcs;
+  // Prisms (after the hexahedra in every per-point array).
+  int64_t Ep = 0;
+  int Nt = 0, Npp = 0;            // triangle nodes, points per prism (Nt * N)
+  std::vector<int32_t> ef_p;      // [Ep][5] packed like ef; triangular faces carry a kTriPerm code
+  std::vector<double> metrics_p;  // [Ep][10][Npp]
+  std::vector<int8_t> if_tri;     // [n_if] 1: triangular interface (meshes with prisms only)
+  std::vector<double> ptab;       // prism operator table (prism_tab layout)
+  std::vector<int32_t> tri_slot;  // [6][Nt] side-0 slot of a side-1 node for each code
 };
 
 fr_status build_host_mesh(const fr_mesh_desc *d, HostMesh &m, std::string &err);
 
 // Slot (side-0 ordering) of the local face point (a, b) for an orientation code.
-inline int orient_slot(int code, int a, int b, int N) {
+FRX_HD inline int orient_slot(int code, int a, int b, int N) {
   if (code & 4) { int t = a; a = b; b = t; }
   if (code & 1) a = N - 1 - a;
   if (code & 2) b = N - 1 - b;

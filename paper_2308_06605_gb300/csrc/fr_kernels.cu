@@ -1,828 +1,9 @@
-// Kernels of the FR residual and the RK44 stage update (arXiv 2308.06605, section "FR
-// Algorithm", Eq. 1-3).  One residual evaluation is four launches (plus two for boundary faces):
-//   interp_faces : Q -> solution traces at the flux points of every face (interface slots)
-//   bc_prepare   : boundary faces: common solution Q^I and ghost traces
-//   volume       : per element, BR2-corrected gradients, physical + transformed fluxes at the
-//                  solution points, gradient traces at the flux points, and the divergence of
-//                  the transformed flux including the own-flux part of the correction
-//   iface_flux   : per interface flux point, Rusanov + BR2 common normal flux (bc_flux for
-//                  boundary faces)
-//   correct      : per solution point, adds the common-flux correction, scales by -1/|J| and
-//                  writes R or applies the RK44 stage update (always FP64).
-//
-// Every kernel is a template on the scalar type T of its element arithmetic and of the arrays it
-// exchanges: T = double is the FP64 path; T = df32 (FP32 hi + lo pairs on the FP32 pipe) is the
-// mixed path, in which the Riemann flux's pressure/energy recovery, the boundary states and the
-// RK update stay FP64.
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <type_traits>
-
-#include <cuda_bf16.h>
-
-#include "df32.cuh"
-#include "fr_device.hpp"
+// Per-mesh launches of the hexahedral FR kernels and their host-side dispatch (the device bodies
+// are in fr_bodies.cuh); dt estimate; basis-table upload for every translation unit; dispatch of
+// the batched stage kernel variants.
+#include "fr_bodies.cuh"
 
 namespace frx {
-
-template <typename T>
-struct BasisT {
-  T D[kMaxN * kMaxN];    // D[i*N + a] = l_a'(x_i)
-  T Dt[kMaxN * kMaxN];   // D - hp (x) lp + hm (x) lm: divergence with the own-flux correction
-  T lm[kMaxN], lp[kMaxN], hm[kMaxN], hp[kMaxN];
-  double w[kMaxN];       // Gauss-Legendre weights (closure's element means)
-};
-
-__constant__ BasisT<double> c_basis_d[kMaxN];   // index N - 1
-__constant__ BasisT<df32> c_basis_f[kMaxN];
-
-template <typename T> __device__ __forceinline__ const BasisT<T> &cbasis(int N);
-template <> __device__ __forceinline__ const BasisT<double> &cbasis<double>(int N) { return c_basis_d[N - 1]; }
-template <> __device__ __forceinline__ const BasisT<df32> &cbasis<df32>(int N) { return c_basis_f[N - 1]; }
-
-template <typename T> __device__ __forceinline__ const PhysT<T> &phys_of(const DevPhys &p);
-template <> __device__ __forceinline__ const PhysT<double> &phys_of<double>(const DevPhys &p) { return p.d; }
-template <> __device__ __forceinline__ const PhysT<df32> &phys_of<df32>(const DevPhys &p) { return p.f; }
-
-cudaError_t upload_basis_tables() {
-  BasisT<double> hd[kMaxN] = {};
-  BasisT<df32> hf[kMaxN] = {};
-  for (int p = 1; p < kMaxN; ++p) {
-    Basis1D b = make_basis(p);
-    const int N = p + 1;
-    BasisT<double> &d = hd[N - 1];
-    for (int i = 0; i < N; ++i) {
-      d.lm[i] = b.lm[i];
-      d.lp[i] = b.lp[i];
-      d.hm[i] = b.hm[i];
-      d.hp[i] = b.hp[i];
-      d.w[i] = b.w[i];
-      for (int a = 0; a < N; ++a) {
-        d.D[i * N + a] = b.D[i * N + a];
-        d.Dt[i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
-      }
-    }
-    BasisT<df32> &f = hf[N - 1];
-    for (int i = 0; i < kMaxN; ++i) {
-      f.lm[i] = df_split_host(d.lm[i]);
-      f.lp[i] = df_split_host(d.lp[i]);
-      f.hm[i] = df_split_host(d.hm[i]);
-      f.hp[i] = df_split_host(d.hp[i]);
-      f.w[i] = d.w[i];
-    }
-    for (int i = 0; i < kMaxN * kMaxN; ++i) {
-      f.D[i] = df_split_host(d.D[i]);
-      f.Dt[i] = df_split_host(d.Dt[i]);
-    }
-  }
-  cudaError_t e = cudaMemcpyToSymbol(c_basis_d, hd, sizeof(hd));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_basis_f, hf, sizeof(hf));
-}
-
-// Strides of the reference axes in the point index m = i + N j + N^2 k.
-template <int N>
-__device__ __forceinline__ int axis_stride(int a) {
-  return a == 0 ? 1 : (a == 1 ? N : N * N);
-}
-
-// Flux point r = a + N b of face f: base index of its normal line and the stride along it.
-template <int N>
-__device__ __forceinline__ void face_line(int f, int r, int &base, int &sd) {
-  const int d = f >> 1;
-  const int t0 = (d == 0) ? 1 : 0, t1 = (d == 2) ? 1 : 2;
-  const int a = r % N, b = r / N;
-  base = a * axis_stride<N>(t0) + b * axis_stride<N>(t1);
-  sd = axis_stride<N>(d);
-}
-
-__device__ __forceinline__ int slot_of(int code, int a, int b, int N) {
-  if (code & 4) { int t = a; a = b; b = t; }
-  if (code & 1) a = N - 1 - a;
-  if (code & 2) b = N - 1 - b;
-  return a + N * b;
-}
-
-// ------------------------------------------------------------------------------------------
-// Gas dynamics (ideal gas, Stokes hypothesis, constant mu, Fourier heat flux).
-// ------------------------------------------------------------------------------------------
-// Normal inviscid flux F(q).n and (|u.n^| + c)|n|, in FP64 (pressure/energy recovery); nn = |n|.
-__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, double g,
-                                                double out[5], double &un_abs_plus_c_n) {
-  const double ri = 1.0 / q[0];
-  const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
-  const double p = (g - 1.0) * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
-  const double un = u * n[0] + v * n[1] + w * n[2];
-  out[0] = q[0] * un;
-  out[1] = q[1] * un + p * n[0];
-  out[2] = q[2] * un + p * n[1];
-  out[3] = q[3] * un + p * n[2];
-  out[4] = (q[4] + p) * un;
-  un_abs_plus_c_n = fabs(un) + sqrt(g * p * ri) * nn;      // (|u.n^| + c) |n|
-}
-
-// Double-float normal flux with the pressure recovery p = (gamma-1)(E - m.u/2) in FP64.
-__device__ __forceinline__ void normal_inviscid(const df32 q[5], const df32 n[3], df32 nn, const DevPhys &dph,
-                                                df32 out[5], df32 &un_abs_plus_c_n) {
-  const PhysT<df32> &ph = dph.f;
-  const df32 ri = ph.one / q[0];
-  const df32 u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-  Dot<df32> mu, unn;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    mu.add(q[1 + c], u[c]);
-    unn.add(u[c], n[c]);
-  }
-  const double pd = (dph.gamma - 1.0) * (to_double(q[4]) - 0.5 * to_double(mu.get()));
-  const df32 p = df_from(pd);
-  const df32 un = unn.get();
-  out[0] = q[0] * un;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Dot<df32> f;
-    f.add(q[1 + c], un);
-    f.add(p, n[c]);
-    out[1 + c] = f.get();
-  }
-  out[4] = (q[4] + p) * un;
-  un_abs_plus_c_n = fabs(un) + sqrt(ph.gamma * p * ri) * nn;
-}
-
-// FP64 overload with the same signature shape (the FP64 path's arithmetic).
-__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, const DevPhys &dph,
-                                                double out[5], double &s) {
-  normal_inviscid(q, n, nn, dph.gamma, out, s);
-}
-
-// Transport coefficients of one viscous-flux evaluation (molecular, or with an eddy viscosity).
-template <typename T>
-struct Visc {
-  T mu, m2mu3, kappa;   // mu, -2 mu / 3, kappa
-};
-
-template <typename T>
-__device__ __forceinline__ Visc<T> visc_of(const PhysT<T> &ph) {
-  return Visc<T>{ph.mu, ph.m2mu3, ph.kappa};
-}
-
-// Closure: mu + rho nu_t, kappa + rho nu_t cp / Pr_t (nu_t = 0 gives the molecular values exactly).
-template <typename T>
-__device__ __forceinline__ Visc<T> visc_with(const PhysT<T> &ph, T rho_nu, const DevPhys &dph) {
-  if (!dph.closure) return visc_of(ph);
-  const T mu = ph.mu + rho_nu;
-  return Visc<T>{mu, ph.m2mu3 + from_double<T>(-2.0 / 3.0) * rho_nu, ph.kappa + from_double<T>(dph.cp_prt) * rho_nu};
-}
-
-// Eddy-viscosity network for one element, evaluated by one warp (lane = 0..31): BF16 weights,
-// FP32 activations and accumulation.  x: the 11 raw features; buf: 128 floats of shared memory.
-// Returns nu_t = s_out Delta^2 softplus(z) (Delta = x[10]).
-__device__ __forceinline__ float closure_mlp(const DevPhys &dph, const float x_raw[11], float *buf, int lane) {
-  const __nv_bfloat16 *W = static_cast<const __nv_bfloat16 *>(dph.cw);
-  const float *sc = dph.cscale;
-  float x[11];
-#pragma unroll
-  for (int c = 0; c < 11; ++c) x[c] = (x_raw[c] - sc[c]) / sc[11 + c];
-  const __nv_bfloat16 *W1 = W, *b1 = W1 + 64 * 11, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
-                      *b3 = W3 + 64 * 64, *w4 = b3 + 64, *b4 = w4 + 64;
-  float *hA = buf, *hB = buf + 64;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int n = lane + 32 * r;
-    float a = __bfloat162float(b1[n]);
-#pragma unroll
-    for (int c = 0; c < 11; ++c) a = fmaf(__bfloat162float(W1[n * 11 + c]), x[c], a);
-    hA[n] = 0.5f * a * (1.f + erff(a * 0.70710678118654752f));
-  }
-  __syncwarp();
-  const __nv_bfloat16 *Ws[2] = {W2, W3}, *bs[2] = {b2, b3};
-  float *hin = hA, *hout = hB;
-#pragma unroll
-  for (int layer = 0; layer < 2; ++layer) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int n = lane + 32 * r;
-      float a = __bfloat162float(bs[layer][n]);
-      for (int c = 0; c < 64; ++c) a = fmaf(__bfloat162float(Ws[layer][n * 64 + c]), hin[c], a);
-      hout[n] = 0.5f * a * (1.f + erff(a * 0.70710678118654752f));
-    }
-    __syncwarp();
-    float *t = hin;
-    hin = hout;
-    hout = t;
-  }
-  float z = __bfloat162float(w4[lane]) * hin[lane] + __bfloat162float(w4[lane + 32]) * hin[lane + 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-  z += __bfloat162float(b4[0]);
-  const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
-  __syncwarp();
-  return sc[22] * x_raw[10] * x_raw[10] * sp;
-}
-
-// Viscous flux F_v[j][v] (j = direction) of state q with gradient G[j*5 + v] = dQ_v/dx_j.
-template <typename T>
-__device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const PhysT<T> &ph, const Visc<T> &vc,
-                                             T Fv[3][5]) {
-  const T ri = ph.one / q[0];
-  const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-  const T eo = q[4] * ri;
-  T du[3][3];   // du[i][j] = du_i/dx_j
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) du[i][j] = (G[j * 5 + 1 + i] - u[i] * G[j * 5]) * ri;
-  T dT[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-    dT[j] = ph.cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri - (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j]));
-  const T lam = vc.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    T t[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      t[i] = vc.mu * (du[i][j] + du[j][i]);
-      if (i == j) t[i] = t[i] + lam;
-    }
-    Fv[j][0] = ph.zero;
-    Fv[j][1] = t[0];
-    Fv[j][2] = t[1];
-    Fv[j][3] = t[2];
-    Fv[j][4] = u[0] * t[0] + u[1] * t[1] + u[2] * t[2] + vc.kappa * dT[j];
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// 1. Solution traces.  Thread per (element, face, flux point).
-// ------------------------------------------------------------------------------------------
-template <int N, typename T>
-__device__ __forceinline__ void interp_body(int64_t t, const T *__restrict__ Q, const int32_t *__restrict__ ef,
-                                            T *__restrict__ Qtr, int64_t E) {
-  constexpr int Np = N * N * N, Nf = N * N;
-  if (t >= E * 6 * Nf) return;
-  const int r = (int)(t % Nf);
-  const int64_t eff = t / Nf;
-  const int f = (int)(eff % 6);
-  const int64_t e = eff / 6;
-  const BasisT<T> &B = cbasis<T>(N);
-  const T *l = (f & 1) ? B.lp : B.lm;
-  int base, sd;
-  face_line<N>(f, r, base, sd);
-  const T *q = Q + e * Np * 5;
-  Dot<T> acc[5];
-#pragma unroll
-  for (int c = 0; c < N; ++c) {
-    const T lc = l[c];
-    const T *qc = q + (base + c * sd) * 5;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v].add(lc, qc[v]);
-  }
-  const int packed = ef[eff];
-  const int64_t I = packed >> 4;
-  const int side = (packed >> 3) & 1;
-  const int slot = slot_of(packed & 7, r % N, r / N, N);
-  T *dst = Qtr + (I * 2 + side) * 5 * Nf + slot;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v].get();
-}
-
-template <int N, typename T>
-__global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restrict__ ef,
-                               T *__restrict__ Qtr, int64_t E) {
-  interp_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Q, ef, Qtr, E);
-}
-
-// ------------------------------------------------------------------------------------------
-// 2. Volume kernel.  One block per element, one thread per solution point.
-// ------------------------------------------------------------------------------------------
-template <int N>
-constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
-// Resident blocks the register budget must allow (smem allows at least this many).
-template <int N>
-constexpr int volume_min_blocks() { return volume_threads<N>() <= 128 ? 3 : (volume_threads<N>() <= 256 ? 2 : 1); }
-
-// Shared-memory values (of T) one element needs in the volume kernel.
-template <int N>
-__host__ __device__ constexpr int volume_smem_values() { return 35 * N * N * N + 30 * N * N; }
-
-// One element e handled by `nth` threads of the block (thread index tid in [0, nth)); every
-// thread of the block calls this together (it contains block barriers); inactive sub-blocks
-// (active = false) only take part in the barriers.
-template <int N, typename T>
-__device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool active, double *sm_raw,
-                                            const T *__restrict__ Q, const T *__restrict__ metrics,
-                                            const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
-                                            const T *__restrict__ liftfac, T *__restrict__ Gtr,
-                                            T *__restrict__ Rpart, const DevPhys &dph,
-                                            const double *__restrict__ hel, float *__restrict__ nu_out) {
-  constexpr int Np = N * N * N, Nf = N * N;
-  T *sm = reinterpret_cast<T *>(sm_raw);
-  T *sQ = sm;                 // [5][Np]
-  T *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
-  T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
-  T *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
-  const PhysT<T> &ph = phys_of<T>(dph);
-  const BasisT<T> &B = cbasis<T>(N);
-  const bool viscous = dph.viscous != 0;
-  if (active)
-    for (int t = tid; t < 5 * Np; t += nth) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
-  if (viscous && active) {
-    for (int t = tid; t < 6 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
-      const int packed = ef[e * 6 + f];
-      const int64_t I = packed >> 4;
-      const int side = (packed >> 3) & 1;
-      const int slot = slot_of(packed & 7, r % N, r / N, N);
-      const T *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
-      const T *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = ph.half * (oth[v * Nf] - own[v * Nf]);
-    }
-  }
-  __syncthreads();
-  const bool pt = active && tid < Np;
-  const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
-  T S[9], invJ, q[5], H[3][5], G[15];
-  if (pt) {
-    const T *met = metrics + e * 10 * Np + m;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
-    invJ = met[9 * Np];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) q[v] = sQ[v * Np + m];
-    {
-      // Inviscid flux F_j.
-      const T ri = ph.one / q[0];
-      const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-      const T p = ph.gm1 * (q[4] - ph.half * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        H[jj][0] = q[1 + jj];
-        H[jj][1] = q[1] * u[jj];
-        H[jj][2] = q[2] * u[jj];
-        H[jj][3] = q[3] * u[jj];
-        H[jj][1 + jj] = H[jj][1 + jj] + p;
-        H[jj][4] = (q[4] + p) * u[jj];
-      }
-    }
-    if (viscous) {
-      T gu[3][5], gc[3][5];
-      const T nhm[3] = {-B.hm[i], -B.hm[j], -B.hm[k]};
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T *sq = sQ + v * Np;
-        Dot<T> a0, a1, a2;
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-          a0.add(B.D[i * N + a], sq[a + N * j + N * N * k]);
-          a1.add(B.D[j * N + a], sq[i + N * a + N * N * k]);
-          a2.add(B.D[k * N + a], sq[i + N * j + N * N * a]);
-        }
-        gu[0][v] = a0.get();
-        gu[1][v] = a1.get();
-        gu[2][v] = a2.get();
-        a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
-        a0.add(B.hp[i], sdQ[(1 * 5 + v) * Nf + j + N * k]);
-        a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
-        a1.add(B.hp[j], sdQ[(3 * 5 + v) * Nf + i + N * k]);
-        a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
-        a2.add(B.hp[k], sdQ[(5 * 5 + v) * Nf + i + N * j]);
-        gc[0][v] = a0.get();
-        gc[1][v] = a1.get();
-        gc[2][v] = a2.get();
-      }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          Dot<T> du, dc;
-          du.add(s0, gu[0][v]);
-          du.add(s1, gu[1][v]);
-          du.add(s2, gu[2][v]);
-          dc.add(s0, gc[0][v]);
-          dc.add(s1, gc[1][v]);
-          dc.add(s2, gc[2][v]);
-          sG[(jj * 5 + v) * Np + m] = du.get();
-          G[jj * 5 + v] = dc.get();
-        }
-      }
-    }
-  }
-  T rho_nu = ph.zero;
-  if (viscous && dph.closure) {
-    // Eddy-viscosity closure: quadrature-weighted element mean of the corrected velocity
-    // gradient, then one warp evaluates the network (BF16 weights, FP32 accumulation).
-    float *red = reinterpret_cast<float *>(sm + volume_smem_values<N>());   // [10][Np] + 129
-    if (pt) {
-      const double ri = 1.0 / to_double(q[0]);
-      const double w = (double)B.w[i] * B.w[j] * B.w[k] / to_double(invJ);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const double dudx = (to_double(G[b * 5 + 1 + a]) - to_double(q[1 + a]) * ri * to_double(G[b * 5])) * ri;
-          red[(a * 3 + b) * Np + m] = (float)(w * dudx);
-        }
-      red[9 * Np + m] = (float)w;
-    }
-    __syncthreads();
-    if (active && tid < 32) {
-      float acc[10];
-#pragma unroll
-      for (int c = 0; c < 10; ++c) {
-        float sacc = 0.f;
-        for (int mm = tid; mm < Np; mm += 32) sacc += red[c * Np + mm];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        acc[c] = sacc;
-      }
-      float x[11];
-      float ss = 0.f;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) x[c] = acc[c] / acc[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const float sab = 0.5f * (x[a * 3 + b] + x[b * 3 + a]);
-          ss += sab * sab;
-        }
-      x[9] = sqrtf(2.f * ss);
-      x[10] = (float)(hel[e] / N);
-      const float nu = closure_mlp(dph, x, red + 10 * Np + 1, tid);
-      if (tid == 0) {
-        red[10 * Np] = nu;
-        if (nu_out) nu_out[e] = nu;
-      }
-    }
-    __syncthreads();
-    if (pt) rho_nu = q[0] * from_double<T>((double)red[10 * Np]);
-  }
-  if (pt) {
-    if (viscous) {
-      T Fv[3][5];
-      viscous_flux<T>(q, G, ph, visc_with(ph, rho_nu, dph), Fv);
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) H[jj][v] -= Fv[jj][v];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Dot<T> h;
-        h.add(S[d * 3 + 0], H[0][v]);
-        h.add(S[d * 3 + 1], H[1][v]);
-        h.add(S[d * 3 + 2], H[2][v]);
-        sH[(d * 5 + v) * Np + m] = h.get();
-      }
-  }
-  __syncthreads();
-  if (viscous && active) {
-    // Gradient traces: uncorrected gradient interpolated to the face + eta * own lifting.
-    for (int t = tid; t < 6 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
-      const T *l = (f & 1) ? B.lp : B.lm;
-      int base, sd;
-      face_line<N>(f, r, base, sd);
-      const int packed = ef[e * 6 + f];
-      const int64_t I = packed >> 4;
-      const int side = (packed >> 3) & 1;
-      const int slot = slot_of(packed & 7, r % N, r / N, N);
-      T *dst = Gtr + (I * 2 + side) * 15 * Nf + slot;
-      const T *lf = liftfac + (e * 6 + f) * 3 * Nf + r;
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T lj = ph.eta * lf[jj * Nf];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const T *sg = sG + (jj * 5 + v) * Np + base;
-          Dot<T> acc;
-#pragma unroll
-          for (int c = 0; c < N; ++c) acc.add(l[c], sg[c * sd]);
-          acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
-          dst[(jj * 5 + v) * Nf] = acc.get();
-        }
-      }
-    }
-  }
-  if (active && tid < Np) {
-    const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
-    T *out = Rpart + (e * Np + m) * 5;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const T *h0 = sH + (0 * 5 + v) * Np, *h1 = sH + (1 * 5 + v) * Np, *h2 = sH + (2 * 5 + v) * Np;
-      Dot<T> acc;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        acc.add(B.Dt[i * N + a], h0[a + N * j + N * N * k]);
-        acc.add(B.Dt[j * N + a], h1[i + N * a + N * N * k]);
-        acc.add(B.Dt[k * N + a], h2[i + N * j + N * N * a]);
-      }
-      out[v] = acc.get();
-    }
-  }
-}
-
-template <int N, typename T>
-__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
-    k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
-             const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
-             DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out) {
-  extern __shared__ double sm_raw[];
-  volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr, Rpart,
-                    dph, hel, nu_out);
-}
-
-// ------------------------------------------------------------------------------------------
-// 3. Common normal flux at the flux points of two-sided interfaces (Rusanov + BR2).  The
-// inviscid part (pressure/energy recovery) is FP64 in both paths.
-// ------------------------------------------------------------------------------------------
-template <int N, typename T>
-__device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
-                                           const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if,
-                                           const DevPhys &dph, const int32_t *__restrict__ if_elem,
-                                           const float *__restrict__ nu) {
-  constexpr int Nf = N * N;
-  if (t >= n_if * Nf) return;
-  const int64_t I = t / Nf;
-  const int q = (int)(t % Nf);
-  const PhysT<T> &ph = phys_of<T>(dph);
-  T qL[5], qR[5], nT[3];
-  const T nn = normals[(I * 4 + 3) * Nf + q];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    qL[v] = Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q];
-    qR[v] = Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q];
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) nT[c] = normals[(I * 4 + c) * Nf + q];
-  T fL[5], fR[5], sL, sR;
-  normal_inviscid(qL, nT, nn, dph, fL, sL);
-  normal_inviscid(qR, nT, nn, dph, fR, sR);
-  const T hl = ph.half * fmax(sL, sR);
-  T F[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = ph.half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
-  if (dph.viscous) {
-    T qc[5], G[15];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qc[v] = ph.half * (qL[v] + qR[v]);
-#pragma unroll
-    for (int c = 0; c < 15; ++c)
-      G[c] = ph.half * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
-    T rho_nu = ph.zero;
-    if (dph.closure) rho_nu = qc[0] * from_double<T>(0.5 * ((double)nu[if_elem[2 * I]] + (double)nu[if_elem[2 * I + 1]]));
-    T Fv[3][5];
-    viscous_flux<T>(qc, G, ph, visc_with(ph, rho_nu, dph), Fv);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
-  }
-#pragma unroll
-  for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
-}
-
-template <int N, typename T>
-__global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
-                             const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph,
-                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu) {
-  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu);
-}
-
-// ------------------------------------------------------------------------------------------
-// 3b. Boundary faces.  Side 0 of a boundary interface is the element; its side-1 slot holds
-// 2 Q^I - Q- so that the volume kernel's (other - own)/2 equals Q^I - Q- for the BR2 jump.
-// Boundary states are FP64 in both paths.
-// ------------------------------------------------------------------------------------------
-// Ghost state (for the Rusanov flux) and boundary common solution Q^I from the interior trace.
-__device__ void boundary_states(const double qm[5], const double n[3], double nn, const fr_bc &bc,
-                                const DevPhys &ph, double ghost[5], double qi[5]) {
-  const double g = ph.gamma, Rg = ph.R;
-  const double ri = 1.0 / qm[0];
-  const double u[3] = {qm[1] * ri, qm[2] * ri, qm[3] * ri};
-  const double p = (g - 1.0) * (qm[4] - 0.5 * (qm[1] * u[0] + qm[2] * u[1] + qm[3] * u[2]));
-  if (bc.kind == FR_BC_DIRICHLET) {
-    for (int v = 0; v < 5; ++v) ghost[v] = qi[v] = bc.params[v];
-    return;
-  }
-  if (bc.kind == FR_BC_WALL_ISOTHERMAL) {
-    ghost[0] = qm[0]; ghost[1] = -qm[1]; ghost[2] = -qm[2]; ghost[3] = -qm[3]; ghost[4] = qm[4];
-    qi[0] = qm[0]; qi[1] = qi[2] = qi[3] = 0.0;
-    qi[4] = qm[0] * Rg * bc.params[0] / (g - 1.0);
-    return;
-  }
-  const double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
-  const double un = u[0] * nh[0] + u[1] * nh[1] + u[2] * nh[2];
-  const double c = sqrt(g * p * ri);
-  const double Rp = un + 2.0 * c / (g - 1.0);          // outgoing Riemann invariant
-  double rb, ub[3], pb;
-  if (bc.kind == FR_BC_CHAR_OUTFLOW) {
-    pb = bc.params[0];
-    const double sent = p / pow(qm[0], g);
-    rb = pow(pb / sent, 1.0 / g);
-    const double unb = Rp - 2.0 * sqrt(g * pb / rb) / (g - 1.0);
-    for (int c3 = 0; c3 < 3; ++c3) ub[c3] = u[c3] + (unb - un) * nh[c3];
-  } else {  // FR_BC_CHAR_INFLOW: total pressure, total temperature, direction
-    const double p0 = bc.params[0], T0 = bc.params[1];
-    double d[3] = {bc.params[2], bc.params[3], bc.params[4]};
-    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    for (int c3 = 0; c3 < 3; ++c3) d[c3] /= dn;
-    const double a = nh[0] * d[0] + nh[1] * d[1] + nh[2] * d[2];
-    const double k = 2.0 / (g - 1.0);
-    const double A = a * a + k, B = -2.0 * a * Rp, C = Rp * Rp - k * k * g * Rg * T0;
-    const double V = (-B + sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
-    const double cp = g * Rg / (g - 1.0);
-    const double Tb = T0 - V * V / (2.0 * cp);
-    pb = p0 * pow(Tb / T0, g / (g - 1.0));
-    rb = pb / (Rg * Tb);
-    for (int c3 = 0; c3 < 3; ++c3) ub[c3] = V * d[c3];
-  }
-  qi[0] = rb;
-  qi[1] = rb * ub[0];
-  qi[2] = rb * ub[1];
-  qi[3] = rb * ub[2];
-  qi[4] = pb / (g - 1.0) + 0.5 * rb * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-  for (int v = 0; v < 5; ++v) ghost[v] = qi[v];
-}
-
-template <int N, typename T>
-__device__ __forceinline__ void bc_prepare_body(int64_t t, T *__restrict__ Qtr, const T *__restrict__ normals,
-                                                const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
-                                                int64_t first, int64_t count, const DevPhys &ph) {
-  constexpr int Nf = N * N;
-  if (t >= count * Nf) return;
-  const int64_t I = first + t / Nf;
-  const int q = (int)(t % Nf);
-  double qm[5], n[3], gh[5], qi[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) n[c] = to_double(normals[(I * 4 + c) * Nf + q]);
-  boundary_states(qm, n, to_double(normals[(I * 4 + 3) * Nf + q]), bcs[if_bc[I]], ph, gh, qi);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) Qtr[(I * 2 + 1) * 5 * Nf + v * Nf + q] = from_double<T>(2.0 * qi[v] - qm[v]);
-}
-
-template <int N, typename T>
-__global__ void k_bc_prepare(T *__restrict__ Qtr, const T *__restrict__ normals,
-                             const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs,
-                             int64_t first, int64_t count, DevPhys ph) {
-  bc_prepare_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, normals, if_bc, bcs, first, count, ph);
-}
-
-template <int N, typename T>
-__device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
-                                             const T *__restrict__ normals, const int32_t *__restrict__ if_bc,
-                                             const fr_bc *__restrict__ bcs, T *__restrict__ FI, int64_t first,
-                                             int64_t count, const DevPhys &dph,
-                                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu) {
-  constexpr int Nf = N * N;
-  if (t >= count * Nf) return;
-  const int64_t I = first + t / Nf;
-  const int q = (int)(t % Nf);
-  double qm[5], n[3], gh[5], qi[5];
-  T nT[3];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) qm[v] = to_double(Qtr[(I * 2 + 0) * 5 * Nf + v * Nf + q]);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    nT[c] = normals[(I * 4 + c) * Nf + q];
-    n[c] = to_double(nT[c]);
-  }
-  const double nn = to_double(normals[(I * 4 + 3) * Nf + q]);
-  boundary_states(qm, n, nn, bcs[if_bc[I]], dph, gh, qi);
-  double fL[5], fR[5], sL, sR;
-  normal_inviscid(qm, n, nn, dph.gamma, fL, sL);
-  normal_inviscid(gh, n, nn, dph.gamma, fR, sR);
-  const double lam = fmax(sL, sR);
-  T F[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]));
-  if (dph.viscous) {
-    const PhysT<T> &ph = phys_of<T>(dph);
-    T G[15], qiT[5];
-#pragma unroll
-    for (int c = 0; c < 15; ++c) G[c] = Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qiT[v] = from_double<T>(qi[v]);
-    T rho_nu = ph.zero;
-    if (dph.closure) rho_nu = qiT[0] * from_double<T>((double)nu[if_elem[2 * I]]);
-    T Fv[3][5];
-    viscous_flux<T>(qiT, G, ph, visc_with(ph, rho_nu, dph), Fv);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
-  }
-#pragma unroll
-  for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
-}
-
-template <int N, typename T>
-__global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
-                          const int32_t *__restrict__ if_bc, const fr_bc *__restrict__ bcs, T *__restrict__ FI,
-                          int64_t first, int64_t count, DevPhys dph, const int32_t *__restrict__ if_elem,
-                          const float *__restrict__ nu) {
-  bc_flux_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, if_bc, bcs, FI, first, count,
-                     dph, if_elem, nu);
-}
-
-// ------------------------------------------------------------------------------------------
-// 4. Correction by the common flux, scaling, and output / RK44 stage update (FP64).
-// ------------------------------------------------------------------------------------------
-template <int N, typename T>
-__device__ __forceinline__ void correct_body(int64_t t, const T *__restrict__ Rpart, const T *__restrict__ FI,
-                                             const int32_t *__restrict__ ef, const T *__restrict__ metrics,
-                                             int64_t E, int mode, int stage, double dt, double *__restrict__ Rout,
-                                             double *__restrict__ Q, T *__restrict__ Qc, double *__restrict__ Un,
-                                             T *__restrict__ Unc, double *__restrict__ acc, int *__restrict__ flag,
-                                             const DevPhys &dph) {
-  constexpr int Np = N * N * N, Nf = N * N;
-  if (t >= E * Np) return;
-  const int64_t e = t / Np;
-  const int m = (int)(t % Np), i = m % N, j = (m / N) % N, k = m / (N * N);
-  const BasisT<T> &B = cbasis<T>(N);
-  const PhysT<T> &ph = phys_of<T>(dph);
-  Dot<T> r[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) r[v].add(ph.one, Rpart[t * 5 + v]);
-  // Faces: (weight, local flux point (a, b)).
-  const int fa[6] = {j, j, i, i, i, i};
-  const int fb[6] = {k, k, k, k, j, j};
-  const T wts[6] = {B.hm[i], B.hp[i], B.hm[j], B.hp[j], B.hm[k], B.hp[k]};
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    const int packed = ef[e * 6 + f];
-    const int64_t I = packed >> 4;
-    const int side = (packed >> 3) & 1;
-    const int slot = slot_of(packed & 7, fa[f], fb[f], N);
-    const T w = side ? -wts[f] : wts[f];
-    const T *src = FI + I * 5 * Nf + slot;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) r[v].add(w, src[v * Nf]);
-  }
-  const T s = -metrics[(e * 10 + 9) * Np + m];
-  double rd[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) rd[v] = to_double(r[v].get() * s);
-  if (mode == MODE_RESIDUAL) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];
-    return;
-  }
-  const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-  const double anext[3] = {0.5, 0.5, 1.0};
-  bool bad = false;
-  if constexpr (std::is_same<T, df32>::value) {
-    // Mixed path: acc and U_n are FP64; the next stage state, read only by the element
-    // kernels, is formed in double-float from the df32 copy of U_n.
-    const T adt = from_double<T>(stage < 3 ? anext[stage] * dt : 0.0);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const int64_t o = t * 5 + v;
-      if (stage < 3) {
-        acc[o] = fma(bcoef[stage] * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
-        Qc[o] = Unc[o] + adt * (r[v].get() * s);
-      } else {
-        const double nv = fma(bcoef[3] * dt, rd[v], Un[o] + acc[o]);
-        Un[o] = nv;
-        Q[o] = nv;
-        const T nc = from_double<T>(nv);
-        Unc[o] = nc;
-        Qc[o] = nc;
-        bad |= !isfinite(nv);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const int64_t o = t * 5 + v;
-      const double un = Un[o];
-      if (stage < 3) {
-        const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
-        acc[o] = a_;
-        Q[o] = un + anext[stage] * dt * rd[v];
-      } else {
-        const double nv = un + acc[o] + bcoef[3] * dt * rd[v];
-        Un[o] = nv;
-        Q[o] = nv;
-        bad |= !isfinite(nv);
-      }
-    }
-  }
-  if (bad) atomicOr(flag, 1);
-}
-
-template <int N, typename T>
-__global__ void k_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef,
-                          const T *__restrict__ metrics, int64_t E, int mode, int stage, double dt,
-                          double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
-                          double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
-                          int *__restrict__ flag, DevPhys dph) {
-  correct_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Rpart, FI, ef, metrics, E, mode, stage, dt, Rout,
-                     Q, Qc, Un, Unc, acc, flag, dph);
-}
 
 // Copies of the FP64 state in the compute type (mixed path): the stage state and U_n.
 __global__ void k_state_to_df(const double *__restrict__ Q, df32 *__restrict__ Qc, df32 *__restrict__ Unc,
@@ -881,42 +62,59 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   const T *met = reinterpret_cast<const T *>(m.metrics), *lift = reinterpret_cast<const T *>(m.liftfac);
   const T *nrm = reinterpret_cast<const T *>(m.normals);
   T *Qc = m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr;
+  const bool tri = m.if_tri != nullptr;
+  cudaError_t err;
   {
     const int64_t n = E * 6 * Nf;
     FR_EV_BEGIN(0);
-    k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
+    if (n > 0) k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
+    if ((err = launch_prism_phase(m, ph, 0, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
-    if (nb > 0)
+    if (nb > 0 && !tri)
       k_bc_prepare<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, nrm, m.if_bc, m.bcs, m.n_interior,
                                                                       m.n_if - m.n_interior, ph);
+    if (nb > 0 && tri)
+      k_bc_prepare_tri<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, nrm, m.if_bc, m.bcs, m.n_interior,
+                                                                          m.n_if - m.n_interior, ph, m.if_tri);
     FR_EV_END(0);
   }
   {
     const int threads = volume_threads<N>();
     const size_t smem = sizeof(T) * (35 * Np + 30 * Nf) + (ph.closure ? sizeof(float) * (10 * Np + 1 + 128) : 0);
-    cudaError_t err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
-    k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu);
+    if (E > 0)
+      k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu);
+    if ((err = launch_prism_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(1);
   }
   {
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
-    if (n > 0)
+    if (n > 0 && !tri)
       k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu);
+    if (n > 0 && tri)
+      k_iface_flux_tri<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph,
+                                                                         m.if_elem, m.nu, m.if_tri);
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
-    if (nb > 0)
+    if (nb > 0 && !tri)
       k_bc_flux<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, m.if_bc, m.bcs, FI, m.n_interior,
                                                                    m.n_if - m.n_interior, ph, m.if_elem, m.nu);
+    if (nb > 0 && tri)
+      k_bc_flux_tri<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, m.if_bc, m.bcs, FI,
+                                                                       m.n_interior, m.n_if - m.n_interior, ph,
+                                                                       m.if_elem, m.nu, m.if_tri);
     FR_EV_END(2);
   }
   {
     const int64_t n = E * Np;
     FR_EV_BEGIN(3);
-    k_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Rpart, FI, m.ef, met, E, mode, stage, dt, Rout, m.Q,
-                                                                 Qc, m.Un, reinterpret_cast<T *>(m.Unc), m.acc,
-                                                                 m.flag, ph);
+    if (n > 0)
+      k_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Rpart, FI, m.ef, met, E, mode, stage, dt, Rout,
+                                                                   m.Q, Qc, m.Un, reinterpret_cast<T *>(m.Unc),
+                                                                   m.acc, m.flag, ph);
+    if ((err = launch_prism_phase(m, ph, 3, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(3);
   }
   return cudaGetLastError();
@@ -945,7 +143,7 @@ cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int s
 
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st) {
   if (!m.mixed) return cudaSuccess;
-  const int64_t n = m.E * m.Np * 5;
+  const int64_t n = (m.E * m.Np + m.Ep * m.Npp) * 5;
   k_state_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m.Q, reinterpret_cast<df32 *>(m.Qc),
                                                              reinterpret_cast<df32 *>(m.Unc), n);
   return cudaGetLastError();
@@ -953,8 +151,10 @@ cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st) {
 
 template <int N>
 static cudaError_t max_dt_impl(const DevMesh &m, const DevPhys &ph, double cfl, double *d_out, cudaStream_t st) {
-  k_elem_dt<N><<<(unsigned)((m.E + 127) / 128), 128, 0, st>>>(m.Q, m.h, m.E, ph.gamma, cfl, m.dtbuf);
-  k_min_reduce<<<1, 1024, 0, st>>>(m.dtbuf, m.E, d_out);
+  if (m.E > 0) k_elem_dt<N><<<(unsigned)((m.E + 127) / 128), 128, 0, st>>>(m.Q, m.h, m.E, ph.gamma, cfl, m.dtbuf);
+  cudaError_t err = launch_prism_dt(m, ph, cfl, st);
+  if (err != cudaSuccess) return err;
+  k_min_reduce<<<1, 1024, 0, st>>>(m.dtbuf, m.E + m.Ep, d_out);
   return cudaGetLastError();
 }
 
@@ -968,116 +168,6 @@ cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, doubl
     case 7: return max_dt_impl<7>(m, ph, cfl, d_out, st);
     case 8: return max_dt_impl<8>(m, ph, cfl, d_out, st);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// Batched persistent stage: one cooperative launch runs every phase of one RK stage for all
-// cases of a ragged ensemble.  Phases are separated by a grid barrier whose waits are bounded:
-// a wait that exceeds the spin limit sets the error word and every block returns.
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ bool batch_grid_sync(BatchSync *sy, long long limit) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = &sy->bar_gen;
-    volatile int *err = &sy->err;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(&sy->bar_count, 1u) == gridDim.x - 1) {
-      atomicExch(&sy->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&sy->bar_gen, 1u);
-    } else {
-      long long it = 0;
-      while (*gen == g) {
-        if (*err) break;
-        if (++it > limit) {
-          atomicExch(&sy->err, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int *)&sy->err == 0;
-}
-
-template <typename T, int N>
-__device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase &c, const BatchLaunch &L,
-                                           double *smem) {
-  const DevMesh &m = c.m;
-  const T *Qin = reinterpret_cast<const T *>(m.mixed ? m.Qc : m.Q);
-  T *Qtr = reinterpret_cast<T *>(m.Qtr), *Gtr = reinterpret_cast<T *>(m.Gtr), *FI = reinterpret_cast<T *>(m.FI);
-  T *Rpart = reinterpret_cast<T *>(m.Rpart);
-  const T *met = reinterpret_cast<const T *>(m.metrics), *lift = reinterpret_cast<const T *>(m.liftfac);
-  const T *nrm = reinterpret_cast<const T *>(m.normals);
-  switch (tk.kind) {
-    case TASK_INTERP:
-      interp_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qin, m.ef, Qtr,
-                        m.E);
-      break;
-    case TASK_BC_PREPARE:
-      bc_prepare_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, nrm,
-                            m.if_bc, m.bcs, m.n_interior, m.n_if - m.n_interior, c.ph);
-      break;
-    case TASK_VOLUME: {
-      // Sub-blocks of nth threads, one element each; threads past the last full sub-block idle.
-      const int tpe = ((N * N * N + 31) / 32) * 32;
-      const int nth = tpe >= (int)blockDim.x ? (int)blockDim.x : tpe;
-      const int epb = (int)blockDim.x / nth;
-      const int le = (int)threadIdx.x / nth;
-      const int tid = (int)threadIdx.x % nth;
-      const int64_t e = tk.begin + le;
-      const bool active = le < epb && e < tk.end;
-      volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * volume_smem_values<N>(), Qin, met,
-                        m.ef, Qtr, lift, Gtr, Rpart, c.ph, m.h, nullptr);
-      break;
-    }
-    case TASK_IFACE:
-      iface_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm, FI,
-                       m.n_interior, c.ph, m.if_elem, m.nu);
-      break;
-    case TASK_BC_FLUX:
-      bc_flux_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm,
-                         m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph, m.if_elem, m.nu);
-      break;
-    case TASK_CORRECT:
-      correct_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Rpart, FI, m.ef,
-                         met, m.E, MODE_RK, L.stage, L.dts[tk.cs], nullptr, m.Q,
-                         m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr, m.Un, reinterpret_cast<T *>(m.Unc), m.acc,
-                         &L.sync->nonfinite, c.ph);
-      break;
-  }
-}
-
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) k_batch_stage(BatchLaunch L) {
-  extern __shared__ double smem[];
-  __shared__ int s_task;
-  if (L.debug_skip_block == (int)blockIdx.x) return;     // never arrives: the others time out
-  for (int ph = 0; ph < L.n_phases; ++ph) {
-    if (ph > 0 && !batch_grid_sync(L.sync, L.spin_limit)) return;
-    const int t0 = L.phase_begin[ph], t1 = L.phase_begin[ph + 1];
-    while (true) {
-      __syncthreads();
-      if (threadIdx.x == 0) s_task = t0 + (int)atomicAdd(&L.sync->counters[ph], 1u);
-      __syncthreads();
-      const int ti = s_task;
-      if (ti >= t1) break;
-      const BatchTask tk = L.tasks[ti];
-      const BatchCase &c = L.cases[tk.cs];
-      switch (c.m.N) {
-        case 2: batch_task<T, 2>(tk, c, L, smem); break;
-        case 3: batch_task<T, 3>(tk, c, L, smem); break;
-        case 4: batch_task<T, 4>(tk, c, L, smem); break;
-        case 5: batch_task<T, 5>(tk, c, L, smem); break;
-        case 6: batch_task<T, 6>(tk, c, L, smem); break;
-        case 7: if (BLOCK >= 352) batch_task<T, 7>(tk, c, L, smem); break;
-        case 8: if (BLOCK >= 512) batch_task<T, 8>(tk, c, L, smem); break;
-      }
-    }
   }
 }
 
@@ -1110,31 +200,24 @@ size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed) {
   return best;
 }
 
-template <typename T, int BLOCK>
-static cudaError_t batch_launch_impl(const BatchLaunch &L, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_stage<T, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  BatchLaunch arg = L;
-  void *args[] = {&arg};
-  return cudaLaunchCooperativeKernel((const void *)k_batch_stage<T, BLOCK>, dim3(grid), dim3(BLOCK), args, smem, st);
+cudaError_t upload_basis_tables() {
+  cudaError_t e = upload_basis_local();
+  if (e == cudaSuccess) e = batch_upload_m0_b256();
+  if (e == cudaSuccess) e = batch_upload_m0_b512();
+  if (e == cudaSuccess) e = batch_upload_m1_b256();
+  if (e == cudaSuccess) e = batch_upload_m1_b512();
+  return e;
 }
 
 cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st) {
-  if (block == 256) return mixed ? batch_launch_impl<df32, 256>(L, grid, smem, st) : batch_launch_impl<double, 256>(L, grid, smem, st);
-  if (block == 512) return mixed ? batch_launch_impl<df32, 512>(L, grid, smem, st) : batch_launch_impl<double, 512>(L, grid, smem, st);
+  if (block == 256) return mixed ? batch_launch_m1_b256(L, grid, smem, st) : batch_launch_m0_b256(L, grid, smem, st);
+  if (block == 512) return mixed ? batch_launch_m1_b512(L, grid, smem, st) : batch_launch_m0_b512(L, grid, smem, st);
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int BLOCK>
-static cudaError_t batch_occ_impl(size_t smem, int *nb) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_stage<T, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_batch_stage<T, BLOCK>, BLOCK, smem);
-}
-
 cudaError_t batch_occupancy(int mixed, int block, size_t smem, int *nb) {
-  if (block == 256) return mixed ? batch_occ_impl<df32, 256>(smem, nb) : batch_occ_impl<double, 256>(smem, nb);
-  if (block == 512) return mixed ? batch_occ_impl<df32, 512>(smem, nb) : batch_occ_impl<double, 512>(smem, nb);
+  if (block == 256) return mixed ? batch_occupancy_m1_b256(smem, nb) : batch_occupancy_m0_b256(smem, nb);
+  if (block == 512) return mixed ? batch_occupancy_m1_b512(smem, nb) : batch_occupancy_m0_b512(smem, nb);
   return cudaErrorInvalidValue;
 }
 

@@ -243,22 +243,124 @@ static int find_orientation(const double c0[4][3], const int r0[4][2], const dou
   return -1;
 }
 
+// Triangular faces: the vertex permutation (kTriPerm code) carrying side-1 corners onto the
+// side-0 corners at the same physical location.
+static int find_tri_orientation(const double c0[4][3], const double c1[4][3], const double shift1[3], double tol) {
+  int match[3];
+  for (int a = 0; a < 3; ++a) {
+    match[a] = -1;
+    for (int b = 0; b < 3; ++b) {
+      double dx = c1[a][0] - shift1[0] - c0[b][0], dy = c1[a][1] - shift1[1] - c0[b][1],
+             dz = c1[a][2] - shift1[2] - c0[b][2];
+      if (dx * dx + dy * dy + dz * dz <= tol * tol) { match[a] = b; break; }
+    }
+    if (match[a] < 0) return -1;
+  }
+  for (int c = 0; c < 6; ++c)
+    if (kTriPerm[c][0] == match[0] && kTriPerm[c][1] == match[1] && kTriPerm[c][2] == match[2]) return c;
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Geometry of the 6-node prism: vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1) and the same at
+// zeta = +1 (VTK wedge order); linear on the triangle times linear in zeta.
+// ------------------------------------------------------------------------------------------
+static Jac prism_map(const double (*X)[3], const double xi[3]) {
+  Jac g{};
+  const double r = xi[0], s = xi[1], z = xi[2];
+  const double lam[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
+  const double dlr[3] = {-0.5, 0.5, 0.0}, dls[3] = {-0.5, 0.0, 0.5};
+  const double lo = (1 - z) / 2, hi = (1 + z) / 2;
+  for (int v = 0; v < 6; ++v) {
+    const int t = v % 3;
+    const double wz = v < 3 ? lo : hi, dz = v < 3 ? -0.5 : 0.5;
+    const double Nv = lam[t] * wz;
+    const double dN[3] = {dlr[t] * wz, dls[t] * wz, lam[t] * dz};
+    for (int i = 0; i < 3; ++i) {
+      g.x[i] += Nv * X[v][i];
+      for (int b = 0; b < 3; ++b) g.J[i][b] += dN[b] * X[v][i];
+    }
+  }
+  return g;
+}
+
+// Prism faces: 0 zeta = -1, 1 zeta = +1 (triangles; corners with reference (r, s) below), 2 s = -1,
+// 3 r + s = 0, 4 r = -1 (quadrilaterals; corners with (sigma, zeta) coordinates below, sigma the
+// parameter of triangle edge f - 2).
+static const int kPrismFace[5][4] = {{0, 1, 2, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+static const int kTriRef[3][2] = {{-1, -1}, {1, -1}, {-1, 1}};
+static const int kQuadRef[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+// Reference normal of prism face f, scaled by the face's measure per unit parameter area.
+static const double kPrismNormal[5][3] = {{0, 0, -1}, {0, 0, 1}, {0, -1, 0}, {1, 1, 0}, {-1, 0, 0}};
+
+struct FaceGeo {
+  int nc;                // corners: 4 quadrilateral, 3 triangle
+  int64_t ids[4];
+  int ref[4][2];
+};
+
 fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &err) {
   char buf[256];
   const int p = desc->p;
   const int N = p + 1, Np = N * N * N, Nf = N * N;
   const int64_t E = desc->n_hex;
-  m.p = p; m.N = N; m.Np = Np; m.Nf = Nf; m.E = E;
+  const int64_t Ep = desc->n_prism > 0 ? desc->n_prism : 0;
+  const int64_t G = E + Ep;                 // elements: hexahedra first, then prisms
+  m.p = p; m.N = N; m.Np = Np; m.Nf = Nf; m.E = E; m.Ep = Ep;
   for (int64_t i = 0; i < E * 8; ++i) {
     if (desc->hex[i] < 0 || desc->hex[i] >= desc->n_nodes) {
       err = "hex vertex id out of range";
       return FR_EINVAL;
     }
   }
+  for (int64_t i = 0; i < Ep * 6; ++i) {
+    if (desc->prism[i] < 0 || desc->prism[i] >= desc->n_nodes) {
+      err = "prism vertex id out of range";
+      return FR_EINVAL;
+    }
+  }
+  if (G >= (int64_t(1) << 31)) {
+    err = "too many elements for this build";
+    return FR_EUNSUPPORTED;
+  }
+  TriBasis tb;
+  if (Ep > 0) {
+    if (!make_tri_basis(p, tb)) {
+      err = "internal: triangle basis construction failed";
+      return FR_EMESH;
+    }
+    m.Nt = tb.Nt;
+    m.Npp = tb.Nt * N;
+  }
+  const int Nt = m.Nt, Npp = m.Npp;
   const double(*xyz)[3] = reinterpret_cast<const double(*)[3]>(desc->xyz);
   auto elem_verts = [&](int64_t e, double X[8][3]) {
     for (int v = 0; v < 8; ++v)
       for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->hex[e * 8 + v]][i];
+  };
+  auto prism_verts = [&](int64_t ep, double X[6][3]) {
+    for (int v = 0; v < 6; ++v)
+      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->prism[ep * 6 + v]][i];
+  };
+  auto nfaces = [&](int64_t g) { return g < E ? 6 : 5; };
+  auto face_index = [&](int64_t g, int f) { return g < E ? g * 6 + f : E * 6 + (g - E) * 5 + f; };
+  auto face_geo = [&](int64_t g, int f, FaceGeo &F) {
+    if (g < E) {
+      F.nc = 4;
+      face_corners(desc->hex, g, f, F.ids, F.ref);
+      return;
+    }
+    const int64_t *pv = desc->prism + (g - E) * 6;
+    F.nc = f < 2 ? 3 : 4;
+    for (int a = 0; a < F.nc; ++a) {
+      F.ids[a] = pv[kPrismFace[f][a]];
+      F.ref[a][0] = f < 2 ? kTriRef[a][0] : kQuadRef[a][0];
+      F.ref[a][1] = f < 2 ? kTriRef[a][1] : kQuadRef[a][1];
+    }
+    if (F.nc == 3) {
+      F.ids[3] = -1;
+      F.ref[3][0] = F.ref[3][1] = 0;
+    }
   };
   // Minimum element size for tolerances.
   double hmin = 1e300;
@@ -268,18 +370,24 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     double dx = X[6][0] - X[0][0], dy = X[6][1] - X[0][1], dz = X[6][2] - X[0][2];
     hmin = std::min(hmin, std::sqrt(dx * dx + dy * dy + dz * dz));
   }
+  for (int64_t ep = 0; ep < Ep; ++ep) {
+    double X[6][3];
+    prism_verts(ep, X);
+    double dx = X[4][0] - X[0][0], dy = X[4][1] - X[0][1], dz = X[4][2] - X[0][2];
+    hmin = std::min(hmin, std::sqrt(dx * dx + dy * dy + dz * dz));
+  }
   const double tol = 1e-7 * hmin;
 
-  // Faces keyed by sorted vertex ids; sorting makes coupled faces adjacent.
-  std::vector<FaceRec> faces(E * 6);
-  for (int64_t e = 0; e < E; ++e)
-    for (int f = 0; f < 6; ++f) {
-      int64_t c[4];
-      int r[4][2];
-      face_corners(desc->hex, e, f, c, r);
-      std::array<int64_t, 4> k = {c[0], c[1], c[2], c[3]};
+  // Faces keyed by sorted vertex ids (a triangle's key carries -1 in the fourth place); sorting
+  // makes coupled faces adjacent.
+  std::vector<FaceRec> faces((size_t)(E * 6 + Ep * 5));
+  for (int64_t g = 0; g < G; ++g)
+    for (int f = 0; f < nfaces(g); ++f) {
+      FaceGeo F;
+      face_geo(g, f, F);
+      std::array<int64_t, 4> k = {F.ids[0], F.ids[1], F.ids[2], F.nc == 4 ? F.ids[3] : -1};
       std::sort(k.begin(), k.end());
-      faces[e * 6 + f] = {k, e, f};
+      faces[face_index(g, f)] = {k, g, f};
     }
   std::sort(faces.begin(), faces.end(), [](const FaceRec &a, const FaceRec &b) {
     if (a.key != b.key) return a.key < b.key;
@@ -301,7 +409,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     }
     i = j;
   }
-  // Boundary tags of the unpaired faces.
+  // Boundary tags of the unpaired faces (a triangle lists -1 as its fourth vertex).
   std::vector<std::pair<std::array<int64_t, 4>, int32_t>> btags(desc->n_bface);
   for (int64_t i = 0; i < desc->n_bface; ++i) {
     std::array<int64_t, 4> k = {desc->bface_nodes[4 * i], desc->bface_nodes[4 * i + 1],
@@ -320,8 +428,11 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
       return FR_EMESH;
     }
     Open o{{fr.e, fr.f}, it->second, {0, 0, 0}};
+    int nc = 0;
+    for (int c = 0; c < 4; ++c) nc += fr.key[c] >= 0;
     for (int c = 0; c < 4; ++c)
-      for (int i = 0; i < 3; ++i) o.cent[i] += 0.25 * xyz[fr.key[c]][i];
+      if (fr.key[c] >= 0)
+        for (int i = 0; i < 3; ++i) o.cent[i] += xyz[fr.key[c]][i] / nc;
     opens.push_back(o);
   }
   // Periodic pairing by translated centroids on a hashed grid.
@@ -396,15 +507,20 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     return FR_EUNSUPPORTED;
   }
   m.ef.assign(E * 6, -1);
+  m.ef_p.assign(Ep * 5, -1);
   m.if_bc.assign(m.n_if, -1);
   m.if_elem.assign(2 * m.n_if, -1);
+  if (Ep > 0) m.if_tri.assign(m.n_if, 0);
+  auto set_ef = [&](Side s, int32_t packed) {
+    if (s.e < E) m.ef[s.e * 6 + s.f] = packed;
+    else m.ef_p[(s.e - E) * 5 + s.f] = packed;
+  };
   std::vector<int> orient(n_int, 0);
   // Orientation of side 1 relative to side 0.
-  auto corner_xyz = [&](Side s, double c[4][3], int r[4][2]) {
-    int64_t ids[4];
-    face_corners(desc->hex, s.e, s.f, ids, r);
-    for (int k = 0; k < 4; ++k)
-      for (int i = 0; i < 3; ++i) c[k][i] = xyz[ids[k]][i];
+  auto corner_xyz = [&](Side s, double c[4][3], FaceGeo &F) {
+    face_geo(s.e, s.f, F);
+    for (int k = 0; k < F.nc; ++k)
+      for (int i = 0; i < 3; ++i) c[k][i] = xyz[F.ids[k]][i];
   };
   for (int64_t I = 0; I < n_int; ++I) {
     bool per = I >= (int64_t)pairs.size();
@@ -413,28 +529,40 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     if (per)
       for (int i = 0; i < 3; ++i) shift[i] = pshift[I - pairs.size()][i];
     double c0[4][3], c1[4][3];
-    int r0[4][2], r1[4][2];
-    corner_xyz(pr.first, c0, r0);
-    corner_xyz(pr.second, c1, r1);
-    int code = find_orientation(c0, r0, c1, r1, shift, tol);
+    FaceGeo F0, F1;
+    corner_xyz(pr.first, c0, F0);
+    corner_xyz(pr.second, c1, F1);
+    if (F0.nc != F1.nc) {
+      err = "a triangular face is paired with a quadrilateral";
+      return FR_EMESH;
+    }
+    int code = F0.nc == 4 ? find_orientation(c0, F0.ref, c1, F1.ref, shift, tol)
+                          : find_tri_orientation(c0, c1, shift, tol);
     if (code < 0) {
       err = "could not orient a matched face pair";
       return FR_EMESH;
     }
     orient[I] = code;
+    if (Ep > 0) m.if_tri[I] = F0.nc == 3 ? 1 : 0;
     m.if_elem[2 * I] = (int32_t)pr.first.e;
     m.if_elem[2 * I + 1] = (int32_t)pr.second.e;
-    m.ef[pr.first.e * 6 + pr.first.f] = (int32_t)((I << 4) | (0 << 3) | 0);
-    m.ef[pr.second.e * 6 + pr.second.f] = (int32_t)((I << 4) | (1 << 3) | code);
+    set_ef(pr.first, (int32_t)((I << 4) | (0 << 3) | 0));
+    set_ef(pr.second, (int32_t)((I << 4) | (1 << 3) | code));
   }
   for (size_t k = 0; k < bfaces.size(); ++k) {
     int64_t I = n_int + (int64_t)k;
     m.if_bc[I] = bfaces[k].second;
     m.if_elem[2 * I] = (int32_t)bfaces[k].first.e;
-    m.ef[bfaces[k].first.e * 6 + bfaces[k].first.f] = (int32_t)(I << 4);
+    if (Ep > 0) m.if_tri[I] = (bfaces[k].first.e >= E && bfaces[k].first.f < 2) ? 1 : 0;
+    set_ef(bfaces[k].first, (int32_t)(I << 4));
   }
   for (int64_t i = 0; i < E * 6; ++i)
     if (m.ef[i] < 0) {
+      err = "internal: element face without interface";
+      return FR_EMESH;
+    }
+  for (int64_t i = 0; i < Ep * 5; ++i)
+    if (m.ef_p[i] < 0) {
       err = "internal: element face without interface";
       return FR_EMESH;
     }
@@ -444,9 +572,9 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   m.metrics.assign((size_t)E * 10 * Np, 0.0);
   m.liftfac.assign((size_t)E * 6 * 3 * Nf, 0.0);
   m.normals.assign((size_t)m.n_if * 4 * Nf, 0.0);
-  m.xsol.assign((size_t)E * Np * 3, 0.0);
-  m.h.assign(E, 0.0);
-  std::vector<double> fx((size_t)E * 6 * Nf * 3);     // flux-point coordinates for the match check
+  m.xsol.assign(((size_t)E * Np + (size_t)Ep * Npp) * 3, 0.0);
+  m.h.assign(G, 0.0);
+  std::vector<double> fx((size_t)(E * 6 + Ep * 5) * Nf * 3);   // flux-point coordinates for the match check
   for (int64_t e = 0; e < E; ++e) {
     double X[8][3];
     elem_verts(e, X);
@@ -498,7 +626,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
           Jac g = trilinear(X, xi);
           double S[3][3], det;
           adjugate_rows(g.J, S, det);
-          for (int c = 0; c < 3; ++c) fx[(((size_t)e * 6 + f) * Nf + r) * 3 + c] = g.x[c];
+          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(e, f) * Nf + r) * 3 + c] = g.x[c];
           if (side == 0) {
             double nn = 0.0;
             for (int jj = 0; jj < 3; ++jj) {
@@ -510,6 +638,101 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
         }
     }
   }
+  if (Ep > 0) {
+    // Prisms: solution points (triangle node q, line point k) -> m = q + Nt k.
+    m.metrics_p.assign((size_t)Ep * 10 * Npp, 0.0);
+    for (int64_t ep = 0; ep < Ep; ++ep) {
+      const int64_t g = E + ep;
+      double X[6][3];
+      prism_verts(ep, X);
+      double vol = 0.0;
+      double *met = &m.metrics_p[(size_t)ep * 10 * Npp];
+      for (int k = 0; k < N; ++k)
+        for (int q = 0; q < Nt; ++q) {
+          const int mm = q + Nt * k;
+          const double xi[3] = {tb.r[q], tb.s[q], b.x[k]};
+          Jac jg = prism_map(X, xi);
+          double S[3][3], det;
+          adjugate_rows(jg.J, S, det);
+          if (!(det > 0.0)) {
+            snprintf(buf, sizeof buf, "non-positive Jacobian in prism %lld", (long long)ep);
+            err = buf;
+            return FR_EMESH;
+          }
+          for (int d = 0; d < 3; ++d)
+            for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Npp + mm] = S[d][jj];
+          met[9 * Npp + mm] = 1.0 / det;
+          vol += tb.wT[q] * b.w[k] * det;
+          for (int c = 0; c < 3; ++c) m.xsol[((size_t)E * Np + (size_t)ep * Npp + mm) * 3 + c] = jg.x[c];
+        }
+      m.h[g] = std::cbrt(vol);
+      for (int f = 0; f < 5; ++f) {
+        const int packed = m.ef_p[ep * 5 + f];
+        const int64_t I = packed >> 4;
+        const int side = (packed >> 3) & 1;
+        const int nq = f < 2 ? Nt : Nf;
+        for (int r = 0; r < nq; ++r) {
+          double xi[3];
+          if (f < 2) {
+            xi[0] = tb.r[r]; xi[1] = tb.s[r]; xi[2] = f == 0 ? -1.0 : 1.0;
+          } else {
+            tri_edge_point(f - 2, b.x[r % N], xi[0], xi[1]);
+            xi[2] = b.x[r / N];
+          }
+          Jac jg = prism_map(X, xi);
+          double S[3][3], det;
+          adjugate_rows(jg.J, S, det);
+          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(g, f) * Nf + r) * 3 + c] = jg.x[c];
+          if (side == 0) {
+            double nn = 0.0;
+            for (int jj = 0; jj < 3; ++jj) {
+              double v = 0.0;
+              for (int d = 0; d < 3; ++d) v += kPrismNormal[f][d] * S[d][jj];
+              m.normals[((size_t)I * 4 + jj) * Nf + r] = v;
+              nn += v * v;
+            }
+            m.normals[((size_t)I * 4 + 3) * Nf + r] = std::sqrt(nn);
+          }
+        }
+      }
+    }
+    // Operator table (prism_tab layout).
+    const PrismTab L = prism_tab(N);
+    m.ptab.assign(L.size, 0.0);
+    double *t = m.ptab.data();
+    for (int i = 0; i < Nt * Nt; ++i) {
+      t[L.Dr + i] = tb.Dr[i];
+      t[L.Ds + i] = tb.Ds[i];
+    }
+    // Own-flux correction of the quadrilateral faces (reference normals (0,-1,0), (1,1,0),
+    // (-1,0,0) for edges 0, 1, 2): Drt = Dr - LQ1 E1 + LQ2 E2, Dst = Ds + LQ0 E0 - LQ1 E1.
+    for (int i = 0; i < Nt; ++i)
+      for (int j = 0; j < Nt; ++j) {
+        long double c[3];
+        for (int e = 0; e < 3; ++e) {
+          long double acc = 0;
+          for (int a = 0; a < N; ++a) acc += (long double)tb.LQ[e][(size_t)i * N + a] * tb.E[e][(size_t)a * Nt + j];
+          c[e] = acc;
+        }
+        t[L.Drt + i * Nt + j] = (double)((long double)tb.Dr[(size_t)i * Nt + j] - c[1] + c[2]);
+        t[L.Dst + i * Nt + j] = (double)((long double)tb.Ds[(size_t)i * Nt + j] + c[0] - c[1]);
+      }
+    for (int e = 0; e < 3; ++e) {
+      for (int i = 0; i < N * Nt; ++i) t[L.E + e * N * Nt + i] = tb.E[e][i];
+      for (int i = 0; i < Nt * N; ++i) t[L.LQ + e * Nt * N + i] = tb.LQ[e][i];
+    }
+    for (int i = 0; i < N; ++i) {
+      for (int a = 0; a < N; ++a) {
+        t[L.D1 + i * N + a] = b.D[i * N + a];
+        t[L.D1t + i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
+      }
+      t[L.lm + i] = b.lm[i];
+      t[L.lp + i] = b.lp[i];
+      t[L.hm + i] = b.hm[i];
+      t[L.hp + i] = b.hp[i];
+    }
+    m.tri_slot = tb.perm;
+  }
   // Check that every side-1 flux point lands on its side-0 slot (coordinates, with shift).
   for (int64_t I = 0; I < n_int; ++I) {
     bool per = I >= (int64_t)pairs.size();
@@ -517,19 +740,19 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     double shift[3] = {0, 0, 0};
     if (per)
       for (int i = 0; i < 3; ++i) shift[i] = pshift[I - pairs.size()][i];
-    for (int bb = 0; bb < N; ++bb)
-      for (int aa = 0; aa < N; ++aa) {
-        int r = aa + N * bb;
-        int q = orient_slot(orient[I], aa, bb, N);
-        const double *x1 = &fx[(((size_t)pr.second.e * 6 + pr.second.f) * Nf + r) * 3];
-        const double *x0 = &fx[(((size_t)pr.first.e * 6 + pr.first.f) * Nf + q) * 3];
-        double dd = 0;
-        for (int c = 0; c < 3; ++c) dd += (x1[c] - shift[c] - x0[c]) * (x1[c] - shift[c] - x0[c]);
-        if (dd > 1e4 * tol * tol) {
-          err = "flux points of a matched face pair do not coincide";
-          return FR_EMESH;
-        }
+    const bool tri = Ep > 0 && m.if_tri[I];
+    const int nq = tri ? Nt : Nf;
+    for (int r = 0; r < nq; ++r) {
+      const int q = tri ? m.tri_slot[(size_t)orient[I] * Nt + r] : orient_slot(orient[I], r % N, r / N, N);
+      const double *x1 = &fx[((size_t)face_index(pr.second.e, pr.second.f) * Nf + r) * 3];
+      const double *x0 = &fx[((size_t)face_index(pr.first.e, pr.first.f) * Nf + q) * 3];
+      double dd = 0;
+      for (int c = 0; c < 3; ++c) dd += (x1[c] - shift[c] - x0[c]) * (x1[c] - shift[c] - x0[c]);
+      if (dd > 1e4 * tol * tol) {
+        err = "flux points of a matched face pair do not coincide";
+        return FR_EMESH;
       }
+    }
   }
   return FR_OK;
 }

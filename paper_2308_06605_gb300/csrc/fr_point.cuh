@@ -1,0 +1,185 @@
+// Pointwise device functions shared by the hexahedral and prismatic kernels: gas dynamics (normal
+// inviscid flux with the Rusanov wave-speed bound, viscous flux with optional eddy viscosity) and
+// the output / RK44 stage update of one solution point.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <type_traits>
+
+#include "df32.cuh"
+#include "fr_device.hpp"
+
+namespace frx {
+
+template <typename T> __device__ __forceinline__ const PhysT<T> &phys_of(const DevPhys &p);
+template <> __device__ __forceinline__ const PhysT<double> &phys_of<double>(const DevPhys &p) { return p.d; }
+template <> __device__ __forceinline__ const PhysT<df32> &phys_of<df32>(const DevPhys &p) { return p.f; }
+
+// ------------------------------------------------------------------------------------------
+// Gas dynamics (ideal gas, Stokes hypothesis, constant mu, Fourier heat flux).
+// ------------------------------------------------------------------------------------------
+// Normal inviscid flux F(q).n and (|u.n^| + c)|n|, in FP64 (pressure/energy recovery); nn = |n|.
+__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, double g,
+                                                double out[5], double &un_abs_plus_c_n) {
+  const double ri = 1.0 / q[0];
+  const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+  const double p = (g - 1.0) * (q[4] - 0.5 * (q[1] * u + q[2] * v + q[3] * w));
+  const double un = u * n[0] + v * n[1] + w * n[2];
+  out[0] = q[0] * un;
+  out[1] = q[1] * un + p * n[0];
+  out[2] = q[2] * un + p * n[1];
+  out[3] = q[3] * un + p * n[2];
+  out[4] = (q[4] + p) * un;
+  un_abs_plus_c_n = fabs(un) + sqrt(g * p * ri) * nn;      // (|u.n^| + c) |n|
+}
+
+// Double-float normal flux with the pressure recovery p = (gamma-1)(E - m.u/2) in FP64.
+__device__ __forceinline__ void normal_inviscid(const df32 q[5], const df32 n[3], df32 nn, const DevPhys &dph,
+                                                df32 out[5], df32 &un_abs_plus_c_n) {
+  const PhysT<df32> &ph = dph.f;
+  const df32 ri = ph.one / q[0];
+  const df32 u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  Dot<df32> mu, unn;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mu.add(q[1 + c], u[c]);
+    unn.add(u[c], n[c]);
+  }
+  const double pd = (dph.gamma - 1.0) * (to_double(q[4]) - 0.5 * to_double(mu.get()));
+  const df32 p = df_from(pd);
+  const df32 un = unn.get();
+  out[0] = q[0] * un;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Dot<df32> f;
+    f.add(q[1 + c], un);
+    f.add(p, n[c]);
+    out[1 + c] = f.get();
+  }
+  out[4] = (q[4] + p) * un;
+  un_abs_plus_c_n = fabs(un) + sqrt(ph.gamma * p * ri) * nn;
+}
+
+// FP64 overload with the same signature shape (the FP64 path's arithmetic).
+__device__ __forceinline__ void normal_inviscid(const double q[5], const double n[3], double nn, const DevPhys &dph,
+                                                double out[5], double &s) {
+  normal_inviscid(q, n, nn, dph.gamma, out, s);
+}
+
+// Transport coefficients of one viscous-flux evaluation (molecular, or with an eddy viscosity).
+template <typename T>
+struct Visc {
+  T mu, m2mu3, kappa;   // mu, -2 mu / 3, kappa
+};
+
+template <typename T>
+__device__ __forceinline__ Visc<T> visc_of(const PhysT<T> &ph) {
+  return Visc<T>{ph.mu, ph.m2mu3, ph.kappa};
+}
+
+// Closure: mu + rho nu_t, kappa + rho nu_t cp / Pr_t (nu_t = 0 gives the molecular values exactly).
+template <typename T>
+__device__ __forceinline__ Visc<T> visc_with(const PhysT<T> &ph, T rho_nu, const DevPhys &dph) {
+  if (!dph.closure) return visc_of(ph);
+  const T mu = ph.mu + rho_nu;
+  return Visc<T>{mu, ph.m2mu3 + from_double<T>(-2.0 / 3.0) * rho_nu, ph.kappa + from_double<T>(dph.cp_prt) * rho_nu};
+}
+
+// Viscous flux F_v[j][v] (j = direction) of state q with gradient G[j*5 + v] = dQ_v/dx_j.
+template <typename T>
+__device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const PhysT<T> &ph, const Visc<T> &vc,
+                                             T Fv[3][5]) {
+  const T ri = ph.one / q[0];
+  const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  const T eo = q[4] * ri;
+  T du[3][3];   // du[i][j] = du_i/dx_j
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) du[i][j] = (G[j * 5 + 1 + i] - u[i] * G[j * 5]) * ri;
+  T dT[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    dT[j] = ph.cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri - (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j]));
+  const T lam = vc.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t[i] = vc.mu * (du[i][j] + du[j][i]);
+      if (i == j) t[i] = t[i] + lam;
+    }
+    Fv[j][0] = ph.zero;
+    Fv[j][1] = t[0];
+    Fv[j][2] = t[1];
+    Fv[j][3] = t[2];
+    Fv[j][4] = u[0] * t[0] + u[1] * t[1] + u[2] * t[2] + vc.kappa * dT[j];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Output or RK44 stage update of solution point t (flat point index over all elements): rv is the
+// bracket of Eq. 3 at the point, s = -1/|J|.  MODE_RESIDUAL writes R; MODE_RK updates the FP64
+// registers (acc, U_n) and the stage state (FP64 Q, or its double-float copy Qc on the mixed
+// path) and ORs a non-finite result into *flag at the last stage.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int mode, int stage, double dt,
+                                             double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
+                                             double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
+                                             int *__restrict__ flag) {
+  double rd[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) rd[v] = to_double(rv[v] * s);
+  if (mode == MODE_RESIDUAL) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];
+    return;
+  }
+  const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double anext[3] = {0.5, 0.5, 1.0};
+  bool bad = false;
+  if constexpr (std::is_same<T, df32>::value) {
+    // Mixed path: acc and U_n are FP64; the next stage state, read only by the element
+    // kernels, is formed in double-float from the df32 copy of U_n.
+    const T adt = from_double<T>(stage < 3 ? anext[stage] * dt : 0.0);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t o = t * 5 + v;
+      if (stage < 3) {
+        acc[o] = fma(bcoef[stage] * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
+        Qc[o] = Unc[o] + adt * (rv[v] * s);
+      } else {
+        const double nv = fma(bcoef[3] * dt, rd[v], Un[o] + acc[o]);
+        Un[o] = nv;
+        Q[o] = nv;
+        const T nc = from_double<T>(nv);
+        Unc[o] = nc;
+        Qc[o] = nc;
+        bad |= !isfinite(nv);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t o = t * 5 + v;
+      const double un = Un[o];
+      if (stage < 3) {
+        const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
+        acc[o] = a_;
+        Q[o] = un + anext[stage] * dt * rd[v];
+      } else {
+        const double nv = un + acc[o] + bcoef[3] * dt * rd[v];
+        Un[o] = nv;
+        Q[o] = nv;
+        bad |= !isfinite(nv);
+      }
+    }
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+}  // namespace frx

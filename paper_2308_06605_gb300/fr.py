@@ -45,7 +45,8 @@ class fr_mesh_desc(C.Structure):
                 ("n_bface", C.c_int64), ("bface_nodes", C.POINTER(C.c_int64)),
                 ("bface_tag", C.POINTER(C.c_int32)),
                 ("n_bc", C.c_int32), ("bc", C.POINTER(fr_bc)),
-                ("n_periodic", C.c_int32), ("periodic", C.POINTER(fr_periodic))]
+                ("n_periodic", C.c_int32), ("periodic", C.POINTER(fr_periodic)),
+                ("n_prism", C.c_int64), ("prism", C.POINTER(C.c_int64))]
 
 
 class fr_physics(C.Structure):
@@ -61,7 +62,8 @@ class fr_batch_info(C.Structure):
 
 class fr_mesh_info(C.Structure):
     _fields_ = [("n_elem", C.c_int64), ("p", C.c_int32), ("n_pts", C.c_int32),
-                ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("device_bytes", C.c_int64)]
+                ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("device_bytes", C.c_int64),
+                ("n_prism", C.c_int64), ("n_pts_prism", C.c_int32), ("n_points", C.c_int64)]
 
 
 # Exported functions: name -> (restype, argtypes)
@@ -143,14 +145,20 @@ def probe_fma(precision: int = 0, iters: int = 20000) -> float:
 
 
 class Mesh:
-    """One FR discretisation living on the current CUDA device (owns the C-side fr_mesh)."""
+    """One FR discretisation living on the current CUDA device (owns the C-side fr_mesh).
+
+    States and residuals are [n_elem][n_pts][5] on hexahedral meshes; on meshes with prisms they
+    are [n_points][5], the hexahedral points first (see `split`).
+    """
 
     def __init__(self, desc: MeshDesc, phys: Physics, p: int, stream: int = 0):
         lib = load()
         self._lib = lib
         self._keep = []
         xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
-        hexa = np.ascontiguousarray(desc.hex, dtype=np.int64)
+        hexa = np.ascontiguousarray(np.asarray(desc.hex, dtype=np.int64).reshape(-1, 8))
+        pri = getattr(desc, "prism", None)
+        pri = np.ascontiguousarray(np.zeros((0, 6)) if pri is None else pri, dtype=np.int64).reshape(-1, 6)
         bn = np.ascontiguousarray(desc.bface_nodes, dtype=np.int64).reshape(-1, 4)
         bt = np.ascontiguousarray(desc.bface_tag, dtype=np.int32)
         bcs = (fr_bc * max(1, len(desc.bcs)))()
@@ -163,11 +171,12 @@ class Mesh:
             per[i].tag_a, per[i].tag_b = pp.tag_a, pp.tag_b
             for k in range(3):
                 per[i].t[k] = pp.t[k]
-        self._keep += [xyz, hexa, bn, bt, bcs, per]
+        self._keep += [xyz, hexa, pri, bn, bt, bcs, per]
         d = fr_mesh_desc(n_nodes=xyz.shape[0], xyz=_ptr(xyz, C.c_double), n_hex=hexa.shape[0],
                          hex=_ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
                          bface_nodes=_ptr(bn, C.c_int64), bface_tag=_ptr(bt, C.c_int32),
-                         n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per)
+                         n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per,
+                         n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64))
         ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
                         viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision)
         h = C.c_void_p()
@@ -179,16 +188,24 @@ class Mesh:
         lib.fr_mesh_query(h, C.byref(info))
         self.n_elem, self.p, self.n_pts = info.n_elem, info.p, info.n_pts
         self.n_iface, self.n_bface, self.device_bytes = info.n_iface, info.n_bface, info.device_bytes
-        self.shape = (self.n_elem, self.n_pts, 5)
+        self.n_prism, self.n_pts_prism, self.n_points = info.n_prism, info.n_pts_prism, info.n_points
+        self.shape = (self.n_elem, self.n_pts, 5) if self.n_prism == 0 else (self.n_points, 5)
 
     def _check(self, st):
         if st != FR_OK:
             raise FRError(st, self._lib.fr_last_error(self._h).decode())
 
     def solution_points(self) -> np.ndarray:
-        x = np.empty((self.n_elem, self.n_pts, 3))
+        x = np.empty(self.shape[:-1] + (3,))
         self._check(self._lib.fr_solution_points(self._h, C.c_void_p(x.ctypes.data)))
         return x
+
+    def split(self, a):
+        """Views of a [n_points][k] array as (hexahedra [n_elem][n_pts][k], prisms [n_prism][n_pts_prism][k])."""
+        nh = self.n_elem * self.n_pts
+        k = a.shape[-1]
+        flat = a.reshape(-1, k)
+        return flat[:nh].reshape(self.n_elem, self.n_pts, k), flat[nh:].reshape(self.n_prism, self.n_pts_prism, k)
 
     def set_state(self, Q):
         p, where = _data_ptr(Q)

@@ -19,6 +19,20 @@ def test_equals_hex_oracle_on_hex_meshes():
     R1 = mh.residual(Q)
     R2 = mm.residual([Q, np.zeros((0, mm.types[1].Np, 5))])[0]
     np.testing.assert_allclose(R2, R1, rtol=0, atol=1e-13 * np.abs(R1).max())
+    # The magnitude scale reduces to the hexahedral oracle's on hexahedral meshes.
+    S1 = mh.residual(Q, magnitude=True)
+    S2 = mm.residual([Q, np.zeros((0, mm.types[1].Np, 5))], magnitude=True)[0]
+    np.testing.assert_allclose(S2, S1, rtol=1e-13)
+
+
+def test_magnitude_bounds_the_residual():
+    d = I.hex_box_mesh((3, 3, 2), prisms="checker", seed=3, rotate=True, perturb=0.05)
+    ph = I.tgv_physics(Ma=0.2, Re=300.0)
+    m = MixedFR(d, ph, 3)
+    Qs = [I.tgv_state(x, Ma=0.2, perturb=1e-2) for x in m.x]
+    for R, S in zip(m.residual(Qs), m.residual(Qs, magnitude=True)):
+        assert np.all(np.abs(R) <= S * (1 + 1e-12))
+        assert np.all(S > 0)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
