@@ -95,7 +95,8 @@ typedef struct {
   double R;             /* gas constant (p = rho R T) */
   double mu;            /* dynamic viscosity (constant) */
   double Pr;            /* Prandtl number */
-  int32_t inviscid;     /* FR_RUSANOV | FR_ROE */
+  int32_t inviscid;     /* FR_RUSANOV (local Lax-Friedrichs) | FR_ROE (Roe average, Harten's entropy
+                           fix on the acoustic waves with delta = 0.1 c); FP64 on both precisions */
   int32_t viscous;      /* FR_VISC_NONE | FR_VISC_BR2 */
   double br2_eta;       /* BR2 penalty factor (number of faces, 6, by default) */
   int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED: element operators (traces, gradients,
@@ -145,8 +146,8 @@ fr_status fr_get_state(fr_mesh *mesh, double *Q, int32_t where);
 
 /*
  * fr_residual — R = dQ/dt of the current state (Eq. 3: -|J|^-1 [div_xi F^ + sum over faces and
- * flux points of div(g) (F^I_perp - F_perp)] with the DG-equivalent correction, the Rusanov
- * common flux and the BR2 viscous flux), written in the canonical layout to R (FR_HOST or
+ * flux points of div(g) (F^I_perp - F_perp)] with the DG-equivalent correction, the Rusanov or
+ * Roe common flux and the BR2 viscous flux), written in the canonical layout to R (FR_HOST or
  * FR_DEVICE).  `t` is the physical time (used by time-dependent boundary data).
  */
 fr_status fr_residual(fr_mesh *mesh, double t, double *R, int32_t where);

@@ -81,3 +81,67 @@ def rusanov(QL, QR, n, gamma):
     lam = np.maximum(np.abs(np.sum(uL * nh, axis=-1)) + sound_speed(QL, gamma),
                      np.abs(np.sum(uR * nh, axis=-1)) + sound_speed(QR, gamma))
     return 0.5 * (FL + FR) - 0.5 * (lam * nmag)[..., None] * (QR - QL)
+
+
+def roe(QL, QR, n, gamma, delta=0.1):
+    """Roe's approximate Riemann flux (Roe 1981) dotted with the area-scaled normal n of side L:
+    1/2 (F(QL) + F(QR)) . n - 1/2 |n| sum_k |lambda_k| alpha_k r_k over the waves of the Jacobian at
+    the Roe average (density-weighted velocity and total enthalpy), with Harten's entropy fix
+    |lambda| -> (lambda^2 + d^2) / (2 d) for |lambda| < d, d = delta * c~ on the acoustic waves.
+    Waves: acoustic u.n^ -/+ c with strengths (dp -/+ rho c du_n) / (2 c^2), entropy u.n^ with
+    drho - dp / c^2, shear u.n^ carrying rho (du - du_n n^)."""
+    FL = np.einsum('...jv,...j->...v', inviscid_flux(QL, gamma), n)
+    FR = np.einsum('...jv,...j->...v', inviscid_flux(QR, gamma), n)
+    return 0.5 * (FL + FR) - 0.5 * roe_dissipation(QL, QR, n, gamma, delta, absolute=True)
+
+
+def roe_dissipation(QL, QR, n, gamma, delta=0.1, absolute=True):
+    """|n| sum_k f(lambda_k) alpha_k r_k with f = |.| (entropy-fixed) or, absolute=False, the
+    identity (then the sum is A(Q~) (QR - QL) |n|, which for the Roe average equals
+    (F(QR) - F(QL)) . n: Roe's property U, used as a pin)."""
+    nmag = np.sqrt(np.sum(n * n, axis=-1))
+    nh = n / nmag[..., None]
+    rL, uL, pL = primitives(QL, gamma)
+    rR, uR, pR = primitives(QR, gamma)
+    HL = (QL[..., 4] + pL) / rL
+    HR = (QR[..., 4] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    r = sL * sR
+    u = (sL[..., None] * uL + sR[..., None] * uR) / (sL + sR)[..., None]
+    H = (sL * HL + sR * HR) / (sL + sR)
+    q2 = np.sum(u * u, axis=-1)
+    c = np.sqrt((gamma - 1.0) * (H - 0.5 * q2))
+    un = np.sum(u * nh, axis=-1)
+    dr = rR - rL
+    dp = pR - pL
+    du = uR - uL
+    dun = np.sum(du * nh, axis=-1)
+    a1 = (dp - r * c * dun) / (2.0 * c * c)
+    a2 = dr - dp / (c * c)
+    a3 = (dp + r * c * dun) / (2.0 * c * c)
+    lam1, lam2, lam3 = un - c, un, un + c
+    if absolute:
+        def fix(lam):
+            d = delta * c
+            a = np.abs(lam)
+            return np.where(a < d, (lam * lam + d * d) / (2.0 * d), a)
+        l1, l2, l3 = fix(lam1), np.abs(lam2), fix(lam3)
+    else:
+        l1, l2, l3 = lam1, lam2, lam3
+    out = np.zeros(QL.shape)
+    # acoustic waves
+    for lam, a, s in ((l1, a1, -1.0), (l3, a3, 1.0)):
+        out[..., 0] += lam * a
+        out[..., 1:4] += (lam * a)[..., None] * (u + s * c[..., None] * nh)
+        out[..., 4] += lam * a * (H + s * c * un)
+    # entropy and shear waves (both travel at u.n^)
+    shear = r[..., None] * (du - dun[..., None] * nh)
+    out[..., 0] += l2 * a2
+    out[..., 1:4] += l2[..., None] * (a2[..., None] * u + shear)
+    out[..., 4] += l2 * (a2 * 0.5 * q2 + np.sum(u * shear, axis=-1))
+    return nmag[..., None] * out
+
+
+def common_flux(kind, QL, QR, n, gamma):
+    """Inviscid common flux: kind 0 = Rusanov, 1 = Roe."""
+    return roe(QL, QR, n, gamma) if kind == 1 else rusanov(QL, QR, n, gamma)

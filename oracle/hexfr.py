@@ -350,7 +350,7 @@ class HexFR:
         Fperp = np.stack([FACE_SIGN[f] * np.einsum('qm,emv->eqv', self.Lf[f], Hhat[:, :, FACE_AXIS[f], :])
                           for f in range(6)], axis=1)              # [E][6][Nf][5]
         # Common normal flux along side L's normal.
-        FI = gas.rusanov(QL, QR, self.nL, gam)
+        FI = gas.common_flux(ph.inviscid_flux, QL, QR, self.nL, gam)
         if viscous:
             gL = gface[self.eL, self.fL]
             gR = gface[self.eR, self.fR][rows, self.perm]
@@ -365,7 +365,7 @@ class HexFR:
             e, f = self.bE[k], self.bF[k]
             n = self.nf[e, f]
             Qm = Qf[e, f]
-            Fb = gas.rusanov(Qm, ghosts[k], n, gam)
+            Fb = gas.common_flux(ph.inviscid_flux, Qm, ghosts[k], n, gam)
             if viscous:
                 # Common gradient at a boundary: the interior side's face gradient.
                 nb = nu_el[e] * bstates[k][..., 0]

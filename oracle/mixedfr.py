@@ -254,7 +254,7 @@ class MixedFR:
         for k, (tL, eL, fL, tR, eR, fR, perm) in enumerate(self.ifaces):
             qL, qR = Qf[tL][fL][eL], Qf[tR][fR][eR][perm]
             n = self.nf[tL][fL][eL]
-            F = gas.rusanov(qL, qR, n, gam)
+            F = gas.common_flux(ph.inviscid_flux, qL, qR, n, gam)
             if visc:
                 g = 0.5 * (gfaces[tL][fL][eL] + gfaces[tR][fR][eR][perm])
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(Qc_if[k], g, gam, ph.R, ph.mu, ph.Pr), n)
@@ -262,7 +262,7 @@ class MixedFR:
             Fc[tR][fR][eR][perm] = -F
         for k, (ti, e, fi, bc) in enumerate(self.bfaces):
             n = self.nf[ti][fi][e]
-            F = gas.rusanov(Qf[ti][fi][e], bst[k], n, gam)
+            F = gas.common_flux(ph.inviscid_flux, Qf[ti][fi][e], bst[k], n, gam)
             if visc:
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(bst[k], gfaces[ti][fi][e], gam, ph.R, ph.mu, ph.Pr), n)
             Fc[ti][fi][e] = F

@@ -141,7 +141,8 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   if (!(phys->gamma > 1.0) || !(phys->R > 0.0) || !(phys->mu >= 0.0) || !(phys->Pr > 0.0) ||
       !(phys->br2_eta >= 0.0))
     return fail(nullptr, FR_EINVAL, "bad physical parameters");
-  if (phys->inviscid != FR_RUSANOV) return fail(nullptr, FR_EUNSUPPORTED, "only the Rusanov flux is built");
+  if (phys->inviscid != FR_RUSANOV && phys->inviscid != FR_ROE)
+    return fail(nullptr, FR_EINVAL, "unknown inviscid flux");
   if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2)
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
   if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED)

@@ -463,13 +463,27 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) nT[c] = normals[(I * 4 + c) * Nf + q];
-  T fL[5], fR[5], sL, sR;
-  normal_inviscid(qL, nT, nn, dph, fL, sL);
-  normal_inviscid(qR, nT, nn, dph, fR, sR);
-  const T hl = ph.half * fmax(sL, sR);
   T F[5];
+  if (dph.inviscid == FR_ROE) {
+    double a[5], b[5], nd[3], Fd[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = ph.half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
+    for (int v = 0; v < 5; ++v) {
+      a[v] = to_double(qL[v]);
+      b[v] = to_double(qR[v]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nd[c] = to_double(nT[c]);
+    roe_flux(a, b, nd, to_double(nn), dph.gamma, Fd);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = from_double<T>(Fd[v]);
+  } else {
+    T fL[5], fR[5], sL, sR;
+    normal_inviscid(qL, nT, nn, dph, fL, sL);
+    normal_inviscid(qR, nT, nn, dph, fR, sR);
+    const T hl = ph.half * fmax(sL, sR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = ph.half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
+  }
   if (dph.viscous) {
     T qc[5], G[15];
 #pragma unroll
@@ -597,13 +611,20 @@ __device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qt
   }
   const double nn = to_double(normals[(I * 4 + 3) * Nf + q]);
   boundary_states(qm, n, nn, bcs[if_bc[I]], dph, gh, qi);
-  double fL[5], fR[5], sL, sR;
-  normal_inviscid(qm, n, nn, dph.gamma, fL, sL);
-  normal_inviscid(gh, n, nn, dph.gamma, fR, sR);
-  const double lam = fmax(sL, sR);
   T F[5];
+  if (dph.inviscid == FR_ROE) {
+    double Fd[5];
+    roe_flux(qm, gh, n, nn, dph.gamma, Fd);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]));
+    for (int v = 0; v < 5; ++v) F[v] = from_double<T>(Fd[v]);
+  } else {
+    double fL[5], fR[5], sL, sR;
+    normal_inviscid(qm, n, nn, dph.gamma, fL, sL);
+    normal_inviscid(gh, n, nn, dph.gamma, fR, sR);
+    const double lam = fmax(sL, sR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = from_double<T>(0.5 * (fL[v] + fR[v]) - 0.5 * lam * (gh[v] - qm[v]));
+  }
   if (dph.viscous) {
     const PhysT<T> &ph = phys_of<T>(dph);
     T G[15], qiT[5];

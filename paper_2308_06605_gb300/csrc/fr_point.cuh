@@ -68,6 +68,60 @@ __device__ __forceinline__ void normal_inviscid(const double q[5], const double 
   normal_inviscid(q, n, nn, dph.gamma, out, s);
 }
 
+// Roe's approximate Riemann flux (Roe 1981) through the area-scaled normal n (|n| = nn), FP64:
+// 1/2 (F(qL) + F(qR)).n - 1/2 |n| sum_k |lambda_k| alpha_k r_k over the waves of the Jacobian at the
+// Roe average (density-weighted velocity and total enthalpy): acoustic waves u.n^ -/+ c with
+// strengths (dp -/+ rho c du_n) / (2 c^2), entropy wave u.n^ with drho - dp / c^2, shear wave u.n^
+// carrying rho (du - du_n n^).  Harten's entropy fix on the acoustic waves: |lambda| below
+// d = 0.1 c becomes (lambda^2 + d^2) / (2 d).
+__device__ __forceinline__ void roe_flux(const double qL[5], const double qR[5], const double n[3], double nn,
+                                         double g, double F[5]) {
+  double fL[5], fR[5], sL, sR;
+  normal_inviscid(qL, n, nn, g, fL, sL);
+  normal_inviscid(qR, n, nn, g, fR, sR);
+  const double inn = 1.0 / nn;
+  const double nh[3] = {n[0] * inn, n[1] * inn, n[2] * inn};
+  const double rL = qL[0], rR = qR[0];
+  const double uL[3] = {qL[1] / rL, qL[2] / rL, qL[3] / rL}, uR[3] = {qR[1] / rR, qR[2] / rR, qR[3] / rR};
+  const double pL = (g - 1.0) * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
+  const double pR = (g - 1.0) * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
+  const double HL = (qL[4] + pL) / rL, HR = (qR[4] + pR) / rR;
+  const double sl = sqrt(rL), sr = sqrt(rR), w = 1.0 / (sl + sr);
+  const double r = sl * sr;
+  double u[3], du[3], q2 = 0.0, un = 0.0, dun = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u[c] = (sl * uL[c] + sr * uR[c]) * w;
+    du[c] = uR[c] - uL[c];
+    q2 += u[c] * u[c];
+    un += u[c] * nh[c];
+    dun += du[c] * nh[c];
+  }
+  const double H = (sl * HL + sr * HR) * w;
+  const double c2 = (g - 1.0) * (H - 0.5 * q2), c = sqrt(c2);
+  const double dp = pR - pL, dr = rR - rL;
+  const double a1 = (dp - r * c * dun) / (2.0 * c2), a2 = dr - dp / c2, a3 = (dp + r * c * dun) / (2.0 * c2);
+  const double d = 0.1 * c;
+  auto fix = [d](double lam) {
+    const double a = fabs(lam);
+    return a < d ? (lam * lam + d * d) / (2.0 * d) : a;
+  };
+  const double l1 = fix(un - c) * a1, l2 = fabs(un), l3 = fix(un + c) * a3;
+  double sh[3], ush = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sh[k] = r * (du[k] - dun * nh[k]);
+    ush += u[k] * sh[k];
+  }
+  double D[5];
+  D[0] = l1 + l2 * a2 + l3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) D[1 + k] = l1 * (u[k] - c * nh[k]) + l3 * (u[k] + c * nh[k]) + l2 * (a2 * u[k] + sh[k]);
+  D[4] = l1 * (H - c * un) + l3 * (H + c * un) + l2 * (a2 * 0.5 * q2 + ush);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * nn * D[v];
+}
+
 // Transport coefficients of one viscous-flux evaluation (molecular, or with an eddy viscosity).
 template <typename T>
 struct Visc {
