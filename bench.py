@@ -142,7 +142,7 @@ DF_FP32_FLOPS_PER_FLOP = 18.0
 class Case:
     """One mesh + state on the device, stepping with RK44 on the torch current stream."""
 
-    def __init__(self, n_edge, p, precision, dt=None):
+    def __init__(self, n_edge, p, precision, dt=None, prisms=None):
         import numpy as np
         import torch
         from paper_2308_06605_gb300 import fr, inputs as I
@@ -150,14 +150,15 @@ class Case:
         self.stream = torch.cuda.current_stream()
         phys = I.tgv_physics()
         phys.precision = 1 if precision == "mixed" else 0
-        self.mesh = fr.Mesh(I.hex_box_mesh((n_edge, n_edge, n_edge)), phys, p, stream=self.stream.cuda_stream)
+        self.mesh = fr.Mesh(I.hex_box_mesh((n_edge, n_edge, n_edge), prisms=prisms), phys, p,
+                            stream=self.stream.cuda_stream)
         x = self.mesh.solution_points()
         self.Q0 = np.ascontiguousarray(I.tgv_state(x, Ma=0.1))
         del x
         self.Qd = torch.from_numpy(self.Q0).to("cuda")
         self.mesh.set_state(self.Qd)
         self.dt = dt if dt is not None else self.mesh.max_dt(CFL)
-        self.n_pts = self.mesh.n_elem * self.mesh.n_pts
+        self.n_pts = self.mesh.n_points
         self.t = 0.0
 
     def step(self):
@@ -177,14 +178,17 @@ class Case:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    def kernels(self, steps, p):
+    def kernels(self, steps, p, prism_model=False):
         from paper_2308_06605_gb300 import perfmodel
         self.mesh.profile(True)
         for _ in range(steps):
             self.step()
         kms, kcnt = self.mesh.profile_read(4)
         self.mesh.profile(False)
-        fl, by = perfmodel.flops_per_point(p), perfmodel.bytes_per_point(p)
+        if prism_model:
+            fl, by = perfmodel.prism_flops_per_point(p), perfmodel.prism_bytes_per_point(p)
+        else:
+            fl, by = perfmodel.flops_per_point(p), perfmodel.bytes_per_point(p)
         out = {}
         for k, name in enumerate(perfmodel.KERNELS):
             avg = kms[k] / max(1, kcnt[k])
@@ -251,6 +255,35 @@ def run_ensemble(precision, steps, stream):
         b.select(chosen)
     for m in meshes:
         m.close()
+    return out
+
+
+PRISM_CASES = [(48, 4, "all"), (48, 4, "checker"), (24, 7, "all")]   # (edge, p, split): 11-22 M points
+
+
+def run_prisms(steps, fp64_peak, df_peak, cases=None):
+    """Prismatic and mixed hexahedral/prismatic periodic TGV meshes, both precisions: updates/s,
+    and on the all-prism meshes the phase times with the prism cost model and the volume kernel's
+    fraction of the arithmetic peak."""
+    out = {}
+    for (n, p, split) in (cases or PRISM_CASES):
+        row = {"n_edge": n, "p": p, "split": split}
+        dt = None
+        for prec in ("fp64", "mixed"):
+            c = Case(n, p, prec, dt=dt, prisms=split)
+            dt = c.dt
+            row["n_points"] = c.n_pts
+            row["n_prism"], row["n_hex"] = c.mesh.n_prism, c.mesh.n_elem
+            c.step()
+            ms = c.timed(max(2, steps))
+            row[prec] = c.n_pts * 4 * max(2, steps) / (ms * 1e-3)
+            if split == "all":
+                k = c.kernels(2, p, prism_model=True)
+                peak = fp64_peak if prec == "fp64" else df_peak
+                row[prec + "_kernels"] = k
+                row[prec + "_volume_frac_of_peak"] = k["volume"]["gflops"] * 1e9 / peak
+            c.close()
+        out[f"{split}_{n}cube_p{p}"] = row
     return out
 
 
@@ -362,6 +395,11 @@ def run_ours(args):
     cmx.close()
     del Qh, Out
 
+    prisms = {}
+    if not args.no_prisms:
+        cases = [(args.prism_edge, args.prism_order, "all")] if args.prism_edge else None
+        prisms = run_prisms(args.steps, fp64_peak, df_peak, cases)
+
     ensemble = {}
     if not args.no_ensemble:
         es = torch.cuda.Stream()
@@ -389,7 +427,7 @@ def run_ours(args):
             "config": config("mixed"), "clocks": clocks, "e2e": e2e,
             "gpu_launches": 4 * 4 * args.steps, "roofline": roofline, "kernels": k_mx,
             "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
-            "ensemble_64_vortex": ensemble,
+            "ensemble_64_vortex": ensemble, "prisms_tgv": prisms,
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, cores = oracle_rate(budget_s=12.0)
@@ -416,6 +454,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the p = 3..7 sweep")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-case batched vortex ensemble")
+    ap.add_argument("--no-prisms", action="store_true", help="skip the prismatic / mixed-mesh measurements")
+    ap.add_argument("--prism-edge", type=int, default=0, help="only an all-prism box of this edge (profiling)")
+    ap.add_argument("--prism-order", type=int, default=4)
     ap.add_argument("--n-edge", type=int, default=N_EDGE, help="elements per edge (profiling of smaller cases)")
     ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()

@@ -59,3 +59,49 @@ def bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dict:
     corr += per_el(5 * Np) * (4 if mode == "rk" else 1)                # Un, acc r/w, Q write (RK)
     b["correct"] = corr
     return b
+
+
+def prism_flops_per_point(p: int, viscous: bool = True) -> dict:
+    """Per solution point of an all-prism periodic mesh: Nt = N(N+1)/2 triangle nodes x N line
+    points per prism, 2 triangular faces of Nt and 3 quadrilateral faces of N^2 flux points."""
+    N = p + 1
+    Nt = N * (N + 1) // 2
+    Np = Nt * N
+    fp = 2 * Nt + 3 * N * N                  # face points per prism
+    fp_pt = fp / Np
+    if_pt = fp_pt / 2
+    f = {}
+    f["interp_faces"] = (2 * Nt * N + 3 * N * N * Nt) * 5 * 2 / Np
+    dense = 2 * Nt + N                        # MACs of one derivative triple (r, s along rows; zeta)
+    vol = 2 * 5 * dense                       # divergence with the own-flux correction folded in
+    vol += _INVISCID + _TRANSFORM
+    if viscous:
+        vol += 2 * 5 * dense                  # reference gradient
+        vol += 5 * 2 * (3 * N + 2)            # liftings of the 3 quadrilateral and 2 triangular faces
+        vol += 5 * 6                          # adding the liftings to the gradient
+        vol += fp_pt * 5 * 2                  # jumps at the flux points
+        vol += _PHYS_GRAD + _VISCOUS + 30     # + BR2 weights
+        vol += (2 * Nt * (15 * (2 * N + 2) + 3 * 2 * N) + 3 * N * N * 15 * 5 * Nt) / Np   # gradient traces
+    f["volume"] = vol
+    f["iface_flux"] = if_pt * (_RUSANOV + (_VISC_COMMON if viscous else 0))
+    f["correct"] = 5 * 2 * (2 + 3 * N) + 5 + 5 * 4
+    return f
+
+
+def prism_bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dict:
+    N = p + 1
+    Nt = N * (N + 1) // 2
+    Np = Nt * N
+    fp = 2 * Nt + 3 * N * N
+    per_el = lambda doubles: 8.0 * doubles / Np          # noqa: E731
+    b = {}
+    b["interp_faces"] = per_el(5 * Np) + per_el(5 * fp)
+    vol = per_el(5 * Np) + per_el(10 * Np) + per_el(5 * Np)
+    if viscous:
+        vol += per_el(2 * 5 * fp) + per_el(15 * fp)
+    b["volume"] = vol
+    b["iface_flux"] = per_el(fp / 2 * (2 * 5 + 3 + 5 + (2 * 15 if viscous else 0)))
+    corr = per_el(5 * Np) + per_el(fp / 2 * 5) + per_el(Np)
+    corr += per_el(5 * Np) * (4 if mode == "rk" else 1)
+    b["correct"] = corr
+    return b
