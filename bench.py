@@ -364,7 +364,7 @@ def run_ours(args):
     ach = k_mx[dom]["gflops"] * 1e9
     roofline = {"bound": "alu", "kernel": dom, "precision": "mixed (double-float on the FP32 pipe)",
                 "achieved": ach / 1e12, "peak": df_peak / 1e12, "unit": "TFLOP/s", "frac": ach / df_peak,
-                "traffic": None,
+                "traffic": TRAFFIC.get(("mixed", ORDER, N_EDGE, dom)),
                 "peak_source": "measured FP32 FMA rate (fr_probe_fma) / 18: a double-float multiply-add is 18 FP32 "
                                "instructions for 2 algorithmic flops",
                 "algorithmic_flops_per_point": fl[dom], "algorithmic_bytes_per_point": by[dom]}
@@ -442,7 +442,7 @@ def run_ours(args):
 # DRAM traffic per launch of the dominant kernel from ncu captures (precision, p, n_edge, kernel)
 # -> bytes; scaled from a 32^3 capture by the element count.  Only valid for the kernel version
 # that was profiled.
-TRAFFIC = {}
+TRAFFIC = {("fp64", 4, 64, "volume"): 8 * 1.5200e9, ("mixed", 4, 64, "volume"): 8 * 1.5225e9}
 
 
 def main():
