@@ -28,6 +28,7 @@ from . import gas
 from .basis import Basis1D
 from .hexfr import BC_DIRICHLET, HEX_REF_VERTS, trilinear_geometry
 from .tri import Tri
+from .curved import curved_geometry
 
 PRISM_REF_VERTS = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1], [1, -1, 1], [-1, 1, 1]], dtype=np.float64)
 
@@ -36,7 +37,7 @@ class ElemType:
     pass
 
 
-def hex_type(p):
+def hex_type(p, curved=False):
     b = Basis1D(p)
     N = p + 1
     I = np.eye(N)
@@ -67,6 +68,8 @@ def hex_type(p):
         corners = np.where(HEX_REF_VERTS[:, d] == s)[0]
         t.faces.append(dict(L=L, C=C, N=Nxi, pts=pts, corners=corners, kind="quad"))
     t.geometry = lambda X, ref: trilinear_geometry(X, ref)
+    if curved:
+        t.nv, t.geometry = 27, curved_geometry("hex", p)
     return t
 
 
@@ -91,7 +94,7 @@ def prism_geometry(X, ref):
     return x, detJ, S
 
 
-def prism_type(p):
+def prism_type(p, curved=False):
     b = Basis1D(p)
     T = Tri(p)
     N, Nt = p + 1, T.Nt
@@ -120,6 +123,8 @@ def prism_type(p):
         t.faces.append(dict(L=np.kron(I, E), C=np.kron(I, Minv @ Ehat), N=Nxi, pts=pts,
                             corners=np.array(corners), kind="quad"))
     t.geometry = prism_geometry
+    if curved:
+        t.nv, t.geometry = 18, curved_geometry("prism", p)
     return t
 
 
@@ -129,9 +134,12 @@ class MixedFR:
     def __init__(self, desc, phys, p):
         self.phys, self.p = phys, p
         prism = getattr(desc, "prism", None)
-        self.types = [hex_type(p), prism_type(p)]
-        conn = [np.asarray(desc.hex, dtype=np.int64).reshape(-1, 8),
-                np.zeros((0, 6), np.int64) if prism is None else np.asarray(prism, dtype=np.int64).reshape(-1, 6)]
+        hexa = np.asarray(desc.hex, dtype=np.int64)
+        pri = np.zeros((0, 6), np.int64) if prism is None else np.asarray(prism, dtype=np.int64)
+        # 27-node hexahedra / 18-node prisms: quadratic maps with curl-form metrics.
+        self.types = [hex_type(p, curved=hexa.ndim == 2 and hexa.shape[1] == 27),
+                      prism_type(p, curved=pri.ndim == 2 and pri.shape[1] == 18)]
+        conn = [hexa.reshape(-1, self.types[0].nv), pri.reshape(-1, self.types[1].nv)]
         self.conn = conn
         self.x, self.detJ, self.S, self.nf, self.xf = [], [], [], [], []
         for t, cn in zip(self.types, conn):

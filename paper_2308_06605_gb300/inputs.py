@@ -213,6 +213,145 @@ def hex_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3,
 
 
 # ---------------------------------------------------------------------------------------------
+# Quadratic (curved) elements.  Node orders (reference coordinates):
+#   27-node hexahedron: the 8 corners (VTK order), the 12 edge midpoints (bottom 01 12 23 30, top
+#   45 56 67 74, vertical 04 15 26 37), the 6 face centres (x-, x+, y-, y+, z-, z+), the centre.
+#   18-node prism: the 6 corners (VTK wedge order), the edge midpoints 01 12 20 (bottom), 34 45 53
+#   (top), 03 14 25 (vertical), then the centres of the quadrilateral faces 0143, 1254, 2035.
+# ---------------------------------------------------------------------------------------------
+HEX27_REF = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1], [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1],
+                      [0, -1, -1], [1, 0, -1], [0, 1, -1], [-1, 0, -1], [0, -1, 1], [1, 0, 1], [0, 1, 1], [-1, 0, 1],
+                      [-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0],
+                      [-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1], [0, 0, 0]], dtype=np.int64)
+PRISM18_REF = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1], [1, -1, 1], [-1, 1, 1],
+                        [0, -1, -1], [0, 0, -1], [-1, 0, -1], [0, -1, 1], [0, 0, 1], [-1, 0, 1],
+                        [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [0, -1, 0], [0, 0, 0], [-1, 0, 0]], dtype=np.int64)
+
+
+def _tri_bary(r, s):
+    return np.array([-(r + s) / 2.0, (1.0 + r) / 2.0, (1.0 + s) / 2.0])
+
+
+def hex27_rotation_permutations() -> np.ndarray:
+    """[24][27]: the node relabelling of each cube rotation (new node k = old node perm[r][k])."""
+    lookup = {tuple(v): i for i, v in enumerate(HEX27_REF.tolist())}
+    return np.array([[lookup[tuple((R @ c).tolist())] for c in HEX27_REF] for R in cube_rotations()], dtype=np.int64)
+
+
+def prism18_permutations() -> np.ndarray:
+    """[6][18]: node relabelling of each PRISM_PERMUTATIONS entry (new node k = old node perm[q][k])."""
+    lookup = {}
+    for i, (r, s, z) in enumerate(PRISM18_REF.tolist()):
+        lookup[tuple(np.round(_tri_bary(r, s), 6).tolist()) + (z,)] = i
+    out = []
+    for P in PRISM_PERMUTATIONS:
+        flip = P[0] >= 3
+        row = []
+        for (r, s, z) in PRISM18_REF.tolist():
+            lam_new = _tri_bary(r, s)
+            lam_old = np.zeros(3)
+            for k in range(3):
+                lam_old[P[k] % 3] = lam_new[k]
+            row.append(lookup[tuple(np.round(lam_old, 6).tolist()) + ((-z if flip else z),)])
+        out.append(row)
+    return np.array(out, dtype=np.int64)
+
+
+def curved_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3, periodic=(True, True, True),
+                    warp: float = 0.1, seed: int | None = None, shuffle: bool = False, rotate: bool = False,
+                    wall_tags: dict | None = None, prisms=None) -> MeshDesc:
+    """Box of nx*ny*nz quadratic (27-node) hexahedra, or 18-node prisms where columns are split like
+    `hex_box_mesh`, on a (2n+1)^3 node lattice whose every node x is moved by the smooth periodic
+    warp d_a(x) = warp L_a / (2 pi) sin(2 pi (x_b - lo_b) / L_b) sin(2 pi (x_c - lo_c) / L_c) ((a, b, c)
+    cyclic), so element faces are curved (also on non-periodic boundaries).  Tags, periodic pairs,
+    `rotate` (the 24 cube rotations / 6 prism relabellings applied to all nodes), `shuffle` and
+    `wall_tags` as in `hex_box_mesh`; boundary faces list their corner nodes."""
+    nx, ny, nz = (int(v) for v in n)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    L = hi - lo
+    rng = np.random.default_rng(seed if seed is not None else 0)
+    xs = [np.linspace(lo[a], hi[a], 2 * m + 1) for a, m in enumerate((nx, ny, nz))]
+    X, Y, Z = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
+    P = np.stack([X, Y, Z], axis=-1).reshape(-1, 3)
+    th = 2 * np.pi * (P - lo[None, :]) / L[None, :]
+    d = np.empty_like(P)
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        d[:, a] = warp * L[a] / (2 * np.pi) * np.sin(th[:, b]) * np.sin(th[:, c])
+    xyz = P + d
+    nid = np.arange(xyz.shape[0]).reshape(2 * nx + 1, 2 * ny + 1, 2 * nz + 1)
+    split = np.zeros((nx, ny), dtype=bool)
+    if prisms == "all":
+        split[:] = True
+    elif prisms == "checker":
+        split[(np.add.outer(np.arange(nx), np.arange(ny)) % 2) == 0] = True
+    hexes, pris = [], []
+    # prism A covers hex corners (-1,-1), (1,-1), (1,1) of the bottom face, prism B (-1,-1), (1,1), (-1,1)
+    tri_corners = (np.array([[-1, -1], [1, -1], [1, 1]]), np.array([[-1, -1], [1, 1], [-1, 1]]))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                base = np.array([2 * i + 1, 2 * j + 1, 2 * k + 1])
+                if not split[i, j]:
+                    hexes.append([nid[tuple(base + c)] for c in HEX27_REF])
+                    continue
+                for V in tri_corners:
+                    row = []
+                    for (r, s, z) in PRISM18_REF.tolist():
+                        lam = _tri_bary(r, s)
+                        pxy = (lam[:, None] * V).sum(axis=0)
+                        row.append(nid[base[0] + int(round(pxy[0])), base[1] + int(round(pxy[1])), base[2] + z])
+                    pris.append(row)
+    hexes = np.array(hexes, dtype=np.int64).reshape(-1, 27)
+    pris = np.array(pris, dtype=np.int64).reshape(-1, 18)
+    # Boundary faces (corner nodes), tags 1..6.
+    bnodes, btags = [], []
+    c = lambda I, J, K: nid[2 * I, 2 * J, 2 * K]   # noqa: E731  corner lattice node
+    for j in range(ny):
+        for k in range(nz):
+            bnodes.append([c(0, j, k), c(0, j + 1, k), c(0, j + 1, k + 1), c(0, j, k + 1)]); btags.append(1)
+            bnodes.append([c(nx, j, k), c(nx, j + 1, k), c(nx, j + 1, k + 1), c(nx, j, k + 1)]); btags.append(2)
+    for i in range(nx):
+        for k in range(nz):
+            bnodes.append([c(i, 0, k), c(i + 1, 0, k), c(i + 1, 0, k + 1), c(i, 0, k + 1)]); btags.append(3)
+            bnodes.append([c(i, ny, k), c(i + 1, ny, k), c(i + 1, ny, k + 1), c(i, ny, k + 1)]); btags.append(4)
+    for i in range(nx):
+        for j in range(ny):
+            for kk, tag in ((0, 5), (nz, 6)):
+                q = [c(i, j, kk), c(i + 1, j, kk), c(i + 1, j + 1, kk), c(i, j + 1, kk)]
+                if split[i, j]:
+                    bnodes.append([q[0], q[1], q[2], -1]); btags.append(tag)
+                    bnodes.append([q[0], q[2], q[3], -1]); btags.append(tag)
+                else:
+                    bnodes.append(q); btags.append(tag)
+    per = []
+    for a in range(3):
+        if periodic[a]:
+            t = np.zeros(3)
+            t[a] = float(L[a])
+            per.append(Periodic(2 * a + 1, 2 * a + 2, tuple(float(v) for v in t)))
+    bcs = []
+    if wall_tags:
+        for tag, (kind, params) in wall_tags.items():
+            bcs.append(BC(int(tag), int(kind), tuple(float(v) for v in params)))
+    if rotate:
+        if len(hexes):
+            r = rng.integers(0, 24, size=hexes.shape[0])
+            hexes = np.take_along_axis(hexes, hex27_rotation_permutations()[r], axis=1)
+        if len(pris):
+            r = rng.integers(0, 6, size=pris.shape[0])
+            pris = np.take_along_axis(pris, prism18_permutations()[r], axis=1)
+    if shuffle:
+        hexes = hexes[rng.permutation(hexes.shape[0])]
+        pris = pris[rng.permutation(pris.shape[0])]
+    return MeshDesc(xyz=np.ascontiguousarray(xyz, dtype=np.float64), hex=np.ascontiguousarray(hexes),
+                    bface_nodes=np.array(bnodes, dtype=np.int64).reshape(-1, 4),
+                    bface_tag=np.array(btags, dtype=np.int32), periodic=per, bcs=bcs,
+                    prism=np.ascontiguousarray(pris))
+
+
+# ---------------------------------------------------------------------------------------------
 # Physical parameters and initial conditions (functions of physical coordinates only).
 # ---------------------------------------------------------------------------------------------
 
