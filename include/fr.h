@@ -86,8 +86,14 @@ typedef struct {
   int32_t n_periodic;
   const fr_periodic *periodic;  /* [n_periodic] */
   int64_t n_prism;              /* 0 for a hexahedral mesh */
-  const int64_t *prism;         /* [n_prism][6] vertex ids, VTK wedge order: (v0, v1, v2) one
-                                   triangle, (v3, v4, v5) the opposite one, v_k+3 above v_k (host) */
+  const int64_t *prism;         /* [n_prism][prism_nodes] vertex ids, VTK wedge order: (v0, v1, v2)
+                                   one triangle, (v3, v4, v5) the opposite one, v_k+3 above v_k (host) */
+  int32_t hex_nodes;            /* nodes per hexahedron: 8 (trilinear; 0 means 8) or 27 (triquadratic:
+                                   the 8 corners, edge midpoints 01 12 23 30 45 56 67 74 04 15 26 37,
+                                   face centres x- x+ y- y+ z- z+, centre) */
+  int32_t prism_nodes;          /* nodes per prism: 6 (0 means 6) or 18 (quadratic: the 6 corners,
+                                   edge midpoints 01 12 20 34 45 53 03 14 25, centres of the
+                                   quadrilateral faces 0143 1254 2035) */
 } fr_mesh_desc;
 
 typedef struct {
@@ -118,7 +124,12 @@ typedef struct {
 /*
  * fr_mesh_create — build connectivity, geometry and device buffers (section "FR Algorithm",
  * Eq. 1: |J| and S = |J| J^-1 at the solution points; the paper's face construction: faces are
- * keyed by their sorted vertex ids, sorted so coupled faces are adjacent, then paired).
+ * keyed by their sorted vertex ids (corners), sorted so coupled faces are adjacent, then paired).
+ * Quadratic (curved) elements take their metric terms from the conservative curl form (Kopriva
+ * 2006): S[i][n] = -(curl I(X_l grad X_m))_i, (n, m, l) cyclic, I the degree-p interpolant on
+ * Gauss-Lobatto points (on the prism: triangle nodes x Gauss-Lobatto in zeta), evaluated exactly
+ * at the solution and flux points, so free stream is preserved to rounding; linear elements use
+ * the analytic S.
  * Periodic faces are paired by translated centroids.  Validates everything before allocating
  * device memory: unmatched interior faces, boundary faces without a condition, non-positive
  * Jacobians -> FR_EMESH; p outside 1..7, NULL arrays, bad physics -> FR_EINVAL.  `stream` is a

@@ -44,6 +44,26 @@ extern const int kTriPerm[6][3];
 // Point of edge e (0: s = -1, 1: r + s = 0, 2: r = -1) at parameter sigma in [-1, 1].
 void tri_edge_point(int edge, double sigma, double &r, double &s);
 bool make_tri_basis(int p, TriBasis &T);
+// p + 1 Gauss-Lobatto-Legendre points (ascending).
+void gll_nodes(int p, double *x);
+
+// Quadratic (curved) element geometry (fr_curved.cpp).  1D operators from the p + 1
+// Gauss-Lobatto points g to the Gauss-Legendre points x of the line and to its ends.
+struct CurvedOps {
+  int p = 0, N = 0;
+  double g[kMaxN];
+  double V[kMaxN * kMaxN], D[kMaxN * kMaxN];   // [i][a] = l_a(x_i), l_a'(x_i)
+  double Ve[2][kMaxN], De[2][kMaxN];           // l_a(-1), l_a'(-1); l_a(+1), l_a'(+1)
+};
+void curved_ops(int p, const Basis1D &b, CurvedOps &o);
+// Position and dx_i/dxi_b of a 27-node hexahedron / 18-node prism at a reference point.
+void hex27_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]);
+void prism18_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]);
+// Conservative-curl metric terms, S[(d*3 + j)] = |J| dxi_d/dx_j, of one element: at the solution
+// points (S_sol [9][Np]) and at the flux points of every face (S_face [faces][9][N^2], a
+// triangular face uses its first Nt slots).
+void hex27_curl(const CurvedOps &o, const double (*X)[3], double *S_sol, double *S_face);
+void prism18_curl(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], double *S_sol, double *S_face);
 
 // Offsets (in values) of the per-mesh prism operator table for line order N (Nt = N(N+1)/2):
 // Dr, Ds (triangle derivatives), Drt, Dst (with the own-flux correction of the quadrilateral

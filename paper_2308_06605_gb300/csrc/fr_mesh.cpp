@@ -202,13 +202,13 @@ struct Side {
   int f;
 };
 
-static void face_corners(const int64_t *hex, int64_t e, int f, int64_t out[4], int ref[4][2]) {
+static void face_corners(const int64_t *hex, int stride, int64_t e, int f, int64_t out[4], int ref[4][2]) {
   int d, s, t0, t1;
   face_axes(f, d, s, t0, t1);
   int c = 0;
   for (int v = 0; v < 8; ++v) {
     if (kVert[v][d] != s) continue;
-    out[c] = hex[e * 8 + v];
+    out[c] = hex[e * stride + v];
     ref[c][0] = kVert[v][t0];
     ref[c][1] = kVert[v][t1];
     ++c;
@@ -306,14 +306,19 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   const int64_t E = desc->n_hex;
   const int64_t Ep = desc->n_prism > 0 ? desc->n_prism : 0;
   const int64_t G = E + Ep;                 // elements: hexahedra first, then prisms
+  const int hn = desc->hex_nodes == 0 ? 8 : desc->hex_nodes, pn = desc->prism_nodes == 0 ? 6 : desc->prism_nodes;
+  if ((hn != 8 && hn != 27) || (pn != 6 && pn != 18)) {
+    err = "hex_nodes must be 8 or 27 and prism_nodes 6 or 18";
+    return FR_EINVAL;
+  }
   m.p = p; m.N = N; m.Np = Np; m.Nf = Nf; m.E = E; m.Ep = Ep;
-  for (int64_t i = 0; i < E * 8; ++i) {
+  for (int64_t i = 0; i < E * hn; ++i) {
     if (desc->hex[i] < 0 || desc->hex[i] >= desc->n_nodes) {
       err = "hex vertex id out of range";
       return FR_EINVAL;
     }
   }
-  for (int64_t i = 0; i < Ep * 6; ++i) {
+  for (int64_t i = 0; i < Ep * pn; ++i) {
     if (desc->prism[i] < 0 || desc->prism[i] >= desc->n_nodes) {
       err = "prism vertex id out of range";
       return FR_EINVAL;
@@ -334,23 +339,24 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   }
   const int Nt = m.Nt, Npp = m.Npp;
   const double(*xyz)[3] = reinterpret_cast<const double(*)[3]>(desc->xyz);
-  auto elem_verts = [&](int64_t e, double X[8][3]) {
-    for (int v = 0; v < 8; ++v)
-      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->hex[e * 8 + v]][i];
+  // Element nodes (the corners come first in both node orders).
+  auto elem_verts = [&](int64_t e, double X[][3], int n = 8) {
+    for (int v = 0; v < n; ++v)
+      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->hex[e * hn + v]][i];
   };
-  auto prism_verts = [&](int64_t ep, double X[6][3]) {
-    for (int v = 0; v < 6; ++v)
-      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->prism[ep * 6 + v]][i];
+  auto prism_verts = [&](int64_t ep, double X[][3], int n = 6) {
+    for (int v = 0; v < n; ++v)
+      for (int i = 0; i < 3; ++i) X[v][i] = xyz[desc->prism[ep * pn + v]][i];
   };
   auto nfaces = [&](int64_t g) { return g < E ? 6 : 5; };
   auto face_index = [&](int64_t g, int f) { return g < E ? g * 6 + f : E * 6 + (g - E) * 5 + f; };
   auto face_geo = [&](int64_t g, int f, FaceGeo &F) {
     if (g < E) {
       F.nc = 4;
-      face_corners(desc->hex, g, f, F.ids, F.ref);
+      face_corners(desc->hex, hn, g, f, F.ids, F.ref);
       return;
     }
-    const int64_t *pv = desc->prism + (g - E) * 6;
+    const int64_t *pv = desc->prism + (g - E) * pn;
     F.nc = f < 2 ? 3 : 4;
     for (int a = 0; a < F.nc; ++a) {
       F.ids[a] = pv[kPrismFace[f][a]];
@@ -575,9 +581,34 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   m.xsol.assign(((size_t)E * Np + (size_t)Ep * Npp) * 3, 0.0);
   m.h.assign(G, 0.0);
   std::vector<double> fx((size_t)(E * 6 + Ep * 5) * Nf * 3);   // flux-point coordinates for the match check
+  // Quadratic elements: positions and |J| from the element map, S from the curl form.
+  const bool curved_h = hn == 27, curved_p = pn == 18;
+  CurvedOps cops;
+  if (curved_h || curved_p) curved_ops(p, b, cops);
+  std::vector<double> Ssol, Sface;
   for (int64_t e = 0; e < E; ++e) {
-    double X[8][3];
-    elem_verts(e, X);
+    double X[27][3];
+    elem_verts(e, X, hn);
+    if (curved_h) {
+      Ssol.resize((size_t)9 * Np);
+      Sface.resize((size_t)6 * 9 * Nf);
+      hex27_curl(cops, X, Ssol.data(), Sface.data());
+    }
+    // Geometry at a reference point: x, S, |J|; `slot` indexes S_sol (face < 0) or S_face[face].
+    auto geo = [&](const double xi[3], int face, int slot, double x[3], double S[3][3], double &det) {
+      if (!curved_h) {
+        Jac g = trilinear(X, xi);
+        adjugate_rows(g.J, S, det);
+        for (int c = 0; c < 3; ++c) x[c] = g.x[c];
+        return;
+      }
+      double J[3][3], Sa[3][3];
+      hex27_point(X, xi, x, J);
+      adjugate_rows(J, Sa, det);
+      for (int d = 0; d < 3; ++d)
+        for (int jj = 0; jj < 3; ++jj)
+          S[d][jj] = face < 0 ? Ssol[(size_t)(d * 3 + jj) * Np + slot] : Sface[((size_t)face * 9 + d * 3 + jj) * Nf + slot];
+    };
     double vol = 0.0;
     double *met = &m.metrics[(size_t)e * 10 * Np];
     for (int k = 0; k < N; ++k)
@@ -585,9 +616,8 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
         for (int i = 0; i < N; ++i) {
           int mm = i + N * j + N * N * k;
           double xi[3] = {b.x[i], b.x[j], b.x[k]};
-          Jac g = trilinear(X, xi);
-          double S[3][3], det;
-          adjugate_rows(g.J, S, det);
+          double S[3][3], det, gx[3];
+          geo(xi, -1, mm, gx, S, det);
           if (!(det > 0.0)) {
             snprintf(buf, sizeof buf, "non-positive Jacobian in element %lld", (long long)e);
             err = buf;
@@ -597,7 +627,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
             for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Np + mm] = S[d][jj];
           met[9 * Np + mm] = 1.0 / det;
           vol += b.w[i] * b.w[j] * b.w[k] * det;
-          for (int c = 0; c < 3; ++c) m.xsol[((size_t)e * Np + mm) * 3 + c] = g.x[c];
+          for (int c = 0; c < 3; ++c) m.xsol[((size_t)e * Np + mm) * 3 + c] = gx[c];
         }
     m.h[e] = std::cbrt(vol);
     for (int f = 0; f < 6; ++f) {
@@ -623,10 +653,9 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
             m.liftfac[(((size_t)e * 6 + f) * 3 + jj) * Nf + r] = s * acc[jj];
           double xi[3];
           xi[d] = (double)s; xi[t0] = b.x[aa]; xi[t1] = b.x[bb];
-          Jac g = trilinear(X, xi);
-          double S[3][3], det;
-          adjugate_rows(g.J, S, det);
-          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(e, f) * Nf + r) * 3 + c] = g.x[c];
+          double S[3][3], det, gx[3];
+          geo(xi, f, r, gx, S, det);
+          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(e, f) * Nf + r) * 3 + c] = gx[c];
           if (side == 0) {
             double nn = 0.0;
             for (int jj = 0; jj < 3; ++jj) {
@@ -643,17 +672,36 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     m.metrics_p.assign((size_t)Ep * 10 * Npp, 0.0);
     for (int64_t ep = 0; ep < Ep; ++ep) {
       const int64_t g = E + ep;
-      double X[6][3];
-      prism_verts(ep, X);
+      double X[18][3];
+      prism_verts(ep, X, pn);
+      if (curved_p) {
+        Ssol.resize((size_t)9 * Npp);
+        Sface.resize((size_t)5 * 9 * Nf);
+        prism18_curl(cops, tb, X, Ssol.data(), Sface.data());
+      }
+      auto pgeo = [&](const double xi[3], int face, int slot, double x[3], double S[3][3], double &det) {
+        if (!curved_p) {
+          Jac jg = prism_map(X, xi);
+          adjugate_rows(jg.J, S, det);
+          for (int c = 0; c < 3; ++c) x[c] = jg.x[c];
+          return;
+        }
+        double J[3][3], Sa[3][3];
+        prism18_point(X, xi, x, J);
+        adjugate_rows(J, Sa, det);
+        for (int d = 0; d < 3; ++d)
+          for (int jj = 0; jj < 3; ++jj)
+            S[d][jj] = face < 0 ? Ssol[(size_t)(d * 3 + jj) * Npp + slot]
+                                : Sface[((size_t)face * 9 + d * 3 + jj) * Nf + slot];
+      };
       double vol = 0.0;
       double *met = &m.metrics_p[(size_t)ep * 10 * Npp];
       for (int k = 0; k < N; ++k)
         for (int q = 0; q < Nt; ++q) {
           const int mm = q + Nt * k;
           const double xi[3] = {tb.r[q], tb.s[q], b.x[k]};
-          Jac jg = prism_map(X, xi);
-          double S[3][3], det;
-          adjugate_rows(jg.J, S, det);
+          double S[3][3], det, gx[3];
+          pgeo(xi, -1, mm, gx, S, det);
           if (!(det > 0.0)) {
             snprintf(buf, sizeof buf, "non-positive Jacobian in prism %lld", (long long)ep);
             err = buf;
@@ -663,7 +711,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
             for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Npp + mm] = S[d][jj];
           met[9 * Npp + mm] = 1.0 / det;
           vol += tb.wT[q] * b.w[k] * det;
-          for (int c = 0; c < 3; ++c) m.xsol[((size_t)E * Np + (size_t)ep * Npp + mm) * 3 + c] = jg.x[c];
+          for (int c = 0; c < 3; ++c) m.xsol[((size_t)E * Np + (size_t)ep * Npp + mm) * 3 + c] = gx[c];
         }
       m.h[g] = std::cbrt(vol);
       for (int f = 0; f < 5; ++f) {
@@ -679,10 +727,9 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
             tri_edge_point(f - 2, b.x[r % N], xi[0], xi[1]);
             xi[2] = b.x[r / N];
           }
-          Jac jg = prism_map(X, xi);
-          double S[3][3], det;
-          adjugate_rows(jg.J, S, det);
-          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(g, f) * Nf + r) * 3 + c] = jg.x[c];
+          double S[3][3], det, gx[3];
+          pgeo(xi, f, r, gx, S, det);
+          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(g, f) * Nf + r) * 3 + c] = gx[c];
           if (side == 0) {
             double nn = 0.0;
             for (int jj = 0; jj < 3; ++jj) {

@@ -163,6 +163,12 @@ void tri_edge_point(int edge, double sigma, double &r, double &s) {
   }
 }
 
+void gll_nodes(int p, double *x) {
+  ld t[kMaxN + 1];
+  gll_points(p, t);
+  for (int i = 0; i <= p; ++i) x[i] = (double)t[i];
+}
+
 bool make_tri_basis(int p, TriBasis &T) {
   const int N = p + 1, Nt = N * (N + 1) / 2;
   T.p = p;

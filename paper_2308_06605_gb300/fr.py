@@ -46,7 +46,8 @@ class fr_mesh_desc(C.Structure):
                 ("bface_tag", C.POINTER(C.c_int32)),
                 ("n_bc", C.c_int32), ("bc", C.POINTER(fr_bc)),
                 ("n_periodic", C.c_int32), ("periodic", C.POINTER(fr_periodic)),
-                ("n_prism", C.c_int64), ("prism", C.POINTER(C.c_int64))]
+                ("n_prism", C.c_int64), ("prism", C.POINTER(C.c_int64)),
+                ("hex_nodes", C.c_int32), ("prism_nodes", C.c_int32)]
 
 
 class fr_physics(C.Structure):
@@ -156,9 +157,11 @@ class Mesh:
         self._lib = lib
         self._keep = []
         xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
-        hexa = np.ascontiguousarray(np.asarray(desc.hex, dtype=np.int64).reshape(-1, 8))
+        hexa = np.asarray(desc.hex, dtype=np.int64)
+        hexa = np.ascontiguousarray(hexa if hexa.ndim == 2 else hexa.reshape(-1, 8))    # 8 or 27 nodes each
         pri = getattr(desc, "prism", None)
-        pri = np.ascontiguousarray(np.zeros((0, 6)) if pri is None else pri, dtype=np.int64).reshape(-1, 6)
+        pri = np.asarray(np.zeros((0, 6)) if pri is None else pri, dtype=np.int64)
+        pri = np.ascontiguousarray(pri if pri.ndim == 2 else pri.reshape(-1, 6))           # 6 or 18 nodes each
         bn = np.ascontiguousarray(desc.bface_nodes, dtype=np.int64).reshape(-1, 4)
         bt = np.ascontiguousarray(desc.bface_tag, dtype=np.int32)
         bcs = (fr_bc * max(1, len(desc.bcs)))()
@@ -176,7 +179,8 @@ class Mesh:
                          hex=_ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
                          bface_nodes=_ptr(bn, C.c_int64), bface_tag=_ptr(bt, C.c_int32),
                          n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per,
-                         n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64))
+                         n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64),
+                         hex_nodes=hexa.shape[1], prism_nodes=pri.shape[1])
         ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
                         viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision)
         h = C.c_void_p()
