@@ -70,6 +70,69 @@ def trilinear_geometry(X, ref):
     return x, detJ, S
 
 
+def boundary_states(kind, prm, Qm, n, g, Rg):
+    """Boundary face of kind `kind` with parameters `prm`: (ghost state for the Riemann flux,
+    common solution Q^I) at its flux points, from the interior trace Qm [Nf][5] and the outward
+    area-scaled normal n [Nf][3] (gas constants g = gamma, Rg = R).
+
+    The paper lists boundary conditions among its physical models without stating them;
+    this build's readings are:
+      wall (isothermal no-slip, T_w): ghost = interior density and energy with reversed
+        momentum (the mirror state); Q^I = wall state (interior density, zero velocity,
+        T = T_w).
+      Dirichlet (exterior state Q_b): ghost = Q^I = Q_b.
+      characteristic outflow (static p_b): interior entropy, tangential velocity and the
+        outgoing invariant u.n^ + 2c/(gamma-1); ghost = Q^I = that boundary state.
+      characteristic inflow (total p0, total T0, unit direction d): interior outgoing
+        invariant; speed V from (d.n^)V + 2c_b/(gamma-1) = invariant with
+        c_b^2 = gamma R (T0 - V^2/(2 cp)); static state from the isentropic relations;
+        ghost = Q^I = that state.
+    """
+    rho, u, p = gas.primitives(Qm, g)
+    if kind == BC_DIRICHLET:
+        Qb = np.broadcast_to(prm[:5], Qm.shape).copy()
+        return Qb, Qb
+    if kind == BC_WALL_ISOTHERMAL:
+        ghost = Qm.copy()
+        ghost[..., 1:4] *= -1.0
+        Qi = np.zeros_like(Qm)
+        Qi[..., 0] = rho
+        Qi[..., 4] = rho * Rg * prm[0] / (g - 1.0)
+        return ghost, Qi
+    nh = n / np.linalg.norm(n, axis=-1, keepdims=True)
+    un = np.sum(u * nh, axis=-1)
+    c = np.sqrt(g * p / rho)
+    Rplus = un + 2.0 * c / (g - 1.0)
+    if kind == BC_CHAR_OUTFLOW:
+        pb = prm[0]
+        s_ent = p / rho ** g
+        rb = (pb / s_ent) ** (1.0 / g)
+        cb = np.sqrt(g * pb / rb)
+        unb = Rplus - 2.0 * cb / (g - 1.0)
+        ub = u + (unb - un)[..., None] * nh
+        Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
+                       pb / (g - 1.0) + 0.5 * rb * np.sum(ub * ub, axis=-1)], axis=-1)
+        return Qb, Qb
+    if kind == BC_CHAR_INFLOW:
+        p0, T0 = prm[0], prm[1]
+        d = np.asarray(prm[2:5], dtype=np.float64)
+        d = d / np.linalg.norm(d)
+        a = nh @ d
+        A = a * a + 2.0 / (g - 1.0)
+        B = -2.0 * a * Rplus
+        Cc = Rplus * Rplus - (2.0 / (g - 1.0)) ** 2 * g * Rg * T0
+        V = (-B + np.sqrt(B * B - 4.0 * A * Cc)) / (2.0 * A)
+        cp = g * Rg / (g - 1.0)
+        Tb = T0 - V * V / (2.0 * cp)
+        pb = p0 * (Tb / T0) ** (g / (g - 1.0))
+        rb = pb / (Rg * Tb)
+        ub = V[..., None] * d
+        Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
+                       pb / (g - 1.0) + 0.5 * rb * V * V], axis=-1)
+        return Qb, Qb
+    raise ValueError("unknown boundary kind %d" % kind)
+
+
 class HexFR:
     """Oracle FR discretisation of one hexahedral mesh at uniform order p."""
 
@@ -221,69 +284,8 @@ class HexFR:
         return np.einsum('mq,eq...->em...', self.Cf[f], B)
 
     def _boundary_states(self, Qm, n, k):
-        """Boundary face k: (ghost state for the Riemann flux, common solution Q^I) at its flux
-        points, from the interior trace Qm [Nf][5] and the outward area-scaled normal n [Nf][3].
-
-        The paper lists boundary conditions among its physical models without stating them;
-        this build's readings are:
-          wall (isothermal no-slip, T_w): ghost = interior density and energy with reversed
-            momentum (the mirror state); Q^I = wall state (interior density, zero velocity,
-            T = T_w).
-          Dirichlet (exterior state Q_b): ghost = Q^I = Q_b.
-          characteristic outflow (static p_b): interior entropy, tangential velocity and the
-            outgoing invariant u.n^ + 2c/(gamma-1); ghost = Q^I = that boundary state.
-          characteristic inflow (total p0, total T0, unit direction d): interior outgoing
-            invariant; speed V from (d.n^)V + 2c_b/(gamma-1) = invariant with
-            c_b^2 = gamma R (T0 - V^2/(2 cp)); static state from the isentropic relations;
-            ghost = Q^I = that state.
-        """
-        ph = self.phys
-        g, Rg = ph.gamma, ph.R
-        kind = self.b_kind[k]
-        prm = self.b_params[k]
-        rho, u, p = gas.primitives(Qm, g)
-        if kind == BC_DIRICHLET:
-            Qb = np.broadcast_to(prm[:5], Qm.shape).copy()
-            return Qb, Qb
-        if kind == BC_WALL_ISOTHERMAL:
-            ghost = Qm.copy()
-            ghost[..., 1:4] *= -1.0
-            Qi = np.zeros_like(Qm)
-            Qi[..., 0] = rho
-            Qi[..., 4] = rho * Rg * prm[0] / (g - 1.0)
-            return ghost, Qi
-        nh = n / np.linalg.norm(n, axis=-1, keepdims=True)
-        un = np.sum(u * nh, axis=-1)
-        c = np.sqrt(g * p / rho)
-        Rplus = un + 2.0 * c / (g - 1.0)
-        if kind == BC_CHAR_OUTFLOW:
-            pb = prm[0]
-            s_ent = p / rho ** g
-            rb = (pb / s_ent) ** (1.0 / g)
-            cb = np.sqrt(g * pb / rb)
-            unb = Rplus - 2.0 * cb / (g - 1.0)
-            ub = u + (unb - un)[..., None] * nh
-            Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
-                           pb / (g - 1.0) + 0.5 * rb * np.sum(ub * ub, axis=-1)], axis=-1)
-            return Qb, Qb
-        if kind == BC_CHAR_INFLOW:
-            p0, T0 = prm[0], prm[1]
-            d = np.asarray(prm[2:5], dtype=np.float64)
-            d = d / np.linalg.norm(d)
-            a = nh @ d
-            A = a * a + 2.0 / (g - 1.0)
-            B = -2.0 * a * Rplus
-            Cc = Rplus * Rplus - (2.0 / (g - 1.0)) ** 2 * g * Rg * T0
-            V = (-B + np.sqrt(B * B - 4.0 * A * Cc)) / (2.0 * A)
-            cp = g * Rg / (g - 1.0)
-            Tb = T0 - V * V / (2.0 * cp)
-            pb = p0 * (Tb / T0) ** (g / (g - 1.0))
-            rb = pb / (Rg * Tb)
-            ub = V[..., None] * d
-            Qb = np.stack([rb, rb * ub[..., 0], rb * ub[..., 1], rb * ub[..., 2],
-                           pb / (g - 1.0) + 0.5 * rb * V * V], axis=-1)
-            return Qb, Qb
-        raise ValueError("unknown boundary kind %d" % kind)
+        """Boundary face k: (ghost, Q^I) by `boundary_states`."""
+        return boundary_states(self.b_kind[k], self.b_params[k], Qm, n, self.phys.gamma, self.phys.R)
 
     # ------------------------------------------------------------------ residual (Eq. 3)
     def residual(self, Q, t=0.0, magnitude=False):

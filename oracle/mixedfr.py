@@ -26,7 +26,7 @@ from scipy.spatial import cKDTree
 
 from . import gas
 from .basis import Basis1D
-from .hexfr import BC_DIRICHLET, HEX_REF_VERTS, trilinear_geometry
+from .hexfr import HEX_REF_VERTS, boundary_states, trilinear_geometry
 from .tri import Tri
 from .curved import curved_geometry
 
@@ -229,13 +229,13 @@ class MixedFR:
             dQ[tL][fL][eL] = qI - qL
             dQ[tR][fR][eR][perm] = qI - qR
             Qc_if.append(qI)
-        bst = []
+        ghosts, bst = [], []
         for (ti, e, fi, bc) in self.bfaces:
-            if bc.kind != BC_DIRICHLET:
-                raise NotImplementedError("the mixed-element oracle covers Dirichlet boundaries")
-            qb = np.broadcast_to(np.asarray(bc.params[:5], dtype=np.float64), Qf[ti][fi][e].shape)
-            dQ[ti][fi][e] = qb - Qf[ti][fi][e]
-            bst.append(qb)
+            gh, qi = boundary_states(bc.kind, np.asarray(bc.params, dtype=np.float64), Qf[ti][fi][e],
+                                     self.nf[ti][fi][e], ph.gamma, ph.R)
+            dQ[ti][fi][e] = qi - Qf[ti][fi][e]
+            ghosts.append(gh)
+            bst.append(qi)
         grads, gfaces, Hhat = [], [], []
         for ti, (t, Q) in enumerate(zip(T, Qs)):
             Sinv = self.S[ti] / self.detJ[ti][..., None, None]
@@ -270,7 +270,7 @@ class MixedFR:
             Fc[tR][fR][eR][perm] = -F
         for k, (ti, e, fi, bc) in enumerate(self.bfaces):
             n = self.nf[ti][fi][e]
-            F = gas.common_flux(ph.inviscid_flux, Qf[ti][fi][e], bst[k], n, gam)
+            F = gas.common_flux(ph.inviscid_flux, Qf[ti][fi][e], ghosts[k], n, gam)
             if visc:
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(bst[k], gfaces[ti][fi][e], gam, ph.R, ph.mu, ph.Pr), n)
             Fc[ti][fi][e] = F

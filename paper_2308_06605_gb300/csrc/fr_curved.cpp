@@ -10,9 +10,10 @@
 // a face's normal depends only on the face's own geometry, so both sides of an interface agree and
 // uniform flow stays uniform to rounding.  For p >= 2 the interpolant reproduces grad X_m (degree
 // <= 2), so measuring X_l from the element's corner centroid leaves S unchanged; it is done to keep
-// coordinates small against the element.  Derivatives of the interpolant at the targets are
-// applied one axis at a time (1D Lagrange matrices from the Gauss-Lobatto points; the triangle's
-// nodal derivative and edge-interpolation matrices).
+// coordinates small against the element.  Everything is evaluated one axis at a time: the
+// quadratic map through 1D quadratic Lagrange matrices (the triangle's 6 quadratic functions on
+// the prism), the interpolant's derivatives through 1D Lagrange matrices from the Gauss-Lobatto
+// points and the triangle's nodal derivative and edge-interpolation matrices.
 #include <cmath>
 #include <vector>
 
@@ -29,14 +30,33 @@ const int kHex27[27][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1}, {
                            {-1, 1, 1},   {0, -1, -1}, {1, 0, -1}, {0, 1, -1},  {-1, 0, -1}, {0, -1, 1}, {1, 0, 1},
                            {0, 1, 1},    {-1, 0, 1},  {-1, -1, 0}, {1, -1, 0}, {1, 1, 0},   {-1, 1, 0}, {-1, 0, 0},
                            {1, 0, 0},    {0, -1, 0},  {0, 1, 0},  {0, 0, -1},  {0, 0, 1},   {0, 0, 0}};
-// Prism: (triangle node code, zeta level); triangle codes 0..2 corners, 3..5 midpoints of 01 12 20.
+// Prism: (triangle function: 0..2 corners, 3..5 midpoints of 01 12 20; zeta level -1, 0, 1).
 const int kPrism18[18][2] = {{0, -1}, {1, -1}, {2, -1}, {0, 1}, {1, 1}, {2, 1}, {3, -1}, {4, -1}, {5, -1},
                              {3, 1},  {4, 1},  {5, 1},  {0, 0}, {1, 0}, {2, 0}, {3, 0},  {4, 0},  {5, 0}};
 
-inline void quad1d(double t, int c, double &L, double &dL) {
-  if (c < 0) { L = 0.5 * t * (t - 1.0); dL = t - 0.5; }
-  else if (c > 0) { L = 0.5 * t * (t + 1.0); dL = t + 0.5; }
-  else { L = 1.0 - t * t; dL = -2.0 * t; }
+// Quadratic Lagrange functions of the nodes -1, 0, 1 at t.
+void quad3(double t, double L[3], double dL[3]) {
+  L[0] = 0.5 * t * (t - 1.0); dL[0] = t - 0.5;
+  L[1] = 1.0 - t * t;         dL[1] = -2.0 * t;
+  L[2] = 0.5 * t * (t + 1.0); dL[2] = t + 0.5;
+}
+
+// The 6 quadratic triangle functions and their r, s derivatives at (r, s).
+void tri6(double r, double s, double T[6], double Tr[6], double Ts[6]) {
+  const double lam[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
+  const double dr[3] = {-0.5, 0.5, 0.0}, ds[3] = {-0.5, 0.0, 0.5};
+  for (int i = 0; i < 3; ++i) {
+    T[i] = lam[i] * (2 * lam[i] - 1);
+    Tr[i] = (4 * lam[i] - 1) * dr[i];
+    Ts[i] = (4 * lam[i] - 1) * ds[i];
+  }
+  const int mid[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+  for (int k = 0; k < 3; ++k) {
+    const int i = mid[k][0], j = mid[k][1];
+    T[3 + k] = 4 * lam[i] * lam[j];
+    Tr[3 + k] = 4 * (dr[i] * lam[j] + lam[i] * dr[j]);
+    Ts[3 + k] = 4 * (ds[i] * lam[j] + lam[i] * ds[j]);
+  }
 }
 
 // Lagrange polynomial a of the nodes g (n of them) and its derivative at x (product formulas).
@@ -54,71 +74,77 @@ void lagrange(const double *g, int n, int a, ld x, ld &L, ld &dL) {
   }
 }
 
-// out[i0 + M0 i1 + M0 M1 i2] = sum A0[i0][a] A1[i1][b] A2[i2][c] f[a + N b + N^2 c].
-void apply3(const double *f, int N, const double *A0, int M0, const double *A1, int M1, const double *A2, int M2,
-            double *out) {
-  std::vector<double> t1((size_t)M0 * N * N), t2((size_t)M0 * M1 * N);
-  for (int c = 0; c < N; ++c)
-    for (int b = 0; b < N; ++b)
+// out[i0 + M0 i1 + M0 M1 i2] = sum A0[i0][a] A1[i1][b] A2[i2][c] f[a + n b + n^2 c] (n inputs per axis).
+void apply3(const double *f, int n, const double *A0, int M0, const double *A1, int M1, const double *A2, int M2,
+            double *out, std::vector<double> &t1, std::vector<double> &t2) {
+  t1.resize((size_t)M0 * n * n);
+  t2.resize((size_t)M0 * M1 * n);
+  for (int c = 0; c < n; ++c)
+    for (int b = 0; b < n; ++b)
       for (int i = 0; i < M0; ++i) {
         double s = 0.0;
-        for (int a = 0; a < N; ++a) s += A0[i * N + a] * f[a + N * b + N * N * c];
-        t1[i + (size_t)M0 * (b + (size_t)N * c)] = s;
+        for (int a = 0; a < n; ++a) s += A0[i * n + a] * f[a + n * b + n * n * c];
+        t1[i + (size_t)M0 * (b + (size_t)n * c)] = s;
       }
-  for (int c = 0; c < N; ++c)
+  for (int c = 0; c < n; ++c)
     for (int j = 0; j < M1; ++j)
       for (int i = 0; i < M0; ++i) {
         double s = 0.0;
-        for (int b = 0; b < N; ++b) s += A1[j * N + b] * t1[i + (size_t)M0 * (b + (size_t)N * c)];
+        for (int b = 0; b < n; ++b) s += A1[j * n + b] * t1[i + (size_t)M0 * (b + (size_t)n * c)];
         t2[i + (size_t)M0 * (j + (size_t)M1 * c)] = s;
       }
   for (int k = 0; k < M2; ++k)
     for (int j = 0; j < M1; ++j)
       for (int i = 0; i < M0; ++i) {
         double s = 0.0;
-        for (int c = 0; c < N; ++c) s += A2[k * N + c] * t2[i + (size_t)M0 * (j + (size_t)M1 * c)];
+        for (int c = 0; c < n; ++c) s += A2[k * n + c] * t2[i + (size_t)M0 * (j + (size_t)M1 * c)];
         out[i + (size_t)M0 * (j + (size_t)M1 * k)] = s;
       }
 }
 
-// out[t + T z] = sum_q sum_k A[t][q] Z[z][k] f[q + Nt k]  (triangle part, then zeta part).
-void apply_tz(const double *f, int Nt, int N, const double *A, int T, const double *Z, int M, double *out) {
-  std::vector<double> t1((size_t)T * N);
-  for (int k = 0; k < N; ++k)
+// out[t + T z] = sum_q sum_k A[t][q] Z[z][k] f[q + nq k]  (triangle part, then zeta part).
+void apply_tz(const double *f, int nq, int nk, const double *A, int T, const double *Z, int M, double *out,
+              std::vector<double> &t1) {
+  t1.resize((size_t)T * nk);
+  for (int k = 0; k < nk; ++k)
     for (int t = 0; t < T; ++t) {
       double s = 0.0;
-      for (int q = 0; q < Nt; ++q) s += A[(size_t)t * Nt + q] * f[q + (size_t)Nt * k];
+      for (int q = 0; q < nq; ++q) s += A[(size_t)t * nq + q] * f[q + (size_t)nq * k];
       t1[t + (size_t)T * k] = s;
     }
   for (int z = 0; z < M; ++z)
     for (int t = 0; t < T; ++t) {
       double s = 0.0;
-      for (int k = 0; k < N; ++k) s += Z[z * N + k] * t1[t + (size_t)T * k];
+      for (int k = 0; k < nk; ++k) s += Z[z * nk + k] * t1[t + (size_t)T * k];
       out[t + (size_t)T * z] = s;
     }
 }
 
-// v[(n*3 + k)*nn + node] = (X_l - c_l) dX_m/dxi_k at the interpolation nodes, (n, m, l) cyclic.
-template <typename PointFn>
-void curl_fields(int p, int nn, int n_corner, const double (*X)[3], PointFn at_node, std::vector<double> &v) {
+double det3(const double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// v[(n*3 + k)*nn + node] = (X_l - c_l) dX_m/dxi_k, (n, m, l) cyclic, from x [3][nn] and
+// J [3 (component)][3 (direction)][nn] at the interpolation nodes.
+void curl_fields(int p, int nn, int n_corner, const double (*X)[3], const double *x, const double *J,
+                 std::vector<double> &v) {
   double c[3] = {0.0, 0.0, 0.0};
   if (p >= 2)
     for (int a = 0; a < n_corner; ++a)
       for (int i = 0; i < 3; ++i) c[i] += X[a][i] / n_corner;
-  v.assign((size_t)9 * nn, 0.0);
-  for (int node = 0; node < nn; ++node) {
-    double x[3], J[3][3];
-    at_node(node, x, J);
-    for (int n = 0; n < 3; ++n) {
-      const int m = (n + 1) % 3, l = (n + 2) % 3;
-      for (int k = 0; k < 3; ++k) v[(size_t)(n * 3 + k) * nn + node] = (x[l] - c[l]) * J[m][k];
-    }
+  v.resize((size_t)9 * nn);
+  for (int n = 0; n < 3; ++n) {
+    const int m = (n + 1) % 3, l = (n + 2) % 3;
+    for (int k = 0; k < 3; ++k)
+      for (int node = 0; node < nn; ++node)
+        v[(size_t)(n * 3 + k) * nn + node] = (x[(size_t)l * nn + node] - c[l]) * J[((size_t)m * 3 + k) * nn + node];
   }
 }
 
 }  // namespace
 
-void curved_ops(int p, const Basis1D &b, CurvedOps &o) {
+void curved_ops(int p, const Basis1D &b, const TriBasis *tb, CurvedOps &o) {
   const int N = p + 1;
   o.p = p;
   o.N = N;
@@ -137,108 +163,135 @@ void curved_ops(int p, const Basis1D &b, CurvedOps &o) {
       o.Ve[e][a] = (double)L;
       o.De[e][a] = (double)dL;
     }
-}
-
-void hex27_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]) {
-  for (int i = 0; i < 3; ++i) {
-    x[i] = 0.0;
-    for (int b = 0; b < 3; ++b) J[i][b] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    quad3(o.g[i], &o.Qg[i * 3], &o.dQg[i * 3]);
+    quad3(b.x[i], &o.Qx[i * 3], &o.dQx[i * 3]);
   }
-  for (int a = 0; a < 27; ++a) {
-    double L[3], dL[3];
-    for (int d = 0; d < 3; ++d) quad1d(xi[d], kHex27[a][d], L[d], dL[d]);
-    const double Nv = L[0] * L[1] * L[2];
-    const double dN[3] = {dL[0] * L[1] * L[2], L[0] * dL[1] * L[2], L[0] * L[1] * dL[2]};
-    for (int i = 0; i < 3; ++i) {
-      x[i] += Nv * X[a][i];
-      for (int b = 0; b < 3; ++b) J[i][b] += dN[b] * X[a][i];
+  quad3(-1.0, &o.Qe[0], &o.dQe[0]);
+  quad3(1.0, &o.Qe[3], &o.dQe[3]);
+  if (!tb) return;
+  const int Nt = tb->Nt;
+  o.Nt = Nt;
+  o.T.resize((size_t)Nt * 6);
+  o.Tr.resize((size_t)Nt * 6);
+  o.Ts.resize((size_t)Nt * 6);
+  for (int q = 0; q < Nt; ++q) tri6(tb->r[q], tb->s[q], &o.T[q * 6], &o.Tr[q * 6], &o.Ts[q * 6]);
+  for (int e = 0; e < 3; ++e) {
+    o.TE[e].resize((size_t)N * 6);
+    o.TEr[e].resize((size_t)N * 6);
+    o.TEs[e].resize((size_t)N * 6);
+    for (int a = 0; a < N; ++a) {
+      double r, s;
+      tri_edge_point(e, b.x[a], r, s);
+      tri6(r, s, &o.TE[e][a * 6], &o.TEr[e][a * 6], &o.TEs[e][a * 6]);
     }
   }
 }
 
-void prism18_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]) {
-  const double r = xi[0], s = xi[1];
-  const double lam[3] = {-(r + s) / 2, (1 + r) / 2, (1 + s) / 2};
-  const double dlr[3] = {-0.5, 0.5, 0.0}, dls[3] = {-0.5, 0.0, 0.5};
-  const int mid[3][2] = {{0, 1}, {1, 2}, {2, 0}};
-  for (int i = 0; i < 3; ++i) {
-    x[i] = 0.0;
-    for (int b = 0; b < 3; ++b) J[i][b] = 0.0;
-  }
-  for (int a = 0; a < 18; ++a) {
-    const int t = kPrism18[a][0];
-    double T, Tr, Ts;
-    if (t < 3) {             // corner: lambda (2 lambda - 1)
-      T = lam[t] * (2 * lam[t] - 1);
-      Tr = (4 * lam[t] - 1) * dlr[t];
-      Ts = (4 * lam[t] - 1) * dls[t];
-    } else {                 // edge midpoint: 4 lambda_i lambda_j
-      const int i = mid[t - 3][0], j = mid[t - 3][1];
-      T = 4 * lam[i] * lam[j];
-      Tr = 4 * (dlr[i] * lam[j] + lam[i] * dlr[j]);
-      Ts = 4 * (dls[i] * lam[j] + lam[i] * dls[j]);
-    }
-    double Z, dZ;
-    quad1d(xi[2], kPrism18[a][1], Z, dZ);
-    const double Nv = T * Z, dN[3] = {Tr * Z, Ts * Z, T * dZ};
-    for (int i = 0; i < 3; ++i) {
-      x[i] += Nv * X[a][i];
-      for (int b = 0; b < 3; ++b) J[i][b] += dN[b] * X[a][i];
-    }
-  }
-}
-
-void hex27_curl(const CurvedOps &o, const double (*X)[3], double *S_sol, double *S_face) {
+void hex27_geometry(const CurvedOps &o, const double (*X)[3], double *x_sol, double *det, double *S_sol,
+                    double *x_face, double *S_face) {
   const int N = o.N, N3 = N * N * N, Nf = N * N;
-  std::vector<double> v;
-  curl_fields(o.p, N3, 8, X, [&](int node, double x[3], double J[3][3]) {
-    const double xi[3] = {o.g[node % N], o.g[(node / N) % N], o.g[node / Nf]};
-    hex27_point(X, xi, x, J);
-  }, v);
-  std::vector<double> A(N3), B(N3);
-  // Solution points: the Gauss-Legendre tensor grid.
-  for (int n = 0; n < 3; ++n)
-    for (int i = 0; i < 3; ++i) {
-      const int j = (i + 1) % 3, k = (i + 2) % 3;
-      const double *M[3];
-      for (int d = 0; d < 3; ++d) M[d] = d == j ? o.D : o.V;
-      apply3(&v[(size_t)(n * 3 + k) * N3], N, M[0], N, M[1], N, M[2], N, A.data());
-      for (int d = 0; d < 3; ++d) M[d] = d == k ? o.D : o.V;
-      apply3(&v[(size_t)(n * 3 + j) * N3], N, M[0], N, M[1], N, M[2], N, B.data());
-      for (int m = 0; m < N3; ++m) S_sol[(size_t)(i * 3 + n) * N3 + m] = -(A[m] - B[m]);
+  std::vector<double> t1, t2;
+  // Node coordinates as 3 x 3 x 3 tensors per component.
+  double Xt[3][27];
+  for (int a = 0; a < 27; ++a)
+    for (int c = 0; c < 3; ++c) Xt[c][(kHex27[a][0] + 1) + 3 * (kHex27[a][1] + 1) + 9 * (kHex27[a][2] + 1)] = X[a][c];
+  // Position and gradient of the map at a tensor target set (1D value / derivative matrices).
+  auto map_at = [&](const double *Q[3], const double *dQ[3], const int M[3], double *x, double *J) {
+    const int nt = M[0] * M[1] * M[2];
+    for (int c = 0; c < 3; ++c) {
+      apply3(Xt[c], 3, Q[0], M[0], Q[1], M[1], Q[2], M[2], x + (size_t)c * nt, t1, t2);
+      if (!J) continue;
+      for (int d = 0; d < 3; ++d) {
+        const double *A[3] = {Q[0], Q[1], Q[2]};
+        A[d] = dQ[d];
+        apply3(Xt[c], 3, A[0], M[0], A[1], M[1], A[2], M[2], J + ((size_t)c * 3 + d) * nt, t1, t2);
+      }
     }
-  // Faces: axis d at its end s, the tangential axes on the Gauss-Legendre points.
+  };
+  // Curl fields at the Gauss-Lobatto nodes.
+  std::vector<double> xg((size_t)3 * N3), Jg((size_t)9 * N3), v;
+  {
+    const double *Q[3] = {o.Qg, o.Qg, o.Qg}, *dQ[3] = {o.dQg, o.dQg, o.dQg};
+    const int M[3] = {N, N, N};
+    map_at(Q, dQ, M, xg.data(), Jg.data());
+  }
+  curl_fields(o.p, N3, 8, X, xg.data(), Jg.data(), v);
+  std::vector<double> A(N3), B(N3);
+  // Row i of S at a tensor target set: axis d takes (value V, derivative D) matrices Vm[d], Dm[d].
+  auto srow = [&](int i, const double *Vm[3], const double *Dm[3], const int M[3], double *out, size_t stride) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3, nt = M[0] * M[1] * M[2];
+    for (int n = 0; n < 3; ++n) {
+      const double *Aj[3] = {Vm[0], Vm[1], Vm[2]}, *Ak[3] = {Vm[0], Vm[1], Vm[2]};
+      Aj[j] = Dm[j];
+      Ak[k] = Dm[k];
+      apply3(&v[(size_t)(n * 3 + k) * N3], N, Aj[0], M[0], Aj[1], M[1], Aj[2], M[2], A.data(), t1, t2);
+      apply3(&v[(size_t)(n * 3 + j) * N3], N, Ak[0], M[0], Ak[1], M[1], Ak[2], M[2], B.data(), t1, t2);
+      for (int r = 0; r < nt; ++r) out[(size_t)(i * 3 + n) * stride + r] = -(A[r] - B[r]);
+    }
+  };
+  // Solution points: position, |J| and all of S.
+  {
+    const double *Q[3] = {o.Qx, o.Qx, o.Qx}, *dQ[3] = {o.dQx, o.dQx, o.dQx};
+    const int M[3] = {N, N, N};
+    std::vector<double> xs((size_t)3 * N3), Js((size_t)9 * N3);
+    map_at(Q, dQ, M, xs.data(), Js.data());
+    for (int m = 0; m < N3; ++m) {
+      double J[3][3];
+      for (int c = 0; c < 3; ++c) {
+        x_sol[(size_t)m * 3 + c] = xs[(size_t)c * N3 + m];
+        for (int d = 0; d < 3; ++d) J[c][d] = Js[((size_t)c * 3 + d) * N3 + m];
+      }
+      det[m] = det3(J);
+    }
+    const double *Vm[3] = {o.V, o.V, o.V}, *Dm[3] = {o.D, o.D, o.D};
+    for (int i = 0; i < 3; ++i) srow(i, Vm, Dm, M, S_sol, N3);
+  }
+  // Faces: axis d at its end e, the tangential axes on the Gauss-Legendre points; the flux point
+  // r = a + N b runs over the two tangential axes in increasing order, so it is the tensor index.
   for (int f = 0; f < 6; ++f) {
     const int d = f / 2, e = f % 2;
-    for (int n = 0; n < 3; ++n)
-      for (int i = 0; i < 3; ++i) {
-        const int j = (i + 1) % 3, k = (i + 2) % 3;
-        const double *M[3];
-        int Ms[3];
-        for (int q = 0; q < 3; ++q) {
-          Ms[q] = q == d ? 1 : N;
-          M[q] = q == d ? (q == j ? o.De[e] : o.Ve[e]) : (q == j ? o.D : o.V);
-        }
-        apply3(&v[(size_t)(n * 3 + k) * N3], N, M[0], Ms[0], M[1], Ms[1], M[2], Ms[2], A.data());
-        for (int q = 0; q < 3; ++q) M[q] = q == d ? (q == k ? o.De[e] : o.Ve[e]) : (q == k ? o.D : o.V);
-        apply3(&v[(size_t)(n * 3 + j) * N3], N, M[0], Ms[0], M[1], Ms[1], M[2], Ms[2], B.data());
-        for (int r = 0; r < Nf; ++r) S_face[((size_t)f * 9 + i * 3 + n) * Nf + r] = -(A[r] - B[r]);
-      }
+    const double *Q[3] = {o.Qx, o.Qx, o.Qx}, *Vm[3] = {o.V, o.V, o.V}, *Dm[3] = {o.D, o.D, o.D};
+    Q[d] = &o.Qe[3 * e];
+    Vm[d] = o.Ve[e];
+    Dm[d] = o.De[e];
+    int M[3] = {N, N, N};
+    M[d] = 1;
+    std::vector<double> xf((size_t)3 * Nf);
+    map_at(Q, nullptr, M, xf.data(), nullptr);
+    for (int r = 0; r < Nf; ++r)
+      for (int c = 0; c < 3; ++c) x_face[((size_t)f * Nf + r) * 3 + c] = xf[(size_t)c * Nf + r];
+    srow(d, Vm, Dm, M, S_face + (size_t)f * 9 * Nf, Nf);
   }
 }
 
-void prism18_curl(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], double *S_sol, double *S_face) {
+void prism18_geometry(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], double *x_sol, double *det,
+                      double *S_sol, double *x_face, double *S_face) {
   const int N = o.N, Nt = tb.Nt, Np = Nt * N, Nf = N * N;
-  std::vector<double> v;
-  curl_fields(o.p, Np, 6, X, [&](int node, double x[3], double J[3][3]) {
-    const double xi[3] = {tb.r[node % Nt], tb.s[node % Nt], o.g[node / Nt]};
-    prism18_point(X, xi, x, J);
-  }, v);
-  // Triangle-part operators at the three kinds of targets: value / d/dr / d/ds.
+  std::vector<double> t1;
+  double Xt[3][18];   // [component][triangle function + 6 level]
+  for (int a = 0; a < 18; ++a)
+    for (int c = 0; c < 3; ++c) Xt[c][kPrism18[a][0] + 6 * (kPrism18[a][1] + 1)] = X[a][c];
+  // Map at (triangle targets via T/Tr/Ts [T][6]) x (zeta targets via Z/dZ [M][3]).
+  auto map_at = [&](const double *Tv, const double *Trm, const double *Tsm, int T, const double *Z, const double *dZ,
+                    int M, double *x, double *J) {
+    const int nt = T * M;
+    for (int c = 0; c < 3; ++c) {
+      apply_tz(Xt[c], 6, 3, Tv, T, Z, M, x + (size_t)c * nt, t1);
+      if (!J) continue;
+      apply_tz(Xt[c], 6, 3, Trm, T, Z, M, J + ((size_t)c * 3 + 0) * nt, t1);
+      apply_tz(Xt[c], 6, 3, Tsm, T, Z, M, J + ((size_t)c * 3 + 1) * nt, t1);
+      apply_tz(Xt[c], 6, 3, Tv, T, dZ, M, J + ((size_t)c * 3 + 2) * nt, t1);
+    }
+  };
+  std::vector<double> xg((size_t)3 * Np), Jg((size_t)9 * Np), v;
+  map_at(o.T.data(), o.Tr.data(), o.Ts.data(), Nt, o.Qg, o.dQg, N, xg.data(), Jg.data());
+  curl_fields(o.p, Np, 6, X, xg.data(), Jg.data(), v);
+  // Triangle-part operators: value / d/dr / d/ds at the nodes and at each edge's Gauss points.
   std::vector<double> I((size_t)Nt * Nt, 0.0);
   for (int q = 0; q < Nt; ++q) I[(size_t)q * Nt + q] = 1.0;
-  const double *Tsol[3] = {I.data(), tb.Dr.data(), tb.Ds.data()};
-  std::vector<double> Ed[3][3];   // edge e: value, d/dr, d/ds at its Gauss points [N][Nt]
+  const double *Tn[3] = {I.data(), tb.Dr.data(), tb.Ds.data()};
+  std::vector<double> Ed[3][3];
   for (int e = 0; e < 3; ++e) {
     Ed[e][0] = tb.E[e];
     for (int w = 1; w < 3; ++w) {
@@ -253,29 +306,45 @@ void prism18_curl(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], 
     }
   }
   std::vector<double> A(Np), B(Np);
-  // d/dxi_w of field F at targets (triangle operator set Tw, zeta value/derivative matrices).
+  // d/dxi_w of a field at targets (triangle operators Tw[value, r, s], zeta value/derivative).
   auto deriv = [&](const double *F, int w, const double *const *Tw, int T, const double *Zv, const double *Zd, int M,
-                   double *out) {
-    apply_tz(F, Nt, N, Tw[w < 2 ? w + 1 : 0], T, w == 2 ? Zd : Zv, M, out);
-  };
-  for (int n = 0; n < 3; ++n)
-    for (int i = 0; i < 3; ++i) {
-      const int j = (i + 1) % 3, k = (i + 2) % 3;
-      deriv(&v[(size_t)(n * 3 + k) * Np], j, Tsol, Nt, o.V, o.D, N, A.data());
-      deriv(&v[(size_t)(n * 3 + j) * Np], k, Tsol, Nt, o.V, o.D, N, B.data());
-      for (int m = 0; m < Np; ++m) S_sol[(size_t)(i * 3 + n) * Np + m] = -(A[m] - B[m]);
-      for (int f = 0; f < 2; ++f) {     // triangles at zeta = -1, +1
-        deriv(&v[(size_t)(n * 3 + k) * Np], j, Tsol, Nt, o.Ve[f], o.De[f], 1, A.data());
-        deriv(&v[(size_t)(n * 3 + j) * Np], k, Tsol, Nt, o.Ve[f], o.De[f], 1, B.data());
-        for (int q = 0; q < Nt; ++q) S_face[((size_t)f * 9 + i * 3 + n) * Nf + q] = -(A[q] - B[q]);
-      }
-      for (int e = 0; e < 3; ++e) {     // quadrilaterals: edge Gauss points x zeta Gauss points
-        const double *Te[3] = {Ed[e][0].data(), Ed[e][1].data(), Ed[e][2].data()};
-        deriv(&v[(size_t)(n * 3 + k) * Np], j, Te, N, o.V, o.D, N, A.data());
-        deriv(&v[(size_t)(n * 3 + j) * Np], k, Te, N, o.V, o.D, N, B.data());
-        for (int r = 0; r < Nf; ++r) S_face[((size_t)(2 + e) * 9 + i * 3 + n) * Nf + r] = -(A[r] - B[r]);
-      }
+                   double *out) { apply_tz(F, Nt, N, Tw[w < 2 ? w + 1 : 0], T, w == 2 ? Zd : Zv, M, out, t1); };
+  auto srow = [&](int i, const double *const *Tw, int T, const double *Zv, const double *Zd, int M, double *out,
+                  size_t stride) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    for (int n = 0; n < 3; ++n) {
+      deriv(&v[(size_t)(n * 3 + k) * Np], j, Tw, T, Zv, Zd, M, A.data());
+      deriv(&v[(size_t)(n * 3 + j) * Np], k, Tw, T, Zv, Zd, M, B.data());
+      for (int r = 0; r < T * M; ++r) out[(size_t)(i * 3 + n) * stride + r] = -(A[r] - B[r]);
     }
+  };
+  {
+    std::vector<double> xs((size_t)3 * Np), Js((size_t)9 * Np);
+    map_at(o.T.data(), o.Tr.data(), o.Ts.data(), Nt, o.Qx, o.dQx, N, xs.data(), Js.data());
+    for (int m = 0; m < Np; ++m) {
+      double J[3][3];
+      for (int c = 0; c < 3; ++c) {
+        x_sol[(size_t)m * 3 + c] = xs[(size_t)c * Np + m];
+        for (int d = 0; d < 3; ++d) J[c][d] = Js[((size_t)c * 3 + d) * Np + m];
+      }
+      det[m] = det3(J);
+    }
+    for (int i = 0; i < 3; ++i) srow(i, Tn, Nt, o.V, o.D, N, S_sol, Np);
+  }
+  std::vector<double> xf((size_t)3 * Nf);
+  for (int f = 0; f < 2; ++f) {            // triangles at zeta = -1, +1: row 2 of S
+    map_at(o.T.data(), nullptr, nullptr, Nt, &o.Qe[3 * f], nullptr, 1, xf.data(), nullptr);
+    for (int r = 0; r < Nt; ++r)
+      for (int c = 0; c < 3; ++c) x_face[((size_t)f * Nf + r) * 3 + c] = xf[(size_t)c * Nt + r];
+    srow(2, Tn, Nt, o.Ve[f], o.De[f], 1, S_face + (size_t)f * 9 * Nf, Nf);
+  }
+  for (int e = 0; e < 3; ++e) {            // quadrilaterals (edge Gauss points x zeta Gauss points): rows 0, 1
+    map_at(o.TE[e].data(), nullptr, nullptr, N, o.Qx, nullptr, N, xf.data(), nullptr);
+    for (int r = 0; r < Nf; ++r)
+      for (int c = 0; c < 3; ++c) x_face[((size_t)(2 + e) * Nf + r) * 3 + c] = xf[(size_t)c * Nf + r];
+    const double *Te[3] = {Ed[e][0].data(), Ed[e][1].data(), Ed[e][2].data()};
+    for (int i = 0; i < 2; ++i) srow(i, Te, N, o.V, o.D, N, S_face + (size_t)(2 + e) * 9 * Nf, Nf);
+  }
 }
 
 }  // namespace frx

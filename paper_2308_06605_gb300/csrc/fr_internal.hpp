@@ -50,20 +50,28 @@ void gll_nodes(int p, double *x);
 // Quadratic (curved) element geometry (fr_curved.cpp).  1D operators from the p + 1
 // Gauss-Lobatto points g to the Gauss-Legendre points x of the line and to its ends.
 struct CurvedOps {
-  int p = 0, N = 0;
+  int p = 0, N = 0, Nt = 0;
   double g[kMaxN];
   double V[kMaxN * kMaxN], D[kMaxN * kMaxN];   // [i][a] = l_a(x_i), l_a'(x_i)
   double Ve[2][kMaxN], De[2][kMaxN];           // l_a(-1), l_a'(-1); l_a(+1), l_a'(+1)
+  // Quadratic Lagrange functions of the nodes -1, 0, 1 (value, derivative) at the Gauss-Lobatto
+  // points [N][3], the Gauss-Legendre points [N][3] and the ends [2][3].
+  double Qg[kMaxN * 3], dQg[kMaxN * 3], Qx[kMaxN * 3], dQx[kMaxN * 3], Qe[6], dQe[6];
+  // Prisms: the 6 quadratic triangle functions (corners 0 1 2, midpoints 01 12 20) and their r, s
+  // derivatives at the triangle nodes [Nt][6] and at the Gauss points of each edge [3][N][6].
+  std::vector<double> T, Tr, Ts, TE[3], TEr[3], TEs[3];
 };
-void curved_ops(int p, const Basis1D &b, CurvedOps &o);
-// Position and dx_i/dxi_b of a 27-node hexahedron / 18-node prism at a reference point.
-void hex27_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]);
-void prism18_point(const double (*X)[3], const double xi[3], double x[3], double J[3][3]);
-// Conservative-curl metric terms, S[(d*3 + j)] = |J| dxi_d/dx_j, of one element: at the solution
-// points (S_sol [9][Np]) and at the flux points of every face (S_face [faces][9][N^2], a
-// triangular face uses its first Nt slots).
-void hex27_curl(const CurvedOps &o, const double (*X)[3], double *S_sol, double *S_face);
-void prism18_curl(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], double *S_sol, double *S_face);
+void curved_ops(int p, const Basis1D &b, const TriBasis *tb, CurvedOps &o);
+// Geometry of one quadratic element (node orders as documented in fr.h): position x and |J| at
+// the solution points (x_sol [Np][3], det [Np]), the conservative-curl metric terms
+// S[(d*3 + j)] = |J| dxi_d/dx_j at the solution points (S_sol [9][Np]), and at the flux points of
+// every face the position (x_face [faces][N^2][3]) and the rows of S that make up the face's
+// reference normal (S_face [faces][9][N^2]; other rows are left untouched; a triangular face uses
+// its first Nt slots).
+void hex27_geometry(const CurvedOps &o, const double (*X)[3], double *x_sol, double *det, double *S_sol,
+                    double *x_face, double *S_face);
+void prism18_geometry(const CurvedOps &o, const TriBasis &tb, const double (*X)[3], double *x_sol, double *det,
+                      double *S_sol, double *x_face, double *S_face);
 
 // Offsets (in values) of the per-mesh prism operator table for line order N (Nt = N(N+1)/2):
 // Dr, Ds (triangle derivatives), Drt, Dst (with the own-flux correction of the quadrilateral

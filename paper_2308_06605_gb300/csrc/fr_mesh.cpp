@@ -4,6 +4,9 @@
 // coupled faces are adjacent, then paired).
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <climits>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <unordered_map>
@@ -299,6 +302,24 @@ struct FaceGeo {
   int ref[4][2];
 };
 
+// Runs body(begin, end) over [0, n) split across host threads (serially for small n).
+template <typename F>
+static void parallel_for(int64_t n, F body) {
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = nt == 0 ? 1 : (nt > 32 ? 32 : nt);
+  if (n < 512 || nt <= 1) {
+    body(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int64_t b = (int64_t)t * chunk, e = std::min<int64_t>(n, b + chunk);
+    if (b < e) th.emplace_back(body, b, e);
+  }
+  for (std::thread &x : th) x.join();
+}
+
 fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &err) {
   char buf[256];
   const int p = desc->p;
@@ -573,7 +594,9 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
       return FR_EMESH;
     }
 
-  // Geometry at solution and flux points.
+  // Geometry at solution and flux points, element by element on host threads (every element
+  // writes only its own metrics, points and lift factors, and the normals of the interfaces whose
+  // side 0 it is).
   Basis1D b = make_basis(p);
   m.metrics.assign((size_t)E * 10 * Np, 0.0);
   m.liftfac.assign((size_t)E * 6 * 3 * Nf, 0.0);
@@ -584,164 +607,188 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   // Quadratic elements: positions and |J| from the element map, S from the curl form.
   const bool curved_h = hn == 27, curved_p = pn == 18;
   CurvedOps cops;
-  if (curved_h || curved_p) curved_ops(p, b, cops);
-  std::vector<double> Ssol, Sface;
-  for (int64_t e = 0; e < E; ++e) {
-    double X[27][3];
-    elem_verts(e, X, hn);
-    if (curved_h) {
-      Ssol.resize((size_t)9 * Np);
-      Sface.resize((size_t)6 * 9 * Nf);
-      hex27_curl(cops, X, Ssol.data(), Sface.data());
+  if (curved_h || curved_p) curved_ops(p, b, Ep > 0 ? &tb : nullptr, cops);
+  std::atomic<int64_t> bad_elem(INT64_MAX);
+  auto store_normal = [&](int64_t I, int r, const double n[3]) {
+    double nn = 0.0;
+    for (int jj = 0; jj < 3; ++jj) {
+      m.normals[((size_t)I * 4 + jj) * Nf + r] = n[jj];
+      nn += n[jj] * n[jj];
     }
-    // Geometry at a reference point: x, S, |J|; `slot` indexes S_sol (face < 0) or S_face[face].
-    auto geo = [&](const double xi[3], int face, int slot, double x[3], double S[3][3], double &det) {
-      if (!curved_h) {
-        Jac g = trilinear(X, xi);
-        adjugate_rows(g.J, S, det);
-        for (int c = 0; c < 3; ++c) x[c] = g.x[c];
-        return;
-      }
-      double J[3][3], Sa[3][3];
-      hex27_point(X, xi, x, J);
-      adjugate_rows(J, Sa, det);
-      for (int d = 0; d < 3; ++d)
-        for (int jj = 0; jj < 3; ++jj)
-          S[d][jj] = face < 0 ? Ssol[(size_t)(d * 3 + jj) * Np + slot] : Sface[((size_t)face * 9 + d * 3 + jj) * Nf + slot];
-    };
-    double vol = 0.0;
-    double *met = &m.metrics[(size_t)e * 10 * Np];
-    for (int k = 0; k < N; ++k)
-      for (int j = 0; j < N; ++j)
-        for (int i = 0; i < N; ++i) {
-          int mm = i + N * j + N * N * k;
-          double xi[3] = {b.x[i], b.x[j], b.x[k]};
-          double S[3][3], det, gx[3];
-          geo(xi, -1, mm, gx, S, det);
-          if (!(det > 0.0)) {
-            snprintf(buf, sizeof buf, "non-positive Jacobian in element %lld", (long long)e);
-            err = buf;
-            return FR_EMESH;
-          }
-          for (int d = 0; d < 3; ++d)
-            for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Np + mm] = S[d][jj];
-          met[9 * Np + mm] = 1.0 / det;
-          vol += b.w[i] * b.w[j] * b.w[k] * det;
-          for (int c = 0; c < 3; ++c) m.xsol[((size_t)e * Np + mm) * 3 + c] = gx[c];
-        }
-    m.h[e] = std::cbrt(vol);
-    for (int f = 0; f < 6; ++f) {
-      int d, s, t0, t1;
-      face_axes(f, d, s, t0, t1);
-      const double *lv = (s > 0) ? b.lp : b.lm;
-      const double *hv = (s > 0) ? b.hp : b.hm;
-      int packed = m.ef[e * 6 + f];
-      int64_t I = packed >> 4;
-      int side = (packed >> 3) & 1;
-      for (int bb = 0; bb < N; ++bb)
-        for (int aa = 0; aa < N; ++aa) {
-          int r = aa + N * bb;
-          double acc[3] = {0, 0, 0};
-          for (int c = 0; c < N; ++c) {
-            int idx[3];
-            idx[d] = c; idx[t0] = aa; idx[t1] = bb;
-            int mm = idx[0] + N * idx[1] + N * N * idx[2];
-            for (int jj = 0; jj < 3; ++jj)
-              acc[jj] += lv[c] * hv[c] * met[(d * 3 + jj) * Np + mm] * met[9 * Np + mm];
-          }
-          for (int jj = 0; jj < 3; ++jj)
-            m.liftfac[(((size_t)e * 6 + f) * 3 + jj) * Nf + r] = s * acc[jj];
-          double xi[3];
-          xi[d] = (double)s; xi[t0] = b.x[aa]; xi[t1] = b.x[bb];
-          double S[3][3], det, gx[3];
-          geo(xi, f, r, gx, S, det);
-          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(e, f) * Nf + r) * 3 + c] = gx[c];
-          if (side == 0) {
-            double nn = 0.0;
-            for (int jj = 0; jj < 3; ++jj) {
-              m.normals[((size_t)I * 4 + jj) * Nf + r] = s * S[d][jj];
-              nn += S[d][jj] * S[d][jj];
+    m.normals[((size_t)I * 4 + 3) * Nf + r] = std::sqrt(nn);
+  };
+  auto note_bad = [&](int64_t g) {
+    int64_t cur = bad_elem.load();
+    while (g < cur && !bad_elem.compare_exchange_weak(cur, g)) {
+    }
+  };
+  parallel_for(E, [&](int64_t e0, int64_t e1) {
+    std::vector<double> xs((size_t)3 * Np), dets(Np), Ssol((size_t)9 * Np), xfc((size_t)6 * Nf * 3),
+        Sface((size_t)6 * 9 * Nf);
+    for (int64_t e = e0; e < e1; ++e) {
+      double X[27][3];
+      elem_verts(e, X, hn);
+      if (curved_h) hex27_geometry(cops, X, xs.data(), dets.data(), Ssol.data(), xfc.data(), Sface.data());
+      double vol = 0.0;
+      double *met = &m.metrics[(size_t)e * 10 * Np];
+      bool ok = true;
+      for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+          for (int i = 0; i < N; ++i) {
+            const int mm = i + N * j + N * N * k;
+            double S[3][3], det, gx[3];
+            if (curved_h) {
+              det = dets[mm];
+              for (int d = 0; d < 3; ++d)
+                for (int jj = 0; jj < 3; ++jj) S[d][jj] = Ssol[(size_t)(d * 3 + jj) * Np + mm];
+              for (int c = 0; c < 3; ++c) gx[c] = xs[(size_t)mm * 3 + c];
+            } else {
+              const double xi[3] = {b.x[i], b.x[j], b.x[k]};
+              Jac g = trilinear(X, xi);
+              adjugate_rows(g.J, S, det);
+              for (int c = 0; c < 3; ++c) gx[c] = g.x[c];
             }
-            m.normals[((size_t)I * 4 + 3) * Nf + r] = std::sqrt(nn);
+            if (!(det > 0.0)) ok = false;
+            for (int d = 0; d < 3; ++d)
+              for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Np + mm] = S[d][jj];
+            met[9 * Np + mm] = 1.0 / det;
+            vol += b.w[i] * b.w[j] * b.w[k] * det;
+            for (int c = 0; c < 3; ++c) m.xsol[((size_t)e * Np + mm) * 3 + c] = gx[c];
           }
-        }
+      if (!ok) {
+        note_bad(e);
+        continue;
+      }
+      m.h[e] = std::cbrt(vol);
+      for (int f = 0; f < 6; ++f) {
+        int d, s, t0, t1;
+        face_axes(f, d, s, t0, t1);
+        const double *lv = (s > 0) ? b.lp : b.lm;
+        const double *hv = (s > 0) ? b.hp : b.hm;
+        const int packed = m.ef[e * 6 + f];
+        const int64_t I = packed >> 4;
+        const int side = (packed >> 3) & 1;
+        for (int bb = 0; bb < N; ++bb)
+          for (int aa = 0; aa < N; ++aa) {
+            const int r = aa + N * bb;
+            double acc[3] = {0, 0, 0};
+            for (int c = 0; c < N; ++c) {
+              int idx[3];
+              idx[d] = c; idx[t0] = aa; idx[t1] = bb;
+              const int mm = idx[0] + N * idx[1] + N * N * idx[2];
+              for (int jj = 0; jj < 3; ++jj)
+                acc[jj] += lv[c] * hv[c] * met[(d * 3 + jj) * Np + mm] * met[9 * Np + mm];
+            }
+            for (int jj = 0; jj < 3; ++jj)
+              m.liftfac[(((size_t)e * 6 + f) * 3 + jj) * Nf + r] = s * acc[jj];
+            double Sd[3], gx[3];
+            if (curved_h) {
+              for (int jj = 0; jj < 3; ++jj) Sd[jj] = Sface[((size_t)f * 9 + d * 3 + jj) * Nf + r];
+              for (int c = 0; c < 3; ++c) gx[c] = xfc[((size_t)f * Nf + r) * 3 + c];
+            } else {
+              double xi[3], S[3][3], det;
+              xi[d] = (double)s; xi[t0] = b.x[aa]; xi[t1] = b.x[bb];
+              Jac g = trilinear(X, xi);
+              adjugate_rows(g.J, S, det);
+              for (int jj = 0; jj < 3; ++jj) Sd[jj] = S[d][jj];
+              for (int c = 0; c < 3; ++c) gx[c] = g.x[c];
+            }
+            for (int c = 0; c < 3; ++c) fx[((size_t)face_index(e, f) * Nf + r) * 3 + c] = gx[c];
+            if (side == 0) {
+              const double n[3] = {s * Sd[0], s * Sd[1], s * Sd[2]};
+              store_normal(I, r, n);
+            }
+          }
+      }
     }
+  });
+  if (bad_elem.load() != INT64_MAX) {
+    snprintf(buf, sizeof buf, "non-positive Jacobian in element %lld", (long long)bad_elem.load());
+    err = buf;
+    return FR_EMESH;
   }
   if (Ep > 0) {
     // Prisms: solution points (triangle node q, line point k) -> m = q + Nt k.
     m.metrics_p.assign((size_t)Ep * 10 * Npp, 0.0);
-    for (int64_t ep = 0; ep < Ep; ++ep) {
-      const int64_t g = E + ep;
-      double X[18][3];
-      prism_verts(ep, X, pn);
-      if (curved_p) {
-        Ssol.resize((size_t)9 * Npp);
-        Sface.resize((size_t)5 * 9 * Nf);
-        prism18_curl(cops, tb, X, Ssol.data(), Sface.data());
-      }
-      auto pgeo = [&](const double xi[3], int face, int slot, double x[3], double S[3][3], double &det) {
-        if (!curved_p) {
-          Jac jg = prism_map(X, xi);
-          adjugate_rows(jg.J, S, det);
-          for (int c = 0; c < 3; ++c) x[c] = jg.x[c];
-          return;
-        }
-        double J[3][3], Sa[3][3];
-        prism18_point(X, xi, x, J);
-        adjugate_rows(J, Sa, det);
-        for (int d = 0; d < 3; ++d)
-          for (int jj = 0; jj < 3; ++jj)
-            S[d][jj] = face < 0 ? Ssol[(size_t)(d * 3 + jj) * Npp + slot]
-                                : Sface[((size_t)face * 9 + d * 3 + jj) * Nf + slot];
-      };
-      double vol = 0.0;
-      double *met = &m.metrics_p[(size_t)ep * 10 * Npp];
-      for (int k = 0; k < N; ++k)
-        for (int q = 0; q < Nt; ++q) {
-          const int mm = q + Nt * k;
-          const double xi[3] = {tb.r[q], tb.s[q], b.x[k]};
-          double S[3][3], det, gx[3];
-          pgeo(xi, -1, mm, gx, S, det);
-          if (!(det > 0.0)) {
-            snprintf(buf, sizeof buf, "non-positive Jacobian in prism %lld", (long long)ep);
-            err = buf;
-            return FR_EMESH;
-          }
-          for (int d = 0; d < 3; ++d)
-            for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Npp + mm] = S[d][jj];
-          met[9 * Npp + mm] = 1.0 / det;
-          vol += tb.wT[q] * b.w[k] * det;
-          for (int c = 0; c < 3; ++c) m.xsol[((size_t)E * Np + (size_t)ep * Npp + mm) * 3 + c] = gx[c];
-        }
-      m.h[g] = std::cbrt(vol);
-      for (int f = 0; f < 5; ++f) {
-        const int packed = m.ef_p[ep * 5 + f];
-        const int64_t I = packed >> 4;
-        const int side = (packed >> 3) & 1;
-        const int nq = f < 2 ? Nt : Nf;
-        for (int r = 0; r < nq; ++r) {
-          double xi[3];
-          if (f < 2) {
-            xi[0] = tb.r[r]; xi[1] = tb.s[r]; xi[2] = f == 0 ? -1.0 : 1.0;
-          } else {
-            tri_edge_point(f - 2, b.x[r % N], xi[0], xi[1]);
-            xi[2] = b.x[r / N];
-          }
-          double S[3][3], det, gx[3];
-          pgeo(xi, f, r, gx, S, det);
-          for (int c = 0; c < 3; ++c) fx[((size_t)face_index(g, f) * Nf + r) * 3 + c] = gx[c];
-          if (side == 0) {
-            double nn = 0.0;
-            for (int jj = 0; jj < 3; ++jj) {
-              double v = 0.0;
-              for (int d = 0; d < 3; ++d) v += kPrismNormal[f][d] * S[d][jj];
-              m.normals[((size_t)I * 4 + jj) * Nf + r] = v;
-              nn += v * v;
+    parallel_for(Ep, [&](int64_t e0, int64_t e1) {
+      std::vector<double> xs((size_t)3 * Npp), dets(Npp), Ssol((size_t)9 * Npp), xfc((size_t)5 * Nf * 3),
+          Sface((size_t)5 * 9 * Nf);
+      for (int64_t ep = e0; ep < e1; ++ep) {
+        const int64_t g = E + ep;
+        double X[18][3];
+        prism_verts(ep, X, pn);
+        if (curved_p) prism18_geometry(cops, tb, X, xs.data(), dets.data(), Ssol.data(), xfc.data(), Sface.data());
+        double vol = 0.0;
+        double *met = &m.metrics_p[(size_t)ep * 10 * Npp];
+        bool ok = true;
+        for (int k = 0; k < N; ++k)
+          for (int q = 0; q < Nt; ++q) {
+            const int mm = q + Nt * k;
+            double S[3][3], det, gx[3];
+            if (curved_p) {
+              det = dets[mm];
+              for (int d = 0; d < 3; ++d)
+                for (int jj = 0; jj < 3; ++jj) S[d][jj] = Ssol[(size_t)(d * 3 + jj) * Npp + mm];
+              for (int c = 0; c < 3; ++c) gx[c] = xs[(size_t)mm * 3 + c];
+            } else {
+              const double xi[3] = {tb.r[q], tb.s[q], b.x[k]};
+              Jac jg = prism_map(X, xi);
+              adjugate_rows(jg.J, S, det);
+              for (int c = 0; c < 3; ++c) gx[c] = jg.x[c];
             }
-            m.normals[((size_t)I * 4 + 3) * Nf + r] = std::sqrt(nn);
+            if (!(det > 0.0)) ok = false;
+            for (int d = 0; d < 3; ++d)
+              for (int jj = 0; jj < 3; ++jj) met[(d * 3 + jj) * Npp + mm] = S[d][jj];
+            met[9 * Npp + mm] = 1.0 / det;
+            vol += tb.wT[q] * b.w[k] * det;
+            for (int c = 0; c < 3; ++c) m.xsol[((size_t)E * Np + (size_t)ep * Npp + mm) * 3 + c] = gx[c];
+          }
+        if (!ok) {
+          note_bad(g);
+          continue;
+        }
+        m.h[g] = std::cbrt(vol);
+        for (int f = 0; f < 5; ++f) {
+          const int packed = m.ef_p[ep * 5 + f];
+          const int64_t I = packed >> 4;
+          const int side = (packed >> 3) & 1;
+          const int nq = f < 2 ? Nt : Nf;
+          for (int r = 0; r < nq; ++r) {
+            double S[3][3], gx[3];
+            if (curved_p) {
+              for (int d = 0; d < 3; ++d)
+                for (int jj = 0; jj < 3; ++jj) S[d][jj] = Sface[((size_t)f * 9 + d * 3 + jj) * Nf + r];
+              for (int c = 0; c < 3; ++c) gx[c] = xfc[((size_t)f * Nf + r) * 3 + c];
+            } else {
+              double xi[3], det;
+              if (f < 2) {
+                xi[0] = tb.r[r]; xi[1] = tb.s[r]; xi[2] = f == 0 ? -1.0 : 1.0;
+              } else {
+                tri_edge_point(f - 2, b.x[r % N], xi[0], xi[1]);
+                xi[2] = b.x[r / N];
+              }
+              Jac jg = prism_map(X, xi);
+              adjugate_rows(jg.J, S, det);
+              for (int c = 0; c < 3; ++c) gx[c] = jg.x[c];
+            }
+            for (int c = 0; c < 3; ++c) fx[((size_t)face_index(g, f) * Nf + r) * 3 + c] = gx[c];
+            if (side == 0) {
+              double n[3];
+              for (int jj = 0; jj < 3; ++jj) {
+                n[jj] = 0.0;
+                for (int d = 0; d < 3; ++d)
+                  if (kPrismNormal[f][d] != 0.0) n[jj] += kPrismNormal[f][d] * S[d][jj];
+              }
+              store_normal(I, r, n);
+            }
           }
         }
       }
+    });
+    if (bad_elem.load() != INT64_MAX) {
+      snprintf(buf, sizeof buf, "non-positive Jacobian in element %lld", (long long)bad_elem.load());
+      err = buf;
+      return FR_EMESH;
     }
     // Operator table (prism_tab layout).
     const PrismTab L = prism_tab(N);

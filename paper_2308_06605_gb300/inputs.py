@@ -351,6 +351,151 @@ def curved_box_mesh(n: Sequence[int], lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3, p
                     prism=np.ascontiguousarray(pris))
 
 
+# Boundary tags of the blade passage.
+TAG_INLET, TAG_OUTLET, TAG_PER_LO, TAG_PER_HI, TAG_SPAN_LO, TAG_SPAN_HI, TAG_SUCTION, TAG_PRESSURE = 1, 2, 3, 4, 5, 6, 7, 8
+
+
+def blade_profile(seed: int = 0, thickness: float = 0.12):
+    """NACA-4-digit-like section of unit chord with camber drawn from the seed: (camber line y_c,
+    its slope, half thickness t) as functions of x in [0, 1] (closed trailing edge)."""
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(0.03, 0.05)            # maximum camber
+    pc = rng.uniform(0.35, 0.45)           # its chordwise position
+
+    def yc(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.where(x < pc, m / pc ** 2 * (2 * pc * x - x * x), m / (1 - pc) ** 2 * ((1 - 2 * pc) + 2 * pc * x - x * x))
+
+    def t(x):
+        x = np.clip(np.asarray(x, dtype=np.float64), 0.0, 1.0)
+        return 5 * thickness * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+    return yc, t, m, pc
+
+
+def blade_passage_mesh(n_up: int = 25, n_blade: int = 75, n_down: int = 25, ny: int = 70, nz: int = 40,
+                       n_prism_rows: int = 8, pitch: float = 0.8, span: float = 0.3, stagger_deg: float = 30.0,
+                       x_in: float = -0.6, x_out: float = 1.6, seed: int = 0, quadratic: bool = True,
+                       bcs=None) -> MeshDesc:
+    """Synthetic linear-cascade passage (unit chord): an H-mesh between the suction side of one
+    blade and the pressure side of the next (a pitch above), sheared by the stagger angle
+    (y -> y + x tan(stagger)), extruded over `span` in z with nz layers.  Upstream and downstream
+    of the blade the lower and upper boundaries are periodic (translation (0, pitch, 0)); z is
+    periodic (translation (0, 0, span)).  Cells within n_prism_rows of either blade surface (over
+    the chord) are split into two prisms each.  With quadratic elements every node of the
+    (2 nx + 1) x (2 ny + 1) x (2 nz + 1) lattice lies on the analytic map, so wall faces follow the
+    blade surface to second order.  Tags: TAG_INLET / TAG_OUTLET, TAG_PER_LO / TAG_PER_HI,
+    TAG_SPAN_LO / TAG_SPAN_HI, TAG_SUCTION / TAG_PRESSURE (walls); `bcs` maps tags to
+    (kind, params) for the non-periodic ones."""
+    yc, t, _, _ = blade_profile(seed)
+    nx = n_up + n_blade + n_down
+    q = 2 if quadratic else 1
+    # Streamwise lattice coordinate: uniform upstream/downstream, cosine-clustered on the blade.
+    u_up = np.linspace(x_in, 0.0, q * n_up + 1)
+    u_bl = 0.5 * (1 - np.cos(np.pi * np.linspace(0.0, 1.0, q * n_blade + 1)))
+    u_dn = np.linspace(1.0, x_out, q * n_down + 1)
+    X1 = np.concatenate([u_up, u_bl[1:], u_dn[1:]])                       # [q nx + 1]
+    on_blade = (X1 >= 0.0) & (X1 <= 1.0)
+    y_lo = np.where(on_blade, yc(np.clip(X1, 0, 1)) + t(X1), 0.0)
+    y_hi = np.where(on_blade, yc(np.clip(X1, 0, 1)) - t(X1), 0.0) + pitch
+    eta = np.linspace(0.0, 1.0, q * ny + 1)
+    eta = 0.5 * (1 - np.cos(np.pi * eta)) * 0.5 + 0.5 * eta               # mild clustering at both walls
+    zz = np.linspace(0.0, span, q * nz + 1)
+    XX = np.broadcast_to(X1[:, None, None], (X1.size, eta.size, zz.size))
+    YY = y_lo[:, None, None] + eta[None, :, None] * (y_hi - y_lo)[:, None, None]
+    ZZ = np.broadcast_to(zz[None, None, :], XX.shape)
+    YY = YY + np.tan(np.radians(stagger_deg)) * XX
+    xyz = np.stack([A.transpose(2, 1, 0).ravel() for A in (XX, YY, ZZ)], 1)   # node I + NI (J + NJ K)
+    NI, NJ = q * nx + 1, q * ny + 1
+    nid = lambda I, J, K: I + NI * (J + NJ * K)   # noqa: E731
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    blade_col = (ci >= n_up) & (ci < n_up + n_blade)
+    split = blade_col & ((cj < n_prism_rows) | (cj >= ny - n_prism_rows))
+    base = [q * ci + (1 if quadratic else 0), q * cj + (1 if quadratic else 0), q * ck + (1 if quadratic else 0)]
+    if quadratic:
+        href, pref = HEX27_REF, PRISM18_REF
+        off = lambda c: c                   # noqa: E731  reference coordinate -> lattice offset
+    else:
+        href, pref = HEX_REF_VERTS.astype(np.int64), PRISM18_REF[:6]
+        off = lambda c: (c + 1) // 2        # noqa: E731
+    hsel = ~split
+    hexes = np.stack([nid(base[0][hsel] + off(c[0]), base[1][hsel] + off(c[1]), base[2][hsel] + off(c[2]))
+                      for c in href], 1)
+    pris = []
+    for V in (np.array([[-1, -1], [1, -1], [1, 1]]), np.array([[-1, -1], [1, 1], [-1, 1]])):
+        cols = []
+        for (r, s_, z) in pref.tolist():
+            lam = _tri_bary(r, s_)
+            pxy = np.round((lam[:, None] * V).sum(axis=0)).astype(np.int64)
+            cols.append(nid(base[0][split] + off(pxy[0]), base[1][split] + off(pxy[1]), base[2][split] + off(z)))
+        pris.append(np.stack(cols, 1))
+    pris = np.stack(pris, 1).reshape(-1, pref.shape[0])                   # the two prisms of a cell adjacent
+    # Boundary faces (corner nodes).
+    c = lambda I, J, K: nid(q * I, q * J, q * K)   # noqa: E731
+    bn, bt = [], []
+    J, K = np.meshgrid(np.arange(ny), np.arange(nz), indexing="ij")
+    J, K = J.ravel(), K.ravel()
+    for I0, tag in ((0, TAG_INLET), (nx, TAG_OUTLET)):
+        bn.append(np.stack([c(I0, J, K), c(I0, J + 1, K), c(I0, J + 1, K + 1), c(I0, J, K + 1)], 1)); bt.append(np.full(J.size, tag))
+    Iw, K = np.meshgrid(np.arange(nx), np.arange(nz), indexing="ij")
+    Iw, K = Iw.ravel(), K.ravel()
+    wall = (Iw >= n_up) & (Iw < n_up + n_blade)
+    for J0, tw, tp in ((0, TAG_SUCTION, TAG_PER_LO), (ny, TAG_PRESSURE, TAG_PER_HI)):
+        bn.append(np.stack([c(Iw, J0, K), c(Iw + 1, J0, K), c(Iw + 1, J0, K + 1), c(Iw, J0, K + 1)], 1))
+        bt.append(np.where(wall, tw, tp))
+    Ic, Jc = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    Ic, Jc = Ic.ravel(), Jc.ravel()
+    sp = ((Ic >= n_up) & (Ic < n_up + n_blade)) & ((Jc < n_prism_rows) | (Jc >= ny - n_prism_rows))
+    for K0, tag in ((0, TAG_SPAN_LO), (nz, TAG_SPAN_HI)):
+        qd = np.stack([c(Ic, Jc, K0), c(Ic + 1, Jc, K0), c(Ic + 1, Jc + 1, K0), c(Ic, Jc + 1, K0)], 1)
+        bn.append(qd[~sp]); bt.append(np.full((~sp).sum(), tag))
+        m1 = -np.ones(sp.sum(), dtype=np.int64)
+        bn.append(np.stack([qd[sp, 0], qd[sp, 1], qd[sp, 2], m1], 1)); bt.append(np.full(sp.sum(), tag))
+        bn.append(np.stack([qd[sp, 0], qd[sp, 2], qd[sp, 3], m1], 1)); bt.append(np.full(sp.sum(), tag))
+    per = [Periodic(TAG_PER_LO, TAG_PER_HI, (0.0, float(pitch), 0.0)), Periodic(TAG_SPAN_LO, TAG_SPAN_HI, (0.0, 0.0, float(span)))]
+    bc_list = [BC(int(tag), int(kind), tuple(float(v) for v in params)) for tag, (kind, params) in (bcs or {}).items()]
+    return MeshDesc(xyz=np.ascontiguousarray(xyz), hex=np.ascontiguousarray(hexes.astype(np.int64)),
+                    bface_nodes=np.ascontiguousarray(np.concatenate(bn).astype(np.int64)),
+                    bface_tag=np.concatenate(bt).astype(np.int32), periodic=per, bcs=bc_list,
+                    prism=np.ascontiguousarray(pris.astype(np.int64)))
+
+
+def cascade_conditions(Ma_in: float = 0.15, Ma_exit: float = 0.9, Re: float = 5e5, gamma: float = 1.4,
+                       stagger_deg: float = 30.0):
+    """Physics and boundary data of the synthetic cascade (unit chord, p0 = rho0 = 1, R = 1, so
+    T0 = 1): characteristic inflow with total conditions along the stagger direction, static
+    back-pressure from the isentropic exit Mach number, isothermal blade walls at T0, mu from the
+    Reynolds number on chord and isentropic exit speed.  Returns (Physics, bcs, inflow state fn)."""
+    R = 1.0
+    T0 = p0 = 1.0
+    f = lambda M: 1 + 0.5 * (gamma - 1) * M * M   # noqa: E731
+    pb = p0 * f(Ma_exit) ** (-gamma / (gamma - 1))
+    Te = T0 / f(Ma_exit)
+    Ue = Ma_exit * np.sqrt(gamma * R * Te)
+    rho_e = pb / (R * Te)
+    mu = rho_e * Ue * 1.0 / Re
+    d = (np.cos(np.radians(stagger_deg)), np.sin(np.radians(stagger_deg)), 0.0)
+    phys = Physics(gamma=gamma, R=R, mu=mu, Pr=0.71, viscous=1)
+    bcs = {TAG_INLET: (BC_CHAR_INFLOW, (p0, T0) + d), TAG_OUTLET: (BC_CHAR_OUTFLOW, (pb,)),
+           TAG_SUCTION: (BC_WALL_ISOTHERMAL, (T0,)), TAG_PRESSURE: (BC_WALL_ISOTHERMAL, (T0,))}
+    Ti = T0 / f(Ma_in)
+    pi = p0 * f(Ma_in) ** (-gamma / (gamma - 1))
+    Ui = Ma_in * np.sqrt(gamma * R * Ti)
+
+    def state(x, perturb=1e-3, seed=0):
+        """Uniform inflow state with a seeded random-phase velocity perturbation."""
+        rng = np.random.default_rng(seed)
+        ph_ = rng.uniform(0, 2 * np.pi, 3)
+        k = 2 * np.pi * np.array([1.0, 1 / 0.8, 1 / 0.3])
+        dv = perturb * Ui * np.stack([np.sin(k[0] * x[..., 0] + ph_[0]) * np.cos(k[1] * x[..., 1]),
+                                      np.sin(k[1] * x[..., 1] + ph_[1]) * np.cos(k[2] * x[..., 2]),
+                                      np.sin(k[2] * x[..., 2] + ph_[2]) * np.cos(k[0] * x[..., 0])], -1)
+        u = Ui * np.asarray(d)[None] * np.ones(x.shape[:-1] + (1,)) + dv
+        rho = pi / (R * Ti) * np.ones(x.shape[:-1])
+        return conserved(rho, u[..., 0], u[..., 1], u[..., 2], pi * np.ones(x.shape[:-1]), gamma)
+    return phys, bcs, state
+
+
 # ---------------------------------------------------------------------------------------------
 # Physical parameters and initial conditions (functions of physical coordinates only).
 # ---------------------------------------------------------------------------------------------

@@ -124,3 +124,35 @@ def test_polynomial_exactness_with_dirichlet(prisms):
         want[..., 1] = -2 * b * u
         want[..., 4] = -(G * P0 * b / (G - 1) + 1.5 * b * u * u) + 4.0 / 3.0 * mu * b * b
         np.testing.assert_allclose(r, want, rtol=0, atol=1e-11 * 2.0)
+
+
+@pytest.mark.parametrize("kinds", [
+    ((I.BC_WALL_ISOTHERMAL, (1.1,)), (I.BC_CHAR_OUTFLOW, (0.7,))),
+    ((I.BC_CHAR_INFLOW, (0.9, 1.05, 1.0, 0.2, 0.0)), (I.BC_WALL_ISOTHERMAL, (0.9,)))])
+def test_boundary_conditions_equal_hex_oracle(kinds):
+    """Walls and characteristic boundaries: on hexahedral meshes the mixed-element oracle equals the
+    hexahedral one (whose boundary states are pinned separately)."""
+    d = I.hex_box_mesh((3, 2, 2), hi=(2.0, 1.0, 1.0), periodic=(False, True, True),
+                       wall_tags={1: kinds[0], 2: kinds[1]}, seed=3, rotate=True, perturb=0.1)
+    ph = I.Physics(gamma=1.4, R=1.0, mu=0.02, Pr=0.71, viscous=1)
+    mh, mm = HexFR(d, ph, 3), MixedFR(d, ph, 3)
+    Q = I.conserved(1 + 0.1 * np.sin(mh.x[..., 0]), 0.2 + 0 * mh.x[..., 0], 0.1 + 0 * mh.x[..., 0],
+                    0.05 * np.sin(2 * np.pi * mh.x[..., 2]), 0.7 + 0.02 * mh.x[..., 0], 1.4)
+    R1 = mh.residual(Q)
+    R2 = mm.residual([Q, np.zeros((0, mm.types[1].Np, 5))])[0]
+    np.testing.assert_allclose(R2, R1, rtol=0, atol=1e-13 * np.abs(R1).max())
+
+
+def test_walls_on_triangular_faces_keep_quiescent_gas_at_rest():
+    """Gas at rest at the wall temperature between isothermal walls through triangular faces:
+    an exact steady state (zero residual)."""
+    T_w = 1.2
+    d = I.hex_box_mesh((2, 2, 3), hi=(1.0, 1.0, 1.5), periodic=(True, True, False), prisms="checker", seed=2,
+                       rotate=True, perturb=0.1,
+                       wall_tags={5: (I.BC_WALL_ISOTHERMAL, (T_w,)), 6: (I.BC_WALL_ISOTHERMAL, (T_w,))})
+    ph = I.Physics(gamma=1.4, R=1.0, mu=0.05, Pr=0.71, viscous=1)
+    m = MixedFR(d, ph, 3)
+    Qs = [I.conserved(np.ones(x.shape[:2]), 0 * x[..., 0], 0 * x[..., 0], 0 * x[..., 0], T_w * np.ones(x.shape[:2]), 1.4)
+          for x in m.x]
+    for R in m.residual(Qs):
+        assert np.abs(R).max() <= 1e-12
