@@ -287,6 +287,56 @@ def run_prisms(steps, fp64_peak, df_peak, cases=None):
     return out
 
 
+def run_cascade(steps, fp64_peak, df_peak, nz=40, p=7):
+    """The synthetic cascade passage (398 000 quadratic elements at nz = 40, 24 % prisms, p = 7,
+    182 M points): walls, characteristic inflow/outflow, periodic pitch and span; both precisions,
+    RK44 steps at CFL 0.3 from the seeded inflow state; updates/s and the phase times."""
+    import numpy as np
+    import torch
+    from paper_2308_06605_gb300 import fr, inputs as I
+    out = {}
+    stream = torch.cuda.current_stream()
+    dt = None
+    for prec in ("fp64", "mixed"):
+        phys, bcs, state_fn = I.cascade_conditions()
+        phys.precision = 1 if prec == "mixed" else 0
+        d = I.blade_passage_mesh(nz=nz, bcs=bcs)
+        t0 = time.perf_counter()
+        m = fr.Mesh(d, phys, p, stream=stream.cuda_stream)
+        t_create = time.perf_counter() - t0
+        x = m.solution_points()
+        Qd = torch.from_numpy(np.ascontiguousarray(state_fn(x, perturb=1e-3))).to("cuda")
+        del x
+        m.set_state(Qd)
+        if dt is None:
+            dt = m.max_dt(0.3)
+        for _ in range(2):
+            m.rk_step(0.0, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(2, steps)
+        e0.record(stream)
+        for _ in range(k):
+            m.rk_step(0.0, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        m.profile(True)
+        m.rk_step(0.0, dt)
+        kms, kcnt = m.profile_read(4)
+        m.profile(False)
+        out[prec] = {"updates_per_s": m.n_points * 4 / (ms * 1e-3), "ms_per_step": ms, "mesh_create_s": t_create,
+                     "phase_ms_per_stage": dict(zip(("interp_faces", "volume", "iface_flux", "correct"),
+                                                    [a / max(1, c) for a, c in zip(kms, kcnt)]))}
+        out["n_points"], out["n_hex"], out["n_prism"], out["p"] = m.n_points, m.n_elem, m.n_prism, p
+        out["device_bytes_" + prec] = m.device_bytes
+        m.close()
+        del Qd
+        torch.cuda.empty_cache()
+    out["dt"] = dt
+    return out
+
+
 def residual_error(a, b):
     """Per-variable max-norm and L2 relative difference of two device residuals (b = reference)."""
     torch = a.torch
@@ -318,6 +368,9 @@ def run_ours(args):
         from paper_2308_06605_gb300 import build as B
         B.build()
     fr.load()
+    if args.cascade_only:
+        print(json.dumps({"cascade_p7": run_cascade(args.steps, None, None)}), flush=True)
+        return 0
 
     def barrier():
         if world > 1:
@@ -429,6 +482,8 @@ def run_ours(args):
             "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
             "ensemble_64_vortex": ensemble, "prisms_tgv": prisms,
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}
+    if args.cascade:
+        line["cascade_p7"] = run_cascade(args.steps, fp64_peak, df_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, cores = oracle_rate(budget_s=12.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -457,6 +512,9 @@ def main():
     ap.add_argument("--no-prisms", action="store_true", help="skip the prismatic / mixed-mesh measurements")
     ap.add_argument("--prism-edge", type=int, default=0, help="only an all-prism box of this edge (profiling)")
     ap.add_argument("--prism-order", type=int, default=4)
+    ap.add_argument("--cascade", action="store_true",
+                    help="also run the synthetic cascade passage (398 000 quadratic elements, p = 7, 182 M points)")
+    ap.add_argument("--cascade-only", action="store_true", help="print only the cascade measurement")
     ap.add_argument("--n-edge", type=int, default=N_EDGE, help="elements per edge (profiling of smaller cases)")
     ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()
