@@ -389,9 +389,12 @@ def blade_passage_mesh(n_up: int = 25, n_blade: int = 75, n_down: int = 25, ny: 
     yc, t, _, _ = blade_profile(seed)
     nx = n_up + n_blade + n_down
     q = 2 if quadratic else 1
-    # Streamwise lattice coordinate: uniform upstream/downstream, cosine-clustered on the blade.
+    # Streamwise lattice coordinate: uniform upstream/downstream, mildly clustered at the leading
+    # and trailing edges on the blade (30 % cosine, 70 % uniform: aspect ratios stay below ~2, so
+    # the volume-based element size is close to the shortest edge).
     u_up = np.linspace(x_in, 0.0, q * n_up + 1)
-    u_bl = 0.5 * (1 - np.cos(np.pi * np.linspace(0.0, 1.0, q * n_blade + 1)))
+    ub = np.linspace(0.0, 1.0, q * n_blade + 1)
+    u_bl = 0.3 * 0.5 * (1 - np.cos(np.pi * ub)) + 0.7 * ub
     u_dn = np.linspace(1.0, x_out, q * n_down + 1)
     X1 = np.concatenate([u_up, u_bl[1:], u_dn[1:]])                       # [q nx + 1]
     on_blade = (X1 >= 0.0) & (X1 <= 1.0)
