@@ -245,7 +245,8 @@ fr_status fr_mlp_adam(float *params, const float *grad, float *m, float *v, int3
  * Batched stages for ensembles of independent cases (the paper runs one mesh per MPI
  * decomposition; on one GPU an ensemble of unevenly sized cases, with different orders, is
  * advanced together).  fr_batch_create borrows the meshes (they must outlive the batch, share
- * precision, device and stream; hexahedral meshes only, FR_EUNSUPPORTED for one with prisms).  fr_batch_rk_stage runs stage `stage` (RK44, same update as
+ * precision, device and stream; meshes may mix hexahedra and prisms, of any geometry order; meshes
+ * with the closure are rejected with FR_EUNSUPPORTED).  fr_batch_rk_stage runs stage `stage` (RK44, same update as
  * fr_rk_stage) of every case in ONE cooperative persistent kernel: phases (face interpolation,
  * boundary states, volume, interface fluxes, correction + update) are separated by grid
  * barriers whose waits are bounded; if a wait gives up, the call returns FR_ETIMEOUT and the

@@ -19,6 +19,7 @@ struct fr_batch {
   std::vector<fr_mesh *> meshes;
   std::vector<BatchCase> cases;
   std::vector<int> Ns;
+  std::vector<int> has_prism;
   int mixed = 0;
   cudaStream_t stream = nullptr;
   int device = 0, sms = 0;
@@ -78,6 +79,7 @@ static std::vector<BatchTask> build_tasks(fr_batch *b, int block, int *phase_beg
   for (int cs : order) {
     const DevMesh &m = b->cases[cs].m;
     chunks(cs, TASK_INTERP, 0, m.E * 6 * m.Nf, block);
+    chunks(cs, TASK_PRISM_INTERP, 0, m.Ep * 5 * m.Nf, block);
   }
   if (any_bc) {
     phase_begin[np++] = (int)t.size();
@@ -90,6 +92,7 @@ static std::vector<BatchTask> build_tasks(fr_batch *b, int block, int *phase_beg
   for (int cs : order) {
     const DevMesh &m = b->cases[cs].m;
     chunks(cs, TASK_VOLUME, 0, m.E, batch_elems_per_block(m.N, block));
+    chunks(cs, TASK_PRISM_VOLUME, 0, m.Ep, batch_prism_elems_per_block(m.N, block));
   }
   phase_begin[np++] = (int)t.size();
   for (int cs : order) {
@@ -101,6 +104,7 @@ static std::vector<BatchTask> build_tasks(fr_batch *b, int block, int *phase_beg
   for (int cs : order) {
     const DevMesh &m = b->cases[cs].m;
     chunks(cs, TASK_CORRECT, 0, m.E * m.Np, block);
+    chunks(cs, TASK_PRISM_CORRECT, 0, m.Ep * m.Npp, block);
   }
   phase_begin[np] = (int)t.size();
   *n_phases = np;
@@ -112,7 +116,7 @@ static fr_status configure(fr_batch *b, int block, int bps) {
   int phase_begin[6];
   int n_phases = 0;
   std::vector<BatchTask> tasks = build_tasks(b, block, phase_begin, &n_phases);
-  const size_t smem = batch_smem_bytes(b->Ns.data(), (int)b->Ns.size(), block, b->mixed);
+  const size_t smem = batch_smem_bytes(b->Ns.data(), b->has_prism.data(), (int)b->Ns.size(), block, b->mixed);
   int occ = 0;
   cudaError_t e = batch_occupancy(b->mixed, block, smem, &occ);
   if (e != cudaSuccess) return bfail(b, FR_ECUDA, std::string("batch occupancy: ") + cudaGetErrorString(e));
@@ -188,10 +192,6 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
     }
-    if (c.m.Ep > 0) {
-      delete b;
-      return bfail(nullptr, FR_EUNSUPPORTED, "meshes with prisms cannot be batched");
-    }
     if (i == 0) {
       b->mixed = c.m.mixed;
       b->stream = st;
@@ -203,7 +203,8 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
     b->meshes.push_back(meshes[i]);
     b->cases.push_back(c);
     b->Ns.push_back(c.m.N);
-    b->n_points += c.m.E * c.m.Np;
+    b->has_prism.push_back(c.m.Ep > 0 ? 1 : 0);
+    b->n_points += c.m.E * c.m.Np + c.m.Ep * c.m.Npp;
   }
   cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_cases, sizeof(BatchCase) * n);
@@ -296,7 +297,7 @@ extern "C" fr_status fr_batch_rk_stage(fr_batch *b, int32_t stage, double t) {
 // Restore every case to U_n (a tuning run advanced their stage states).
 static cudaError_t restore_states(fr_batch *b) {
   for (const BatchCase &c : b->cases) {
-    const size_t bytes = (size_t)c.m.E * c.m.Np * 5 * sizeof(double);
+    const size_t bytes = ((size_t)c.m.E * c.m.Np + (size_t)c.m.Ep * c.m.Npp) * 5 * sizeof(double);
     cudaError_t e = cudaMemcpyAsync(c.m.Q, c.m.Un, bytes, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = launch_state_copy(c.m, b->stream);
     if (e != cudaSuccess) return e;

@@ -31,6 +31,7 @@
 #include "df32.cuh"
 #include "fr_device.hpp"
 #include "fr_point.cuh"
+#include "fr_prism_bodies.cuh"
 
 namespace frx {
 namespace {
@@ -782,14 +783,17 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
   T *Rpart = reinterpret_cast<T *>(m.Rpart);
   const T *met = reinterpret_cast<const T *>(m.metrics), *lift = reinterpret_cast<const T *>(m.liftfac);
   const T *nrm = reinterpret_cast<const T *>(m.normals);
+  const int64_t pts = m.E * m.Np * 5;               // first prism value in per-point arrays
+  const T *ptab = reinterpret_cast<const T *>(m.ptab), *pmet = reinterpret_cast<const T *>(m.metrics_p);
+  const int64_t idx = tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62;
   switch (tk.kind) {
     case TASK_INTERP:
       interp_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qin, m.ef, Qtr,
                         m.E);
       break;
     case TASK_BC_PREPARE:
-      bc_prepare_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, nrm,
-                            m.if_bc, m.bcs, m.n_interior, m.n_if - m.n_interior, c.ph);
+      if (m.if_tri && unused_tri_slot<N>(idx, m.n_interior, m.n_if - m.n_interior, m.if_tri)) break;
+      bc_prepare_body<N, T>(idx, Qtr, nrm, m.if_bc, m.bcs, m.n_interior, m.n_if - m.n_interior, c.ph);
       break;
     case TASK_VOLUME: {
       // Sub-blocks of nth threads, one element each; threads past the last full sub-block idle.
@@ -805,12 +809,33 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
       break;
     }
     case TASK_IFACE:
-      iface_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm, FI,
-                       m.n_interior, c.ph, m.if_elem, m.nu);
+      if (m.if_tri && unused_tri_slot<N>(idx, 0, m.n_interior, m.if_tri)) break;
+      iface_body<N, T>(idx, Qtr, Gtr, nrm, FI, m.n_interior, c.ph, m.if_elem, m.nu);
       break;
     case TASK_BC_FLUX:
-      bc_flux_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Qtr, Gtr, nrm,
-                         m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph, m.if_elem, m.nu);
+      if (m.if_tri && unused_tri_slot<N>(idx, m.n_interior, m.n_if - m.n_interior, m.if_tri)) break;
+      bc_flux_body<N, T>(idx, Qtr, Gtr, nrm, m.if_bc, m.bcs, FI, m.n_interior, m.n_if - m.n_interior, c.ph, m.if_elem,
+                         m.nu);
+      break;
+    case TASK_PRISM_INTERP:
+      prism_interp_body<N, T>(idx, Qin + pts, m.ef_p, ptab, m.tri_slot, Qtr, m.Ep);
+      break;
+    case TASK_PRISM_VOLUME: {
+      const int tpe = ((N * (N + 1) / 2 * N + 31) / 32) * 32;
+      const int nth = tpe >= (int)blockDim.x ? (int)blockDim.x : tpe;
+      const int epb = (int)blockDim.x / nth;
+      const int le = (int)threadIdx.x / nth;
+      const int tid = (int)threadIdx.x % nth;
+      const int64_t e = tk.begin + le;
+      const bool active = le < epb && e < tk.end;
+      prism_volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * prism_smem_values<N>(),
+                              Qin + pts, pmet, m.ef_p, Qtr, ptab, m.tri_slot, Gtr, Rpart + pts, c.ph);
+      break;
+    }
+    case TASK_PRISM_CORRECT:
+      prism_correct_body<N, T>(idx, Rpart + pts, FI, m.ef_p, pmet, ptab, m.tri_slot, m.Ep, m.E * m.Np, MODE_RK, L.stage,
+                               L.dts[tk.cs], nullptr, m.Q, m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr, m.Un,
+                               reinterpret_cast<T *>(m.Unc), m.acc, &L.sync->nonfinite, c.ph);
       break;
     case TASK_CORRECT:
       correct_body<N, T>(tk.begin + threadIdx.x < tk.end ? tk.begin + threadIdx.x : (int64_t)1 << 62, Rpart, FI, m.ef,

@@ -72,7 +72,8 @@ struct BatchCase {
 
 // Work item of a phase: case `cs`, kind, and an item range [begin, end) -- flux/solution
 // points for the pointwise kinds, elements for the volume kind.
-enum { TASK_INTERP = 0, TASK_BC_PREPARE = 1, TASK_VOLUME = 2, TASK_IFACE = 3, TASK_BC_FLUX = 4, TASK_CORRECT = 5 };
+enum { TASK_INTERP = 0, TASK_BC_PREPARE = 1, TASK_VOLUME = 2, TASK_IFACE = 3, TASK_BC_FLUX = 4, TASK_CORRECT = 5,
+       TASK_PRISM_INTERP = 6, TASK_PRISM_VOLUME = 7, TASK_PRISM_CORRECT = 8 };
 struct BatchTask {
   int32_t cs, kind;
   int64_t begin, end;
@@ -114,13 +115,19 @@ FRX_BATCH_VARIANT_DECL(1, 512)
 // Launch one cooperative persistent stage over all cases (block size 256 or 512).
 cudaError_t launch_batch_stage(const BatchLaunch &L, int mixed, int block, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cudaStream_t st);
-// Largest dynamic shared memory one block needs for the given orders and block size.
-size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed);
+// Largest dynamic shared memory one block needs for the given orders (and whether each case has
+// prisms) and block size.
+size_t batch_smem_bytes(const int *Ns, const int *has_prism, int n, int block, int mixed);
 // Resident blocks per SM of the batch kernel for the given configuration.
 cudaError_t batch_occupancy(int mixed, int block, size_t smem, int *blocks_per_sm);
 // Elements a block of `block` threads processes at once in the volume phase for order N.
 inline int batch_elems_per_block(int N, int block) {
   const int tpe = ((N * N * N + 31) / 32) * 32;
+  return tpe >= block ? 1 : block / tpe;
+}
+// The same for prisms (N(N+1)/2 x N points).
+inline int batch_prism_elems_per_block(int N, int block) {
+  const int tpe = ((N * (N + 1) / 2 * N + 31) / 32) * 32;
   return tpe >= block ? 1 : block / tpe;
 }
 

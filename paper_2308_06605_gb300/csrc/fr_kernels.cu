@@ -1,6 +1,8 @@
 // Per-mesh launches of the hexahedral FR kernels and their host-side dispatch (the device bodies
 // are in fr_bodies.cuh); dt estimate; basis-table upload for every translation unit; dispatch of
 // the batched stage kernel variants.
+#include <algorithm>
+
 #include "fr_bodies.cuh"
 
 namespace frx {
@@ -187,15 +189,17 @@ cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cu
   return cudaGetLastError();
 }
 
-size_t batch_smem_bytes(const int *Ns, int n, int block, int mixed) {
+size_t batch_smem_bytes(const int *Ns, const int *has_prism, int n, int block, int mixed) {
   (void)mixed;
   size_t best = 0;
   for (int k = 0; k < n; ++k) {
     const int N = Ns[k];
-    const int tpe = ((N * N * N + 31) / 32) * 32;
-    const size_t per = (size_t)(35 * N * N * N + 30 * N * N) * sizeof(double);
-    const size_t need = per * (size_t)(tpe >= block ? 1 : block / tpe);
-    if (need > best) best = need;
+    const size_t hex = (size_t)(35 * N * N * N + 30 * N * N) * sizeof(double) * batch_elems_per_block(N, block);
+    best = std::max(best, hex);
+    if (has_prism[k]) {
+      const size_t per = (size_t)(65 * (N * (N + 1) / 2 * N) + 25 * N * N) * sizeof(double);
+      best = std::max(best, per * batch_prism_elems_per_block(N, block));
+    }
   }
   return best;
 }

@@ -25,291 +25,29 @@
 #include "df32.cuh"
 #include "fr_device.hpp"
 #include "fr_point.cuh"
+#include "fr_prism_bodies.cuh"
 
 namespace frx {
 
-template <int N>
-constexpr int prism_points() { return N * (N + 1) / 2 * N; }
-template <int N>
-constexpr int prism_threads() { return ((prism_points<N>() + 31) / 32) * 32; }
-// Shared-memory values (of T) of the volume kernel: Q 5, grad 15, flux 15, BR2 weights 15, quad
-// lifts 15 (per point) and the jumps of 5 faces x 5 variables x N^2 slots.
-template <int N>
-constexpr int prism_smem_values() { return 65 * prism_points<N>() + 25 * N * N; }
-
-template <typename T>
-__device__ __forceinline__ const PhysT<T> &pphys(const DevPhys &p);
-template <> __device__ __forceinline__ const PhysT<double> &pphys<double>(const DevPhys &p) { return p.d; }
-template <> __device__ __forceinline__ const PhysT<df32> &pphys<df32>(const DevPhys &p) { return p.f; }
-
-// Interface slot of local flux point r of prism face f for a packed face word.
-template <int N>
-__device__ __forceinline__ int prism_slot(int f, int r, int code, const int32_t *__restrict__ tri_slot) {
-  constexpr int Nt = N * (N + 1) / 2;
-  return f < 2 ? tri_slot[code * Nt + r] : orient_slot(code, r % N, r / N, N);
-}
-
 // ------------------------------------------------------------------------------------------
-// 1. Solution traces.  Thread per (prism, face, flux point); triangular faces use r < Nt.
+// Per-mesh kernels: one launch per phase over all prisms of a mesh.
 // ------------------------------------------------------------------------------------------
 template <int N, typename T>
 __global__ void k_prism_interp(const T *__restrict__ Q, const int32_t *__restrict__ ef_p, const T *__restrict__ tab,
                                const int32_t *__restrict__ tri_slot, T *__restrict__ Qtr, int64_t Ep) {
-  constexpr int Nt = N * (N + 1) / 2, Np = Nt * N, Nf = N * N;
-  constexpr PrismTab L = prism_tab(N);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Ep * 5 * Nf) return;
-  const int r = (int)(t % Nf);
-  const int64_t eff = t / Nf;
-  const int f = (int)(eff % 5);
-  const int64_t e = eff / 5;
-  if (f < 2 && r >= Nt) return;
-  const T *q = Q + e * Np * 5;
-  Dot<T> acc[5];
-  if (f < 2) {
-    const T *l = tab + (f ? L.lp : L.lm);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T lk = l[k];
-      const T *qk = q + (r + Nt * k) * 5;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v].add(lk, qk[v]);
-    }
-  } else {
-    const int a = r % N, b = r / N;
-    const T *Ea = tab + L.E + (f - 2) * N * Nt + a * Nt;
-#pragma unroll 4
-    for (int j = 0; j < Nt; ++j) {
-      const T ej = Ea[j];
-      const T *qj = q + (j + Nt * b) * 5;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v].add(ej, qj[v]);
-    }
-  }
-  const int packed = ef_p[eff];
-  const int64_t I = packed >> 4;
-  const int side = (packed >> 3) & 1;
-  T *dst = Qtr + (I * 2 + side) * 5 * Nf + prism_slot<N>(f, r, packed & 7, tri_slot);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v].get();
+  prism_interp_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Q, ef_p, tab, tri_slot, Qtr, Ep);
 }
 
-// ------------------------------------------------------------------------------------------
-// 2. Volume kernel.  One block per prism, one thread per solution point.
-// ------------------------------------------------------------------------------------------
 template <int N, typename T>
 __global__ void __launch_bounds__(prism_threads<N>())
     k_prism_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef_p,
                    const T *__restrict__ Qtr, const T *__restrict__ tab, const int32_t *__restrict__ tri_slot,
                    T *__restrict__ Gtr, T *__restrict__ Rpart, DevPhys dph) {
-  constexpr int Nt = N * (N + 1) / 2, Np = Nt * N, Nf = N * N;
-  constexpr PrismTab L = prism_tab(N);
   extern __shared__ double sm_raw[];
-  T *sm = reinterpret_cast<T *>(sm_raw);
-  T *sQ = sm;                 // [5][Np]
-  T *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
-  T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
-  T *sW = sH + 15 * Np;       // [5][3][Np] eta (N_f . S[.][j]) / |J|: BR2 lifting to physical space
-  T *sL = sW + 15 * Np;       // [3][5][Np] C_f (Q^I - Q_f) of the quadrilateral faces
-  T *sdQ = sL + 15 * Np;      // [5][5][Nf] Q^I - Q_own at the flux points
-  const PhysT<T> &ph = pphys<T>(dph);
-  const bool viscous = dph.viscous != 0;
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int t = tid; t < 5 * Np; t += nth) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
-  if (viscous) {
-    for (int t = tid; t < 5 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
-      if (f < 2 && r >= Nt) continue;
-      const int packed = ef_p[e * 5 + f];
-      const int64_t I = packed >> 4;
-      const int side = (packed >> 3) & 1;
-      const int slot = prism_slot<N>(f, r, packed & 7, tri_slot);
-      const T *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
-      const T *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = ph.half * (oth[v * Nf] - own[v * Nf]);
-    }
-  }
-  __syncthreads();
-  const bool pt = tid < Np;
-  const int m = pt ? tid : 0, q = m % Nt, k = m / Nt;
-  if (pt) {
-    T S[9], invJ, qv[5], H[3][5], G[15];
-    const T *met = metrics + e * 10 * Np + m;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
-    invJ = met[9 * Np];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qv[v] = sQ[v * Np + m];
-    {
-      const T ri = ph.one / qv[0];
-      const T u[3] = {qv[1] * ri, qv[2] * ri, qv[3] * ri};
-      const T p = ph.gm1 * (qv[4] - ph.half * (qv[1] * u[0] + qv[2] * u[1] + qv[3] * u[2]));
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        H[jj][0] = qv[1 + jj];
-        H[jj][1] = qv[1] * u[jj];
-        H[jj][2] = qv[2] * u[jj];
-        H[jj][3] = qv[3] * u[jj];
-        H[jj][1 + jj] = H[jj][1 + jj] + p;
-        H[jj][4] = (qv[4] + p) * u[jj];
-      }
-    }
-    if (viscous) {
-      const T *Dr = tab + L.Dr + q * Nt, *Ds = tab + L.Ds + q * Nt, *D1 = tab + L.D1 + k * N;
-      const T hmk = tab[L.hm + k], hpk = tab[L.hp + k];
-      const T *LQ0 = tab + L.LQ + q * N, *LQ1 = LQ0 + Nt * N, *LQ2 = LQ1 + Nt * N;
-      T gu[3][5], gc[3][5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T *sq = sQ + v * Np;
-        Dot<T> a0, a1, a2;
-#pragma unroll 4
-        for (int j = 0; j < Nt; ++j) {
-          const T qj = sq[j + Nt * k];
-          a0.add(Dr[j], qj);
-          a1.add(Ds[j], qj);
-        }
-#pragma unroll
-        for (int c = 0; c < N; ++c) a2.add(D1[c], sq[q + Nt * c]);
-        gu[0][v] = a0.get();
-        gu[1][v] = a1.get();
-        gu[2][v] = a2.get();
-        // Lifted jumps: quadrilateral faces (edge e = f - 2) and the two triangles.
-        Dot<T> l2, l3, l4;
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-          l2.add(LQ0[a], sdQ[(2 * 5 + v) * Nf + a + N * k]);
-          l3.add(LQ1[a], sdQ[(3 * 5 + v) * Nf + a + N * k]);
-          l4.add(LQ2[a], sdQ[(4 * 5 + v) * Nf + a + N * k]);
-        }
-        const T L2 = l2.get(), L3 = l3.get(), L4 = l4.get();
-        sL[(0 * 5 + v) * Np + m] = L2;
-        sL[(1 * 5 + v) * Np + m] = L3;
-        sL[(2 * 5 + v) * Np + m] = L4;
-        // sum_f N_f C_f dQ_f with N = (0,0,-1), (0,0,1), (0,-1,0), (1,1,0), (-1,0,0).
-        a0.add(ph.one, L3);
-        a0.add(-ph.one, L4);
-        a1.add(-ph.one, L2);
-        a1.add(ph.one, L3);
-        a2.add(-hmk, sdQ[(0 * 5 + v) * Nf + q]);
-        a2.add(hpk, sdQ[(1 * 5 + v) * Nf + q]);
-        gc[0][v] = a0.get();
-        gc[1][v] = a1.get();
-        gc[2][v] = a2.get();
-      }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          Dot<T> du, dc;
-          du.add(s0, gu[0][v]);
-          du.add(s1, gu[1][v]);
-          du.add(s2, gu[2][v]);
-          dc.add(s0, gc[0][v]);
-          dc.add(s1, gc[1][v]);
-          dc.add(s2, gc[2][v]);
-          sG[(jj * 5 + v) * Np + m] = du.get();
-          G[jj * 5 + v] = dc.get();
-        }
-        const T ej = ph.eta * invJ;
-        sW[(0 * 3 + jj) * Np + m] = -(ej * S[2 * 3 + jj]);
-        sW[(1 * 3 + jj) * Np + m] = ej * S[2 * 3 + jj];
-        sW[(2 * 3 + jj) * Np + m] = -(ej * S[1 * 3 + jj]);
-        sW[(3 * 3 + jj) * Np + m] = ej * (S[0 * 3 + jj] + S[1 * 3 + jj]);
-        sW[(4 * 3 + jj) * Np + m] = -(ej * S[0 * 3 + jj]);
-      }
-      T Fv[3][5];
-      viscous_flux<T>(qv, G, ph, visc_of(ph), Fv);
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) H[jj][v] -= Fv[jj][v];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Dot<T> h;
-        h.add(S[d * 3 + 0], H[0][v]);
-        h.add(S[d * 3 + 1], H[1][v]);
-        h.add(S[d * 3 + 2], H[2][v]);
-        sH[(d * 5 + v) * Np + m] = h.get();
-      }
-  }
-  __syncthreads();
-  if (viscous) {
-    // Gradient traces: interpolated uncorrected gradient + eta * own lifting, per face point.
-    for (int t = tid; t < 5 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
-      if (f < 2 && r >= Nt) continue;
-      const int packed = ef_p[e * 5 + f];
-      const int64_t I = packed >> 4;
-      const int side = (packed >> 3) & 1;
-      T *dst = Gtr + (I * 2 + side) * 15 * Nf + prism_slot<N>(f, r, packed & 7, tri_slot);
-      if (f < 2) {
-        const T *l = tab + (f ? L.lp : L.lm), *hh = tab + (f ? L.hp : L.hm);
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          Dot<T> lf;
-#pragma unroll
-          for (int c = 0; c < N; ++c) lf.add(l[c] * hh[c], sW[(f * 3 + jj) * Np + r + Nt * c]);
-          const T lfac = lf.get();
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            Dot<T> acc;
-#pragma unroll
-            for (int c = 0; c < N; ++c) acc.add(l[c], sG[(jj * 5 + v) * Np + r + Nt * c]);
-            acc.add(lfac, sdQ[(f * 5 + v) * Nf + r]);
-            dst[(jj * 5 + v) * Nf] = acc.get();
-          }
-        }
-      } else {
-        const int a = r % N, b = r / N;
-        const T *Ea = tab + L.E + (f - 2) * N * Nt + a * Nt;
-        const T *lq = sL + ((f - 2) * 5) * Np + Nt * b;
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const T *w = sW + (f * 3 + jj) * Np + Nt * b;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const T *g = sG + (jj * 5 + v) * Np + Nt * b;
-            Dot<T> acc;
-            for (int j = 0; j < Nt; ++j) {
-              acc.add(Ea[j], g[j]);
-              acc.add(Ea[j] * w[j], lq[v * Np + j]);
-            }
-            dst[(jj * 5 + v) * Nf] = acc.get();
-          }
-        }
-      }
-    }
-  }
-  if (pt) {
-    const T *Drt = tab + L.Drt + q * Nt, *Dst = tab + L.Dst + q * Nt, *D1t = tab + L.D1t + k * N;
-    T *out = Rpart + (e * Np + m) * 5;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const T *h0 = sH + (0 * 5 + v) * Np + Nt * k, *h1 = sH + (1 * 5 + v) * Np + Nt * k;
-      const T *h2 = sH + (2 * 5 + v) * Np + q;
-      Dot<T> acc;
-#pragma unroll 4
-      for (int j = 0; j < Nt; ++j) {
-        acc.add(Drt[j], h0[j]);
-        acc.add(Dst[j], h1[j]);
-      }
-#pragma unroll
-      for (int c = 0; c < N; ++c) acc.add(D1t[c], h2[Nt * c]);
-      out[v] = acc.get();
-    }
-  }
+  prism_volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef_p, Qtr, tab, tri_slot,
+                          Gtr, Rpart, dph);
 }
 
-// ------------------------------------------------------------------------------------------
-// 4. Correction by the common flux, scaling and output / RK44 update.  Thread per prism point.
-// ------------------------------------------------------------------------------------------
 template <int N, typename T>
 __global__ void k_prism_correct(const T *__restrict__ Rpart, const T *__restrict__ FI, const int32_t *__restrict__ ef_p,
                                 const T *__restrict__ metrics, const T *__restrict__ tab,
@@ -317,47 +55,8 @@ __global__ void k_prism_correct(const T *__restrict__ Rpart, const T *__restrict
                                 int stage, double dt, double *__restrict__ Rout, double *__restrict__ Q,
                                 T *__restrict__ Qc, double *__restrict__ Un, T *__restrict__ Unc,
                                 double *__restrict__ acc, int *__restrict__ flag, DevPhys dph) {
-  constexpr int Nt = N * (N + 1) / 2, Np = Nt * N, Nf = N * N;
-  constexpr PrismTab L = prism_tab(N);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= Ep * Np) return;
-  const int64_t e = t / Np;
-  const int m = (int)(t % Np), q = m % Nt, k = m / Nt;
-  const PhysT<T> &ph = pphys<T>(dph);
-  Dot<T> r[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) r[v].add(ph.one, Rpart[t * 5 + v]);
-#pragma unroll
-  for (int f = 0; f < 2; ++f) {
-    const int packed = ef_p[e * 5 + f];
-    const int64_t I = packed >> 4;
-    const int side = (packed >> 3) & 1;
-    const T h = tab[(f ? L.hp : L.hm) + k];
-    const T w = side ? -h : h;
-    const T *src = FI + I * 5 * Nf + tri_slot[(packed & 7) * Nt + q];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) r[v].add(w, src[v * Nf]);
-  }
-#pragma unroll
-  for (int f = 2; f < 5; ++f) {
-    const int packed = ef_p[e * 5 + f];
-    const int64_t I = packed >> 4;
-    const int side = (packed >> 3) & 1;
-    const T *lq = tab + L.LQ + (f - 2) * Nt * N + q * N;
-    const T *src = FI + I * 5 * Nf;
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const T w = side ? -lq[a] : lq[a];
-      const int slot = orient_slot(packed & 7, a, k, N);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) r[v].add(w, src[v * Nf + slot]);
-    }
-  }
-  const T s = -metrics[(e * 10 + 9) * Np + m];
-  T rv[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) rv[v] = r[v].get();
-  finish_point<T>(first_point + t, rv, s, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag);
+  prism_correct_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Rpart, FI, ef_p, metrics, tab, tri_slot, Ep,
+                           first_point, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag, dph);
 }
 
 // dt bound per prism: cfl h / ((2p + 1) max(|u| + c)) over its points (FP64 state).

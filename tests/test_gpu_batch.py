@@ -138,3 +138,77 @@ def test_batch_barrier_timeout_reports_error():
     b.close()
     x = torch.ones(4, device="cuda")
     assert float((x * 2).sum().item()) == 8.0     # the device still works
+
+
+def _mixed_type_specs():
+    """Hexahedral, prismatic and curved mixed meshes of orders 2..7 (p = 7 prisms need 512-thread
+    blocks)."""
+    return [(I.hex_box_mesh((3, 3, 2), prisms="checker", seed=1, rotate=True, shuffle=True, perturb=0.05), 3),
+            (I.hex_box_mesh((2, 2, 2), prisms="all", seed=2, rotate=True), 5),
+            (I.curved_box_mesh((2, 2, 2), prisms="checker", warp=0.1, seed=3, rotate=True), 4),
+            (I.hex_box_mesh((3, 3, 3), seed=4, rotate=True), 2),
+            (I.curved_box_mesh((2, 2, 2), prisms="all", warp=0.1, seed=5), 7)]
+
+
+def _mixed_type_build(precision):
+    from oracle.mixedfr import MixedFR
+    oras, meshes, Qs = [], [], []
+    for k, (d, p) in enumerate(_mixed_type_specs()):
+        ph = I.tgv_physics(Ma=0.2, Re=300.0)
+        ph.precision = precision
+        ora = MixedFR(d, I.tgv_physics(Ma=0.2, Re=300.0), p)
+        Q = [np.ascontiguousarray(I.tgv_state(x, Ma=0.2, perturb=1e-2, seed=k)) for x in ora.x]
+        m = fr.Mesh(d, ph, p)
+        m.set_state(np.ascontiguousarray(np.concatenate([q.reshape(-1, 5) for q in Q])))
+        oras.append(ora)
+        meshes.append(m)
+        Qs.append(Q)
+    return oras, meshes, Qs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_mixed_element_types(precision, mode):
+    dt = 1e-3
+    _, single, _ = _mixed_type_build(precision)
+    oras, batched, Qs = _mixed_type_build(precision)
+    for m in single:
+        for _ in range(2):
+            m.rk_step(0.0, dt)
+    with fr.Batch(batched) as b:
+        b.select(mode)
+        b.set_dt([dt] * len(batched))
+        assert b.info()["block"] == 512
+        for _ in range(2):
+            b.rk_step(0.0)
+    for a, c in zip(single, batched):
+        if mode == 1:
+            np.testing.assert_array_equal(c.get_state(), a.get_state())
+        else:
+            _close(c.get_state(), a.get_state())
+    if precision == 0 and mode == 0:
+        # one case against the oracle's RK44 (two steps)
+        ora, m, Q = oras[0], batched[0], Qs[0]
+        S = np.concatenate([s.reshape(-1, 5) for s in ora.residual(Q, magnitude=True)])
+        for _ in range(2):
+            k1 = ora.residual(Q)
+            k2 = ora.residual([q + 0.5 * dt * k for q, k in zip(Q, k1)])
+            k3 = ora.residual([q + 0.5 * dt * k for q, k in zip(Q, k2)])
+            k4 = ora.residual([q + dt * k for q, k in zip(Q, k3)])
+            Q = [q + dt / 6.0 * (a + 2 * b_ + 2 * c + e) for q, a, b_, c, e in zip(Q, k1, k2, k3, k4)]
+        assert_state_parity(m.get_state(), np.concatenate([q.reshape(-1, 5) for q in Q]), S, 2 * dt)
+
+
+def test_batch_mixed_types_tuning_restores_state():
+    oras, meshes, Qs = _mixed_type_build(1)
+    before = [m.get_state().copy() for m in meshes]
+    with fr.Batch(meshes) as b:
+        b.set_dt([1e-3] * len(meshes))
+        b.tune()
+        info = b.info()
+        assert info["mode"] in (0, 1) and info["n_points"] == sum(m.n_points for m in meshes)
+        for m, q in zip(meshes, before):
+            np.testing.assert_array_equal(m.get_state(), q)
+        b.rk_step(0.0)
+    for m in meshes:
+        assert np.isfinite(m.get_state()).all()
