@@ -36,13 +36,13 @@ namespace {
 
 
 template <int N>
-constexpr int prism_points() { return N * (N + 1) / 2 * N; }
+__host__ __device__ constexpr int prism_points() { return N * (N + 1) / 2 * N; }
 template <int N>
-constexpr int prism_threads() { return ((prism_points<N>() + 31) / 32) * 32; }
+__host__ __device__ constexpr int prism_threads() { return ((prism_points<N>() + 31) / 32) * 32; }
 // Shared-memory values (of T) of the volume kernel: Q 5, grad 15, flux 15, BR2 weights 15, quad
 // lifts 15 (per point) and the jumps of 5 faces x 5 variables x N^2 slots.
 template <int N>
-constexpr int prism_smem_values() { return 65 * prism_points<N>() + 25 * N * N; }
+__host__ __device__ constexpr int prism_smem_values() { return 65 * prism_points<N>() + 25 * N * N; }
 
 
 // Interface slot of local flux point r of prism face f for a packed face word.
