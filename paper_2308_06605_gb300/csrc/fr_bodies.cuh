@@ -799,7 +799,7 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
       // Sub-blocks of nth threads, one element each; threads past the last full sub-block idle.
       const int tpe = ((N * N * N + 31) / 32) * 32;
       const int nth = tpe >= (int)blockDim.x ? (int)blockDim.x : tpe;
-      const int epb = (int)blockDim.x / nth;
+      const int epb = batch_elems_per_block(N, (int)blockDim.x);
       const int le = (int)threadIdx.x / nth;
       const int tid = (int)threadIdx.x % nth;
       const int64_t e = tk.begin + le;
@@ -823,7 +823,7 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
     case TASK_PRISM_VOLUME: {
       const int tpe = ((N * (N + 1) / 2 * N + 31) / 32) * 32;
       const int nth = tpe >= (int)blockDim.x ? (int)blockDim.x : tpe;
-      const int epb = (int)blockDim.x / nth;
+      const int epb = batch_prism_elems_per_block(N, (int)blockDim.x);
       const int le = (int)threadIdx.x / nth;
       const int tid = (int)threadIdx.x % nth;
       const int64_t e = tk.begin + le;

@@ -120,15 +120,23 @@ cudaError_t launch_gather_flags(const BatchCase *cases, int n, BatchSync *sy, cu
 size_t batch_smem_bytes(const int *Ns, const int *has_prism, int n, int block, int mixed);
 // Resident blocks per SM of the batch kernel for the given configuration.
 cudaError_t batch_occupancy(int mixed, int block, size_t smem, int *blocks_per_sm);
-// Elements a block of `block` threads processes at once in the volume phase for order N.
-inline int batch_elems_per_block(int N, int block) {
-  const int tpe = ((N * N * N + 31) / 32) * 32;
-  return tpe >= block ? 1 : block / tpe;
+// Elements a block of `block` threads processes at once in the volume phase for order N: as many
+// sub-blocks of (points rounded up to a warp) threads as fit, capped so that their shared memory
+// stays within kBatchSmemBudget bytes.  Host (task lists, shared-memory size) and device (sub-block
+// layout) use the same functions.
+constexpr int kBatchSmemBudget = 220 * 1024;
+FRX_HD inline int batch_fit(int points, int smem_values, int block) {
+  const int tpe = ((points + 31) / 32) * 32;
+  const int by_threads = tpe >= block ? 1 : block / tpe;
+  const int by_smem = kBatchSmemBudget / (smem_values * 8);
+  return by_threads < by_smem ? by_threads : (by_smem > 0 ? by_smem : 1);
+}
+FRX_HD inline int batch_elems_per_block(int N, int block) {
+  return batch_fit(N * N * N, 35 * N * N * N + 30 * N * N, block);
 }
 // The same for prisms (N(N+1)/2 x N points).
-inline int batch_prism_elems_per_block(int N, int block) {
-  const int tpe = ((N * (N + 1) / 2 * N + 31) / 32) * 32;
-  return tpe >= block ? 1 : block / tpe;
+FRX_HD inline int batch_prism_elems_per_block(int N, int block) {
+  return batch_fit(N * (N + 1) / 2 * N, 65 * (N * (N + 1) / 2 * N) + 25 * N * N, block);
 }
 
 // Accessors of the opaque mesh (fr_api.cu): a copy of its device view (fails if poisoned), and
