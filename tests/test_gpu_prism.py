@@ -168,15 +168,13 @@ def test_free_stream_on_perturbed_mixed_mesh():
     assert np.abs(R).max() <= 1e-10
 
 
-def test_prism_meshes_reject_closure_batch_and_static():
+def test_prism_meshes_reject_closure_and_static():
     torch = pytest.importorskip("torch")
     d = _mesh((2, 2, 2), "checker", seed=11)
     ph = _phys()
     with fr.Mesh(d, ph, 2) as g:
         with pytest.raises(fr.FRError, match="FR_EUNSUPPORTED"):
             g.set_closure(np.zeros(9153, np.float32), np.concatenate([np.zeros(11), np.ones(12)]).astype(np.float32))
-        with pytest.raises(fr.FRError, match="FR_EUNSUPPORTED"):
-            fr.Batch([g])
         Q = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
         with pytest.raises(fr.FRError, match="FR_EUNSUPPORTED"):
             g.residual_static(Q, torch.empty_like(Q))
