@@ -50,7 +50,11 @@ enum { FR_HOST = 0, FR_DEVICE = 1 };                       /* where a state poin
 enum { FR_RUSANOV = 0, FR_ROE = 1 };                       /* inviscid common flux */
 enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1 };                /* viscous treatment */
 enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1 };              /* arithmetic of the element operators */
-enum { FR_RK44 = 0 };                                      /* classical four-stage Runge–Kutta */
+enum {                                                     /* explicit Runge–Kutta schemes */
+  FR_RK44 = 0,      /* classical four-stage, fourth order */
+  FR_SSPRK33 = 1,   /* three-stage third-order SSP (Shu–Osher form), SSP coefficient 1 */
+  FR_SSPRK104 = 2   /* Ketcheson's ten-stage fourth-order SSP scheme (two registers), coefficient 6 */
+};
 enum {                                                     /* boundary-condition kinds */
   FR_BC_WALL_ISOTHERMAL = 1,  /* params[0] = wall temperature */
   FR_BC_CHAR_INFLOW = 2,      /* params = total pressure, total temperature, flow direction (3) */
@@ -175,6 +179,13 @@ fr_status fr_residual(fr_mesh *mesh, double t, double *R, int32_t where);
  * Stages must be called in order 0,1,2,3;
  * `t` is the time at the start of the step.  Returns FR_ENONFINITE (checked at stage 3 only) if
  * a non-finite value was written.
+ * The paper names strong-stability-preserving RK (Ketcheson 2008) as its integrator; two are
+ * built, with FP64 registers on both precisions (U_n, the stage state U, and acc):
+ *   FR_SSPRK33  stages 0..2:  U = a_k U_n + b_k (U + dt R), (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3)
+ *   FR_SSPRK104 stages 0..9:  U = U + dt/6 R (stages 0..8); after stage 4, q2 = U_n/25 + 9/25 U is
+ *               kept in acc and U = 15 q2 - 5 U; stage 9: U = q2 + 3/5 U + dt/10 R.
+ * At the last stage U_n = U and non-finite values are reported.  Between stages fr_get_state
+ * returns the stage state U for these schemes (on both precisions).
  */
 fr_status fr_rk_stage(fr_mesh *mesh, int32_t scheme, int32_t stage, double t, double dt);
 

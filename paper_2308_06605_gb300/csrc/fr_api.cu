@@ -359,10 +359,16 @@ extern "C" fr_status fr_rk_stage(fr_mesh *m, int32_t scheme, int32_t stage, doub
   (void)t;
   fr_status st = check_mesh(m);
   if (st) return st;
-  if (scheme != FR_RK44) return fail(m, FR_EUNSUPPORTED, "only RK44 is built");
-  if (stage < 0 || stage > 3 || !std::isfinite(dt)) return fail(m, FR_EINVAL, "bad stage or dt");
-  FR_CUDA(m, launch_residual(m->dev, m->dphys, MODE_RK, stage, dt, nullptr, m->stream, next_events(m)));
-  if (stage == 3) {
+  int mode, last;
+  switch (scheme) {
+    case FR_RK44: mode = MODE_RK; last = 3; break;
+    case FR_SSPRK33: mode = MODE_SSP33; last = 2; break;
+    case FR_SSPRK104: mode = MODE_SSP104; last = 9; break;
+    default: return fail(m, FR_EINVAL, "unknown Runge-Kutta scheme");
+  }
+  if (stage < 0 || stage > last || !std::isfinite(dt)) return fail(m, FR_EINVAL, "bad stage or dt");
+  FR_CUDA(m, launch_residual(m->dev, m->dphys, mode, stage, dt, nullptr, m->stream, next_events(m)));
+  if (stage == last) {
     int *hflag = reinterpret_cast<int *>(m->h_scalar);
     FR_CUDA(m, cudaMemcpyAsync(hflag, m->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     FR_CUDA(m, cudaStreamSynchronize(m->stream));

@@ -51,7 +51,9 @@ struct DevMesh {
   int8_t *if_tri;          // [n_if] 1: triangular interface (only its first Nt slots are used)
 };
 
-enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
+// What the correction kernels do with the residual: write it, or apply a stage of RK44, of the
+// three-stage SSP scheme (Shu-Osher form) or of Ketcheson's ten-stage fourth-order SSP scheme.
+enum { MODE_RESIDUAL = 0, MODE_RK = 1, MODE_SSP33 = 2, MODE_SSP104 = 3 };
 
 // Optional per-kernel event pairs (instrumentation); null = off.
 struct PhaseEvents {

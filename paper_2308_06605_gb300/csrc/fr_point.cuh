@@ -193,6 +193,44 @@ __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int 
     for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];
     return;
   }
+  if (mode == MODE_SSP33 || mode == MODE_SSP104) {
+    // FP64 registers on both paths: U_n (start of the step), Q (stage state) and, for the ten-stage
+    // scheme, acc (its second register); the mixed path also refreshes the double-float copy Qc.
+    //   SSP(3,3):  Q <- a_k U_n + b_k (Q + dt R), (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3).
+    //   SSP(10,4): Q <- Q + dt/6 R at stages 0..8; after stage 4 the registers recombine,
+    //              q2 = U_n/25 + 9/25 Q, Q <- 15 q2 - 5 Q; stage 9: Q <- q2 + 3/5 Q + dt/10 R.
+    const int last = mode == MODE_SSP33 ? 2 : 9;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t o = t * 5 + v;
+      const double q = Q[o];
+      double nq;
+      if (mode == MODE_SSP33) {
+        const double a = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+        const double b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+        nq = a * Un[o] + b * fma(dt, rd[v], q);
+      } else if (stage < 9) {
+        nq = fma(dt / 6.0, rd[v], q);
+        if (stage == 4) {
+          const double q2 = Un[o] / 25.0 + 9.0 / 25.0 * nq;
+          acc[o] = q2;
+          nq = 15.0 * q2 - 5.0 * nq;
+        }
+      } else {
+        nq = acc[o] + 0.6 * q + 0.1 * dt * rd[v];
+      }
+      Q[o] = nq;
+      if constexpr (std::is_same<T, df32>::value) Qc[o] = from_double<T>(nq);
+      if (stage == last) {
+        Un[o] = nq;
+        if constexpr (std::is_same<T, df32>::value) Unc[o] = from_double<T>(nq);
+        bad |= !isfinite(nq);
+      }
+    }
+    if (bad) atomicOr(flag, 1);
+    return;
+  }
   const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double anext[3] = {0.5, 0.5, 1.0};
   bool bad = false;

@@ -20,7 +20,8 @@ FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_EMESH, FR_EUNSUPPORTED, FR_ENONFINITE,
 STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_EUNSUPPORTED",
                 "FR_ENONFINITE", "FR_ETIMEOUT"]
 FR_HOST, FR_DEVICE = 0, 1
-FR_RK44 = 0
+FR_RK44, FR_SSPRK33, FR_SSPRK104 = 0, 1, 2
+RK_STAGES = {FR_RK44: 4, FR_SSPRK33: 3, FR_SSPRK104: 10}
 
 
 class FRError(RuntimeError):
@@ -240,9 +241,9 @@ class Mesh:
     def rk_stage(self, stage: int, t: float, dt: float, scheme: int = FR_RK44):
         self._check(self._lib.fr_rk_stage(self._h, scheme, stage, t, dt))
 
-    def rk_step(self, t: float, dt: float):
-        for s in range(4):
-            self.rk_stage(s, t, dt)
+    def rk_step(self, t: float, dt: float, scheme: int = FR_RK44):
+        for s in range(RK_STAGES[scheme]):
+            self.rk_stage(s, t, dt, scheme)
 
     def max_dt(self, cfl: float) -> float:
         v = C.c_double()
