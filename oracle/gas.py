@@ -145,3 +145,9 @@ def roe_dissipation(QL, QR, n, gamma, delta=0.1, absolute=True):
 def common_flux(kind, QL, QR, n, gamma):
     """Inviscid common flux: kind 0 = Rusanov, 1 = Roe."""
     return roe(QL, QR, n, gamma) if kind == 1 else rusanov(QL, QR, n, gamma)
+
+
+# LDG (Cockburn & Shu; the paper's viscous scheme via Huynh 2009): at each interface one side
+# supplies the common solution and the other the common gradient.  The choice is geometric: the
+# side whose outward normal, summed over the face, points along LDG_SWITCH supplies Q^I.
+LDG_SWITCH = np.array([1.0, np.sqrt(2.0) / 2.0, np.sqrt(3.0) / 4.0])

@@ -18,6 +18,10 @@ per-element operators built as Kronecker products of the 1D arrays of `basis`:
   interpolated to the face plus eta times the face's own lifting r_f interpolated to the face;
   the common gradient is the average of the two sides; the common viscous flux is
   F_v(Q^I, common gradient) . n.
+  Viscous part, LDG (viscous = 2): per interface the side whose face normal points along
+  gas.LDG_SWITCH supplies Q^I (its own trace), the other side supplies the common gradient; side
+  gradients are the corrected gradient interpolated to the face; the common flux adds the penalty
+  tau |n| (Q_0 - Q_1) (side 0's frame) and at boundaries tau |n| (Q- - Q_b).
   Time: classical four-stage Runge-Kutta.
 
 Reference faces: f = 2 d + (s + 1)/2, i.e. 0: xi=-1, 1: xi=+1, 2: eta=-1, 3: eta=+1,
@@ -298,6 +302,7 @@ class HexFR:
         ph = self.phys
         gam = ph.gamma
         viscous = ph.viscous != 0 and ph.mu != 0.0
+        ldg = viscous and ph.viscous == 2
         E, Nf = self.E, self.Nf
         rows = np.arange(self.n_if)[:, None]
         # Solution at flux points, both sides of every interface.
@@ -305,7 +310,11 @@ class HexFR:
         QL = Qf[self.eL, self.fL]
         QR = Qf[self.eR, self.fR][rows, self.perm]
         Qc_face = np.empty_like(Qf)                                # common solution per element face
-        QI = 0.5 * (QL + QR)
+        if ldg:
+            up = (self.nL.sum(axis=1) @ gas.LDG_SWITCH) > 0        # side 0 supplies Q^I
+            QI = np.where(up[:, None, None], QL, QR)
+        else:
+            QI = 0.5 * (QL + QR)
         Qc_face[self.eL, self.fL] = QI
         Qc_face[self.eR, self.fR] = QI[rows, self.invperm]
         ghosts, bstates = [], []
@@ -332,7 +341,10 @@ class HexFR:
             gface = np.empty((E, 6, Nf, 3, 5))
             for f in range(6):
                 r_f = np.einsum('emj,emv->emjv', Sinv[:, :, FACE_AXIS[f], :], lifts[f])
-                gface[:, f] = np.einsum('qm,emjv->eqjv', self.Lf[f], grad_unc + ph.br2_eta * r_f)
+                if ldg:
+                    gface[:, f] = np.einsum('qm,emjv->eqjv', self.Lf[f], grad)
+                else:
+                    gface[:, f] = np.einsum('qm,emjv->eqjv', self.Lf[f], grad_unc + ph.br2_eta * r_f)
             kappa0 = ph.mu * gam * ph.R / ((gam - 1.0) * ph.Pr)
             cp = gam * ph.R / (gam - 1.0)
             nu_el = np.zeros(E)
@@ -356,10 +368,12 @@ class HexFR:
         if viscous:
             gL = gface[self.eL, self.fL]
             gR = gface[self.eR, self.fR][rows, self.perm]
-            gc = 0.5 * (gL + gR)
+            gc = np.where(up[:, None, None, None], gR, gL) if ldg else 0.5 * (gL + gR)
             nu_if = 0.5 * (nu_el[self.eL] + nu_el[self.eR])[:, None] * QI[..., 0]
             FI = FI - np.einsum('pqjv,pqj->pqv', gas.viscous_flux(QI, gc, gam, ph.R, ph.mu + nu_if, ph.Pr,
                                                                   kappa=kappa0 + nu_if * cp / PR_TURB), self.nL)
+            if ldg:
+                FI = FI + ph.ldg_tau * np.linalg.norm(self.nL, axis=-1)[..., None] * (QL - QR)
         Fc = np.empty_like(Fperp)
         Fc[self.eL, self.fL] = FI
         Fc[self.eR, self.fR] = -FI[rows, self.invperm]
@@ -373,6 +387,8 @@ class HexFR:
                 nb = nu_el[e] * bstates[k][..., 0]
                 Fb = Fb - np.einsum('qjv,qj->qv', gas.viscous_flux(bstates[k], gface[e, f], gam, ph.R, ph.mu + nb, ph.Pr,
                                                                    kappa=kappa0 + nb * cp / PR_TURB), n)
+                if ldg:
+                    Fb = Fb + ph.ldg_tau * np.linalg.norm(n, axis=-1)[:, None] * (Qm - bstates[k])
             Fc[e, f] = Fb
         if magnitude:
             A = np.abs(Hhat)

@@ -219,13 +219,17 @@ class MixedFR:
         ph = self.phys
         gam = ph.gamma
         visc = ph.viscous != 0 and ph.mu != 0.0
+        ldg = visc and ph.viscous == 2
         T = self.types
         Qf = [[np.einsum('qm,emv->eqv', f["L"], Q) for f in t.faces] for t, Q in zip(T, Qs)]
         dQ = [[np.zeros_like(a) for a in qf] for qf in Qf]
-        Qc_if, gh = [], []
+        Qc_if, gh, ups = [], [], []
         for (tL, eL, fL, tR, eR, fR, perm) in self.ifaces:
             qL, qR = Qf[tL][fL][eL], Qf[tR][fR][eR][perm]
-            qI = 0.5 * (qL + qR)
+            # LDG: the side whose face normal points along gas.LDG_SWITCH supplies Q^I.
+            up = bool(self.nf[tL][fL][eL].sum(axis=0) @ gas.LDG_SWITCH > 0)
+            ups.append(up)
+            qI = (qL if up else qR) if ldg else 0.5 * (qL + qR)
             dQ[tL][fL][eL] = qI - qL
             dQ[tR][fR][eR][perm] = qI - qR
             Qc_if.append(qI)
@@ -250,6 +254,9 @@ class MixedFR:
             gunc = np.einsum('emdj,emdv->emjv', Sinv, gu)
             gf = []
             for fi, f in enumerate(t.faces):
+                if ldg:
+                    gf.append(np.einsum('qm,emjv->eqjv', f["L"], grad))
+                    continue
                 rf = np.einsum('emdj,d,emv->emjv', Sinv, f["N"], lifts[fi])
                 gf.append(np.einsum('qm,emjv->eqjv', f["L"], gunc + ph.br2_eta * rf))
             H = gas.inviscid_flux(Q, gam)
@@ -264,8 +271,11 @@ class MixedFR:
             n = self.nf[tL][fL][eL]
             F = gas.common_flux(ph.inviscid_flux, qL, qR, n, gam)
             if visc:
-                g = 0.5 * (gfaces[tL][fL][eL] + gfaces[tR][fR][eR][perm])
+                gl, gr = gfaces[tL][fL][eL], gfaces[tR][fR][eR][perm]
+                g = (gr if ups[k] else gl) if ldg else 0.5 * (gl + gr)
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(Qc_if[k], g, gam, ph.R, ph.mu, ph.Pr), n)
+                if ldg:
+                    F = F + ph.ldg_tau * np.linalg.norm(n, axis=-1)[:, None] * (qL - qR)
             Fc[tL][fL][eL] = F
             Fc[tR][fR][eR][perm] = -F
         for k, (ti, e, fi, bc) in enumerate(self.bfaces):
@@ -273,6 +283,8 @@ class MixedFR:
             F = gas.common_flux(ph.inviscid_flux, Qf[ti][fi][e], ghosts[k], n, gam)
             if visc:
                 F = F - np.einsum('qjv,qj->qv', gas.viscous_flux(bst[k], gfaces[ti][fi][e], gam, ph.R, ph.mu, ph.Pr), n)
+                if ldg:
+                    F = F + ph.ldg_tau * np.linalg.norm(n, axis=-1)[:, None] * (Qf[ti][fi][e] - bst[k])
             Fc[ti][fi][e] = F
         out = []
         if magnitude:

@@ -510,8 +510,9 @@ class Physics:
     mu: float = 0.0
     Pr: float = 0.71
     inviscid_flux: int = 0      # 0 = Rusanov, 1 = Roe
-    viscous: int = 1            # 0 = Euler, 1 = BR2
+    viscous: int = 1            # 0 = Euler, 1 = BR2, 2 = LDG
     br2_eta: float = 6.0
+    ldg_tau: float = 0.1        # LDG penalty
     vcjh_c: float = 0.0
     precision: int = 0          # 0 = FP64, 1 = mixed (FP32 element operators)
 
