@@ -48,7 +48,7 @@ typedef enum {
 
 enum { FR_HOST = 0, FR_DEVICE = 1 };                       /* where a state pointer lives */
 enum { FR_RUSANOV = 0, FR_ROE = 1 };                       /* inviscid common flux */
-enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1 };                /* viscous treatment */
+enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1, FR_VISC_LDG = 2 }; /* viscous treatment */
 enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1 };              /* arithmetic of the element operators */
 enum {                                                     /* explicit Runge–Kutta schemes */
   FR_RK44 = 0,      /* classical four-stage, fourth order */
@@ -112,6 +112,11 @@ typedef struct {
   int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED: element operators (traces, gradients,
                            fluxes at solution points, divergence, correction) in double-float
                            (FP32 hi + lo pairs); Riemann flux, boundary states and RK in FP64 */
+  double ldg_tau;       /* LDG penalty tau (FR_VISC_LDG): at each interface the side whose face
+                           normal (summed over the face) points along (1, sqrt2/2, sqrt3/4)
+                           supplies the common solution, the other side the common gradient
+                           (corrected gradients interpolated to the face), and the common
+                           normal flux gains tau |n| (Q_0 - Q_1) (boundaries: tau |n| (Q- - Q_b)) */
 } fr_physics;
 
 typedef struct {

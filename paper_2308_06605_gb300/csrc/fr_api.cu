@@ -102,6 +102,7 @@ static void release(fr_mesh *m) {
   if (d.ef_p) cudaFree(d.ef_p);
   if (d.tri_slot) cudaFree(d.tri_slot);
   if (d.if_tri) cudaFree(d.if_tri);
+  if (d.if_up) cudaFree(d.if_up);
   if (m->d_cw) cudaFree(m->d_cw);
   if (m->d_cscale) cudaFree(m->d_cscale);
   m->d_cw = nullptr;
@@ -143,8 +144,10 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
     return fail(nullptr, FR_EINVAL, "bad physical parameters");
   if (phys->inviscid != FR_RUSANOV && phys->inviscid != FR_ROE)
     return fail(nullptr, FR_EINVAL, "unknown inviscid flux");
-  if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2)
+  if (phys->viscous != FR_VISC_NONE && phys->viscous != FR_VISC_BR2 && phys->viscous != FR_VISC_LDG)
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
+  if (phys->viscous == FR_VISC_LDG && !(phys->ldg_tau >= 0.0))
+    return fail(nullptr, FR_EINVAL, "LDG penalty must be non-negative");
   if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED)
     return fail(nullptr, FR_EINVAL, "unknown precision");
   for (int k = 0; k < desc->n_bc; ++k) {
@@ -184,17 +187,19 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   dp.R = phys->R;
   dp.mu = phys->mu;
   dp.kappa = phys->mu * phys->gamma * phys->R / ((phys->gamma - 1.0) * phys->Pr);
-  dp.eta = phys->br2_eta;
-  dp.viscous = (phys->viscous == FR_VISC_BR2 && phys->mu > 0.0) ? 1 : 0;
+  dp.viscous = (phys->viscous != FR_VISC_NONE && phys->mu > 0.0) ? 1 : 0;
+  dp.ldg = phys->viscous == FR_VISC_LDG ? 1 : 0;
+  dp.ldg_tau = dp.ldg ? phys->ldg_tau : 0.0;
+  dp.eta = dp.ldg ? 0.0 : phys->br2_eta;     // LDG's face gradients carry no lifting term
   dp.inviscid = phys->inviscid;
   {
-    const double vals[10] = {dp.gamma, dp.gamma - 1.0, (dp.gamma - 1.0) / dp.R, dp.mu, -2.0 * dp.mu / 3.0,
-                             dp.kappa, dp.eta, 0.0, 0.5, 1.0};
-    double *dd[10] = {&dp.d.gamma, &dp.d.gm1, &dp.d.cT, &dp.d.mu, &dp.d.m2mu3, &dp.d.kappa, &dp.d.eta,
-                      &dp.d.zero, &dp.d.half, &dp.d.one};
-    df32 *ff[10] = {&dp.f.gamma, &dp.f.gm1, &dp.f.cT, &dp.f.mu, &dp.f.m2mu3, &dp.f.kappa, &dp.f.eta,
-                    &dp.f.zero, &dp.f.half, &dp.f.one};
-    for (int k = 0; k < 10; ++k) {
+    const double vals[11] = {dp.gamma, dp.gamma - 1.0, (dp.gamma - 1.0) / dp.R, dp.mu, -2.0 * dp.mu / 3.0,
+                             dp.kappa, dp.eta, 0.0, 0.5, 1.0, dp.ldg_tau};
+    double *dd[11] = {&dp.d.gamma, &dp.d.gm1, &dp.d.cT, &dp.d.mu, &dp.d.m2mu3, &dp.d.kappa, &dp.d.eta,
+                      &dp.d.zero, &dp.d.half, &dp.d.one, &dp.d.tau};
+    df32 *ff[11] = {&dp.f.gamma, &dp.f.gm1, &dp.f.cT, &dp.f.mu, &dp.f.m2mu3, &dp.f.kappa, &dp.f.eta,
+                    &dp.f.zero, &dp.f.half, &dp.f.one, &dp.f.tau};
+    for (int k = 0; k < 11; ++k) {
       *dd[k] = vals[k];
       *ff[k] = df_split_host(vals[k]);
     }
@@ -241,6 +246,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
                    (st = dalloc(m, &d.ptab, h.ptab.size())) || (st = dalloc(m, &d.tri_slot, h.tri_slot.size())) ||
                    (st = dalloc(m, &d.if_tri, h.if_tri.size()))))
     return bail(st);
+  if ((st = dalloc(m, &d.if_up, h.if_up.size()))) return bail(st);
   if (d.mixed) {
     // Geometry in the element arithmetic's format: each double becomes a df32 (hi, lo) pair
     // stored in the same 8-byte slot.
@@ -265,6 +271,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
       {d.ptab, h.ptab.data(), h.ptab.size() * sizeof(double)},
       {d.tri_slot, h.tri_slot.data(), h.tri_slot.size() * sizeof(int32_t)},
       {d.if_tri, h.if_tri.data(), h.if_tri.size() * sizeof(int8_t)},
+      {d.if_up, h.if_up.data(), h.if_up.size() * sizeof(int8_t)},
   };
   for (const Up &u : ups) {
     if (u.bytes == 0) continue;

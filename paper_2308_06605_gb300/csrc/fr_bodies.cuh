@@ -219,7 +219,8 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
                                             const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
                                             const T *__restrict__ liftfac, T *__restrict__ Gtr,
                                             T *__restrict__ Rpart, const DevPhys &dph,
-                                            const double *__restrict__ hel, float *__restrict__ nu_out) {
+                                            const double *__restrict__ hel, float *__restrict__ nu_out,
+                                            const int8_t *__restrict__ if_up, int64_t n_interior) {
   constexpr int Np = N * N * N, Nf = N * N;
   T *sm = reinterpret_cast<T *>(sm_raw);
   T *sQ = sm;                 // [5][Np]
@@ -240,8 +241,12 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
       const int slot = slot_of(packed & 7, r % N, r / N, N);
       const T *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
       const T *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
+      // Q^I - Q_own.  BR2: (other - own)/2 (a boundary's other slot holds 2 Q^I - Q-).  LDG: 0 on
+      // the side that supplies Q^I, other - own on the other; boundaries as BR2.
+      T w = ph.half;
+      if (dph.ldg && I < n_interior) w = side == (if_up[I] ? 0 : 1) ? ph.zero : ph.one;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = ph.half * (oth[v * Nf] - own[v * Nf]);
+      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = w * (oth[v * Nf] - own[v * Nf]);
     }
   }
   __syncthreads();
@@ -308,8 +313,9 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
           dc.add(s0, gc[0][v]);
           dc.add(s1, gc[1][v]);
           dc.add(s2, gc[2][v]);
-          sG[(jj * 5 + v) * Np + m] = du.get();
           G[jj * 5 + v] = dc.get();
+          // Face-gradient source: BR2 the uncorrected gradient (+ eta r_f), LDG the corrected one.
+          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();
         }
       }
     }
@@ -435,10 +441,11 @@ template <int N, typename T>
 __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
     k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
              const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
-             DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out) {
+             DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out,
+             const int8_t *__restrict__ if_up, int64_t n_interior) {
   extern __shared__ double sm_raw[];
   volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr, Rpart,
-                    dph, hel, nu_out);
+                    dph, hel, nu_out, if_up, n_interior);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -449,7 +456,7 @@ template <int N, typename T>
 __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                                            const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if,
                                            const DevPhys &dph, const int32_t *__restrict__ if_elem,
-                                           const float *__restrict__ nu) {
+                                           const float *__restrict__ nu, const int8_t *__restrict__ if_up) {
   constexpr int Nf = N * N;
   if (t >= n_if * Nf) return;
   const int64_t I = t / Nf;
@@ -487,17 +494,31 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
   }
   if (dph.viscous) {
     T qc[5], G[15];
+    if (dph.ldg) {
+      // LDG: the supplying side's solution, the other side's gradient.
+      const int sup = if_up[I] ? 0 : 1;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qc[v] = ph.half * (qL[v] + qR[v]);
+      for (int v = 0; v < 5; ++v) qc[v] = sup == 0 ? qL[v] : qR[v];
 #pragma unroll
-    for (int c = 0; c < 15; ++c)
-      G[c] = ph.half * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
+      for (int c = 0; c < 15; ++c) G[c] = Gtr[(I * 2 + (1 - sup)) * 15 * Nf + c * Nf + q];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qc[v] = ph.half * (qL[v] + qR[v]);
+#pragma unroll
+      for (int c = 0; c < 15; ++c)
+        G[c] = ph.half * (Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q] + Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
+    }
     T rho_nu = ph.zero;
     if (dph.closure) rho_nu = qc[0] * from_double<T>(0.5 * ((double)nu[if_elem[2 * I]] + (double)nu[if_elem[2 * I + 1]]));
     T Fv[3][5];
     viscous_flux<T>(qc, G, ph, visc_with(ph, rho_nu, dph), Fv);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
+    if (dph.ldg) {
+      const T tn = ph.tau * nn;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[v] += tn * (qL[v] - qR[v]);
+    }
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
@@ -506,8 +527,10 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
 template <int N, typename T>
 __global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                              const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph,
-                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu) {
-  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu);
+                             const int32_t *__restrict__ if_elem, const float *__restrict__ nu,
+                             const int8_t *__restrict__ if_up) {
+  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu,
+                   if_up);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -639,6 +662,10 @@ __device__ __forceinline__ void bc_flux_body(int64_t t, const T *__restrict__ Qt
     viscous_flux<T>(qiT, G, ph, visc_with(ph, rho_nu, dph), Fv);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] -= Fv[0][v] * nT[0] + Fv[1][v] * nT[1] + Fv[2][v] * nT[2];
+    if (dph.ldg) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[v] += from_double<T>(dph.ldg_tau * nn * (qm[v] - qi[v]));
+    }
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
@@ -716,10 +743,11 @@ __device__ __forceinline__ bool unused_tri_slot(int64_t t, int64_t first, int64_
 template <int N, typename T>
 __global__ void k_iface_flux_tri(const T *__restrict__ Qtr, const T *__restrict__ Gtr, const T *__restrict__ normals,
                                  T *__restrict__ FI, int64_t n_if, DevPhys dph, const int32_t *__restrict__ if_elem,
-                                 const float *__restrict__ nu, const int8_t *__restrict__ if_tri) {
+                                 const float *__restrict__ nu, const int8_t *__restrict__ if_tri,
+                                 const int8_t *__restrict__ if_up) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (unused_tri_slot<N>(t, 0, n_if, if_tri)) return;
-  iface_body<N, T>(t, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu);
+  iface_body<N, T>(t, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu, if_up);
 }
 
 template <int N, typename T>
@@ -805,12 +833,12 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
       const int64_t e = tk.begin + le;
       const bool active = le < epb && e < tk.end;
       volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * volume_smem_values<N>(), Qin, met,
-                        m.ef, Qtr, lift, Gtr, Rpart, c.ph, m.h, nullptr);
+                        m.ef, Qtr, lift, Gtr, Rpart, c.ph, m.h, nullptr, m.if_up, m.n_interior);
       break;
     }
     case TASK_IFACE:
       if (m.if_tri && unused_tri_slot<N>(idx, 0, m.n_interior, m.if_tri)) break;
-      iface_body<N, T>(idx, Qtr, Gtr, nrm, FI, m.n_interior, c.ph, m.if_elem, m.nu);
+      iface_body<N, T>(idx, Qtr, Gtr, nrm, FI, m.n_interior, c.ph, m.if_elem, m.nu, m.if_up);
       break;
     case TASK_BC_FLUX:
       if (m.if_tri && unused_tri_slot<N>(idx, m.n_interior, m.n_if - m.n_interior, m.if_tri)) break;
@@ -829,7 +857,8 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const BatchCase 
       const int64_t e = tk.begin + le;
       const bool active = le < epb && e < tk.end;
       prism_volume_body<N, T>(e, tid, nth, active, smem + (size_t)(le < epb ? le : 0) * prism_smem_values<N>(),
-                              Qin + pts, pmet, m.ef_p, Qtr, ptab, m.tri_slot, Gtr, Rpart + pts, c.ph);
+                              Qin + pts, pmet, m.ef_p, Qtr, ptab, m.tri_slot, Gtr, Rpart + pts, c.ph, m.if_up,
+                              m.n_interior);
       break;
     }
     case TASK_PRISM_CORRECT:

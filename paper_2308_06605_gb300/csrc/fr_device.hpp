@@ -14,13 +14,16 @@ namespace frx {
 // Physical constants in the element arithmetic's scalar type (double or df32).
 template <typename T>
 struct PhysT {
-  T gamma, gm1, cT, mu, m2mu3, kappa, eta;   // cT = (gamma-1)/R, m2mu3 = -2 mu / 3
+  T gamma, gm1, cT, mu, m2mu3, kappa, eta;   // cT = (gamma-1)/R, m2mu3 = -2 mu / 3; eta = 0 for LDG
   T zero, half, one;
+  T tau;                                     // LDG penalty
 };
 
 struct DevPhys {
   double gamma, R, mu, kappa, eta;
   int viscous;
+  int ldg;                 // viscous scheme: 0 BR2, 1 LDG
+  double ldg_tau;
   int inviscid;
   int closure;             // eddy-viscosity network on (weights below)
   double cp_prt;           // cp / Pr_t
@@ -49,6 +52,7 @@ struct DevMesh {
   double *ptab;            // prism operator table (prism_tab layout), in the element type
   int32_t *tri_slot;       // [6][Nt] side-0 slot of a side-1 triangle node per code
   int8_t *if_tri;          // [n_if] 1: triangular interface (only its first Nt slots are used)
+  int8_t *if_up;           // [n_if] LDG: 1 if side 0 supplies the common solution, else side 1
 };
 
 // What the correction kernels do with the residual: write it, or apply a stage of RK44, of the

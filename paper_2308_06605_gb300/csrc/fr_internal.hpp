@@ -119,6 +119,7 @@ struct HostMesh {
   std::vector<int32_t> ef_p;      // [Ep][5] packed like ef; triangular faces carry a kTriPerm code
   std::vector<double> metrics_p;  // [Ep][10][Npp]
   std::vector<int8_t> if_tri;     // [n_if] 1: triangular interface (meshes with prisms only)
+  std::vector<int8_t> if_up;      // [n_if] LDG switch: 1 if side 0 supplies the common solution
   std::vector<double> ptab;       // prism operator table (prism_tab layout)
   std::vector<int32_t> tri_slot;  // [6][Nt] side-0 slot of a side-1 node for each code
 };

@@ -87,7 +87,8 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
     if (E > 0)
-      k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu);
+      k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu, m.if_up,
+                                                         m.n_interior);
     if ((err = launch_prism_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(1);
   }
@@ -95,10 +96,11 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
     if (n > 0 && !tri)
-      k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu);
+      k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu,
+                                                                       m.if_up);
     if (n > 0 && tri)
       k_iface_flux_tri<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph,
-                                                                         m.if_elem, m.nu, m.if_tri);
+                                                                         m.if_elem, m.nu, m.if_tri, m.if_up);
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
     if (nb > 0 && !tri)
       k_bc_flux<N, T><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, m.if_bc, m.bcs, FI, m.n_interior,

@@ -827,6 +827,22 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
     }
     m.tri_slot = tb.perm;
   }
+  // LDG switch per interface: side 0 supplies the common solution when its outward normal, summed
+  // over the face's flux points, points along (1, sqrt(2)/2, sqrt(3)/4).
+  m.if_up.assign(m.n_if, 0);
+  {
+    const double sw[3] = {1.0, std::sqrt(2.0) / 2.0, std::sqrt(3.0) / 4.0};
+    for (int64_t I = 0; I < n_int; ++I) {
+      const int nq = (Ep > 0 && m.if_tri[I]) ? Nt : Nf;
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int r = 0; r < nq; ++r) acc += m.normals[((size_t)I * 4 + c) * Nf + r];
+        s += acc * sw[c];
+      }
+      m.if_up[I] = s > 0.0 ? 1 : 0;
+    }
+  }
   // Check that every side-1 flux point lands on its side-0 slot (coordinates, with shift).
   for (int64_t I = 0; I < n_int; ++I) {
     bool per = I >= (int64_t)pairs.size();

@@ -42,10 +42,11 @@ template <int N, typename T>
 __global__ void __launch_bounds__(prism_threads<N>())
     k_prism_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef_p,
                    const T *__restrict__ Qtr, const T *__restrict__ tab, const int32_t *__restrict__ tri_slot,
-                   T *__restrict__ Gtr, T *__restrict__ Rpart, DevPhys dph) {
+                   T *__restrict__ Gtr, T *__restrict__ Rpart, DevPhys dph, const int8_t *__restrict__ if_up,
+                   int64_t n_interior) {
   extern __shared__ double sm_raw[];
   prism_volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef_p, Qtr, tab, tri_slot,
-                          Gtr, Rpart, dph);
+                          Gtr, Rpart, dph, if_up, n_interior);
 }
 
 template <int N, typename T>
@@ -96,7 +97,7 @@ static cudaError_t prism_phase_impl(const DevMesh &m, const DevPhys &ph, int pha
     cudaError_t err = cudaFuncSetAttribute(k_prism_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_prism_volume<N, T><<<(unsigned)m.Ep, prism_threads<N>(), smem, st>>>(Qin, met, m.ef_p, Qtr, tab, m.tri_slot,
-                                                                          Gtr, Rpart, ph);
+                                                                          Gtr, Rpart, ph, m.if_up, m.n_interior);
   } else if (phase == 3) {
     const int64_t n = m.Ep * Np;
     k_prism_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(

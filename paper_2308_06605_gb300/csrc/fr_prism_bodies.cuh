@@ -108,7 +108,8 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
                                                   const T *__restrict__ Q, const T *__restrict__ metrics,
                                                   const int32_t *__restrict__ ef_p, const T *__restrict__ Qtr,
                                                   const T *__restrict__ tab, const int32_t *__restrict__ tri_slot,
-                                                  T *__restrict__ Gtr, T *__restrict__ Rpart, const DevPhys &dph) {
+                                                  T *__restrict__ Gtr, T *__restrict__ Rpart, const DevPhys &dph,
+                                                  const int8_t *__restrict__ if_up, int64_t n_interior) {
   constexpr int Nt = N * (N + 1) / 2, Np = Nt * N, Nf = N * N;
   constexpr PrismTab L = prism_tab(N);
   T *sm = reinterpret_cast<T *>(sm_raw);
@@ -132,8 +133,11 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
       const int slot = prism_slot<N>(f, r, packed & 7, tri_slot);
       const T *own = Qtr + (I * 2 + side) * 5 * Nf + slot;
       const T *oth = Qtr + (I * 2 + (1 - side)) * 5 * Nf + slot;
+      // Q^I - Q_own: BR2 (other - own)/2; LDG 0 on the supplying side, other - own on the other.
+      T w = ph.half;
+      if (dph.ldg && I < n_interior) w = side == (if_up[I] ? 0 : 1) ? ph.zero : ph.one;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = ph.half * (oth[v * Nf] - own[v * Nf]);
+      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = w * (oth[v * Nf] - own[v * Nf]);
     }
   }
   __syncthreads();
@@ -216,8 +220,8 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
           dc.add(s0, gc[0][v]);
           dc.add(s1, gc[1][v]);
           dc.add(s2, gc[2][v]);
-          sG[(jj * 5 + v) * Np + m] = du.get();
           G[jj * 5 + v] = dc.get();
+          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();   // LDG: corrected
         }
         const T ej = ph.eta * invJ;
         sW[(0 * 3 + jj) * Np + m] = -(ej * S[2 * 3 + jj]);
