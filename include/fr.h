@@ -238,6 +238,18 @@ fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_de
 #define FR_CLOSURE_NPARAMS 9153
 #define FR_CLOSURE_PRT 0.9
 fr_status fr_set_closure(fr_mesh *mesh, const float *params, const float *scales, int32_t enable);
+
+/*
+ * fr_set_source — the source term S of Eq. 3 (the paper's body forcing and sponge zones near
+ * inflow and outflow), added to the residual at every solution point in FP64:
+ *   body acceleration g (accel[3], NULL = off):  S = (0, rho g, rho u . g)
+ *   sponge (sigma [n_points] >= 0 and Q_ref [n_points][5], canonical order, both NULL = off):
+ *                                                S = -sigma (Q - Q_ref)
+ * evaluated on the state the residual is computed from (the stage state in RK stages).  Host
+ * arrays are copied; a later call replaces the previous settings.  sigma without Q_ref (or the
+ * reverse), negative or non-finite values -> FR_EINVAL.
+ */
+fr_status fr_set_source(fr_mesh *mesh, const double *accel, const double *sigma, const double *Q_ref);
 fr_status fr_closure_nu(fr_mesh *mesh, float *nu_host);
 
 /*

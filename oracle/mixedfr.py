@@ -206,6 +206,23 @@ class MixedFR:
         self.bfaces = bfaces
         self.h = [np.cbrt(np.einsum('m,em->e', t.W, dJ)) for t, dJ in zip(self.types, self.detJ)]
 
+    def set_source(self, accel=None, sigma=None, Q_ref=None):
+        """Source term S of Eq. 3 added to the residual: body acceleration g (S = (0, rho g,
+        rho u . g)) and a sponge S = -sigma(x) (Q - Q_ref(x)); sigma and Q_ref are lists per element
+        type ([E][Np] and [E][Np][5]).  None switches a part off."""
+        self.accel = None if accel is None else np.asarray(accel, dtype=np.float64)
+        self.sigma = sigma
+        self.Q_ref = Q_ref
+
+    def _source(self, ti, Q):
+        S = np.zeros_like(Q)
+        if getattr(self, "accel", None) is not None:
+            S[..., 1:4] = Q[..., 0:1] * self.accel
+            S[..., 4] = Q[..., 1:4] @ self.accel
+        if getattr(self, "sigma", None) is not None:
+            S -= self.sigma[ti][..., None] * (Q - self.Q_ref[ti])
+        return S
+
     def solution_points(self):
         return [x.copy() for x in self.x]
 
@@ -294,14 +311,14 @@ class MixedFR:
                 for fi, f in enumerate(t.faces):
                     own = np.einsum('qm,emv->eqv', np.abs(f["L"]), np.einsum('d,emdv->emv', np.abs(f["N"]), A))
                     mag = mag + np.einsum('mq,eqv->emv', np.abs(f["C"]), np.abs(Fc[ti][fi]) + own)
-                out.append(mag / self.detJ[ti][..., None])
+                out.append(mag / self.detJ[ti][..., None] + np.abs(self._source(ti, Qs[ti])))
             return out
         for ti, t in enumerate(T):
             R = sum(np.einsum('mn,env->emv', t.Dop[d], Hhat[ti][:, :, d, :]) for d in range(3))
             for fi, f in enumerate(t.faces):
                 own = np.einsum('qm,emv->eqv', f["L"], np.einsum('d,emdv->emv', f["N"], Hhat[ti]))
                 R = R + np.einsum('mq,eqv->emv', f["C"], Fc[ti][fi] - own)
-            out.append(-R / self.detJ[ti][..., None])
+            out.append(-R / self.detJ[ti][..., None] + self._source(ti, Qs[ti]))
         return out
 
     def integrate(self, Rs):

@@ -24,6 +24,8 @@ struct fr_mesh {
   std::string err;
   int64_t bytes = 0;
   double *h_scalar = nullptr;   // pinned host scalar for dt / flags
+  // Source term arrays (allocated by fr_set_source).
+  double *d_sigma = nullptr, *d_qref = nullptr;
   // Eddy-viscosity closure (allocated by fr_set_closure).
   void *d_cw = nullptr;
   float *d_cscale = nullptr;
@@ -105,6 +107,9 @@ static void release(fr_mesh *m) {
   if (d.if_up) cudaFree(d.if_up);
   if (m->d_cw) cudaFree(m->d_cw);
   if (m->d_cscale) cudaFree(m->d_cscale);
+  if (m->d_sigma) cudaFree(m->d_sigma);
+  if (m->d_qref) cudaFree(m->d_qref);
+  m->d_sigma = m->d_qref = nullptr;
   m->d_cw = nullptr;
   m->d_cscale = nullptr;
   if (m->h_scalar) cudaFreeHost(m->h_scalar);
@@ -440,6 +445,34 @@ extern "C" fr_status fr_set_closure(fr_mesh *m, const float *params, const float
   m->dphys.cw = m->d_cw;
   m->dphys.cscale = m->d_cscale;
   m->dphys.cp_prt = m->phys.gamma * m->phys.R / (m->phys.gamma - 1.0) / FR_CLOSURE_PRT;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_set_source(fr_mesh *m, const double *accel, const double *sigma, const double *Q_ref) {
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if ((sigma == nullptr) != (Q_ref == nullptr)) return fail(m, FR_EINVAL, "sigma and Q_ref go together");
+  DevPhys &dp = m->dphys;
+  dp.src_body = accel ? 1 : 0;
+  for (int c = 0; c < 3; ++c) dp.accel[c] = accel ? accel[c] : 0.0;
+  if (accel)
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(accel[c])) return fail(m, FR_EINVAL, "non-finite body acceleration");
+  dp.src_sponge = 0;
+  if (!sigma) return FR_OK;
+  const size_t n = (size_t)m->dev.E * m->dev.Np + (size_t)m->dev.Ep * m->dev.Npp;
+  for (size_t i = 0; i < n; ++i)
+    if (!(sigma[i] >= 0.0) || !std::isfinite(sigma[i])) return fail(m, FR_EINVAL, "sponge strength must be >= 0");
+  if (!m->d_sigma) {
+    fr_status s;
+    if ((s = dalloc(m, &m->d_sigma, n)) || (s = dalloc(m, &m->d_qref, n * 5))) return s;
+  }
+  FR_CUDA(m, cudaMemcpyAsync(m->d_sigma, sigma, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  FR_CUDA(m, cudaMemcpyAsync(m->d_qref, Q_ref, n * 5 * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  FR_CUDA(m, cudaStreamSynchronize(m->stream));
+  dp.sigma = m->d_sigma;
+  dp.Q_ref = m->d_qref;
+  dp.src_sponge = 1;
   return FR_OK;
 }
 

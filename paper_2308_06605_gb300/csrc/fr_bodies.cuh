@@ -718,7 +718,7 @@ __device__ __forceinline__ void correct_body(int64_t t, const T *__restrict__ Rp
   T rv[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) rv[v] = r[v].get();
-  finish_point<T>(t, rv, s, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag);
+  finish_point<T>(t, rv, s, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag, dph);
 }
 
 template <int N, typename T>

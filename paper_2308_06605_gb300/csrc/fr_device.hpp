@@ -31,6 +31,11 @@ struct DevPhys {
   const float *cscale;     // [23] input mean (11), input std (11), output scale (device)
   PhysT<double> d;
   PhysT<df32> f;
+  // Source term S of Eq. 3 (fr_set_source): body acceleration and sponge, FP64.
+  int src_body, src_sponge;
+  double accel[3];
+  const double *sigma;     // [n_points] device
+  const double *Q_ref;     // [n_points][5] device
 };
 
 // Device buffers of one mesh (all owned by the mesh).

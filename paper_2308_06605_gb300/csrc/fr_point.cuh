@@ -184,10 +184,27 @@ template <typename T>
 __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int mode, int stage, double dt,
                                              double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
                                              double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
-                                             int *__restrict__ flag) {
+                                             int *__restrict__ flag, const DevPhys &dph) {
   double rd[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) rd[v] = to_double(rv[v] * s);
+  if (dph.src_body || dph.src_sponge) {
+    // Source term at the state the residual was evaluated on (the element kernels' input).
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = Qc ? to_double(Qc[t * 5 + v]) : Q[t * 5 + v];
+    if (dph.src_body) {
+      rd[1] += q[0] * dph.accel[0];
+      rd[2] += q[0] * dph.accel[1];
+      rd[3] += q[0] * dph.accel[2];
+      rd[4] += q[1] * dph.accel[0] + q[2] * dph.accel[1] + q[3] * dph.accel[2];
+    }
+    if (dph.src_sponge) {
+      const double sg = dph.sigma[t];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) rd[v] -= sg * (q[v] - dph.Q_ref[t * 5 + v]);
+    }
+  }
   if (mode == MODE_RESIDUAL) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rout[t * 5 + v] = rd[v];

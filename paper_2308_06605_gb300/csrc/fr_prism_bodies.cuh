@@ -367,7 +367,7 @@ __device__ __forceinline__ void prism_correct_body(int64_t t, const T *__restric
   T rv[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) rv[v] = r[v].get();
-  finish_point<T>(first_point + t, rv, s, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag);
+  finish_point<T>(first_point + t, rv, s, mode, stage, dt, Rout, Q, Qc, Un, Unc, acc, flag, dph);
 }
 
 }  // namespace

@@ -81,6 +81,7 @@ SIGNATURES = {
     "fr_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_set_closure": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32]),
     "fr_closure_nu": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "fr_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_mlp_workspace_floats": (C.c_int64, [C.c_int64]),
     "fr_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t]),
     "fr_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -258,6 +259,16 @@ class Mesh:
         self._keep_closure = (p, sc)
         self._check(self._lib.fr_set_closure(self._h, p.ctypes.data_as(C.POINTER(C.c_float)),
                                              sc.ctypes.data_as(C.POINTER(C.c_float)), 1 if enable else 0))
+
+    def set_source(self, accel=None, sigma=None, Q_ref=None):
+        """Source term: body acceleration (3,) and / or sponge strength sigma [n_points] with its
+        reference state Q_ref [n_points][5] (canonical order); None switches a part off."""
+        a = None if accel is None else np.ascontiguousarray(accel, dtype=np.float64)
+        sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+        qr = None if Q_ref is None else np.ascontiguousarray(Q_ref, dtype=np.float64)
+        self._keep_source = (a, sg, qr)
+        ptr = lambda x: None if x is None else C.c_void_p(x.ctypes.data)   # noqa: E731
+        self._check(self._lib.fr_set_source(self._h, ptr(a), ptr(sg), ptr(qr)))
 
     def closure_nu(self):
         out = np.empty(self.n_elem, dtype=np.float32)
