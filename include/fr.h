@@ -162,6 +162,17 @@ fr_status fr_solution_points(fr_mesh *mesh, double *xyz_host);
  * Runge–Kutta registers (the solution becomes the start of a new step).
  */
 fr_status fr_set_state(fr_mesh *mesh, const double *Q, int32_t where);
+
+/*
+ * fr_project_state — set dst's state to the L2 projection of src's current state onto dst's order
+ * (the paper starts at low order and switches to a higher one).  src and dst describe the same
+ * elements (same mesh description, any two orders); in reference coordinates the projection keeps
+ * the Legendre modal coefficients on each hexahedron axis, and the orthonormal triangle modes times
+ * Legendre on prisms, up to the lower of the two degrees.  Waits for src's stream, works on dst's
+ * and returns when done; dst's Runge-Kutta registers restart from the projected state.  Different
+ * element counts or devices -> FR_EINVAL.
+ */
+fr_status fr_project_state(fr_mesh *src, fr_mesh *dst);
 fr_status fr_get_state(fr_mesh *mesh, double *Q, int32_t where);
 
 /*

@@ -44,6 +44,9 @@ extern const int kTriPerm[6][3];
 // Point of edge e (0: s = -1, 1: r + s = 0, 2: r = -1) at parameter sigma in [-1, 1].
 void tri_edge_point(int edge, double sigma, double &r, double &s);
 bool make_tri_basis(int p, TriBasis &T);
+// [Nt_q][Nt_p]: the L2 projection from the order-p to the order-q triangle (nodal values in,
+// nodal values out; orthonormal modes of total degree <= min(p, q) kept).
+bool tri_transfer(int p, int q, std::vector<double> &T);
 // p + 1 Gauss-Lobatto-Legendre points (ascending).
 void gll_nodes(int p, double *x);
 

@@ -163,6 +163,32 @@ void tri_edge_point(int edge, double sigma, double &r, double &s) {
   }
 }
 
+bool tri_transfer(int p, int q, std::vector<double> &T) {
+  TriBasis bp, bq;
+  if (!make_tri_basis(p, bp) || !make_tri_basis(q, bq)) return false;
+  const Modes Mp = modes_of(p), Mq = modes_of(q);
+  const int np = Mp.n, nq = Mq.n;
+  std::vector<ld> Vp((size_t)np * np), row(np), rowq(nq);
+  for (int k = 0; k < np; ++k) eval_modes(Mp, (ld)bp.r[k], (ld)bp.s[k], &Vp[(size_t)k * np], nullptr, nullptr);
+  if (!invert(Vp, np)) return false;          // modal coefficients from nodal values
+  T.assign((size_t)nq * np, 0.0);
+  for (int t = 0; t < nq; ++t) {
+    eval_modes(Mq, (ld)bq.r[t], (ld)bq.s[t], rowq.data(), nullptr, nullptr);
+    for (int j = 0; j < np; ++j) {
+      ld acc = 0;
+      for (int n = 0; n < np; ++n) {
+        if (Mp.i[n] + Mp.j[n] > q) continue;  // modes above the target degree are dropped
+        int nn = -1;
+        for (int k = 0; k < nq; ++k)
+          if (Mq.i[k] == Mp.i[n] && Mq.j[k] == Mp.j[n]) nn = k;
+        acc += rowq[nn] * Vp[(size_t)n * np + j];
+      }
+      T[(size_t)t * np + j] = (double)acc;
+    }
+  }
+  return true;
+}
+
 void gll_nodes(int p, double *x) {
   ld t[kMaxN + 1];
   gll_points(p, t);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "fr_set_closure": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32]),
     "fr_closure_nu": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "fr_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_project_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fr_mlp_workspace_floats": (C.c_int64, [C.c_int64]),
     "fr_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t]),
     "fr_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -300,6 +301,13 @@ class Mesh:
 
     def __exit__(self, *a):
         self.close()
+
+
+def project_state(src: "Mesh", dst: "Mesh"):
+    """fr_project_state: dst's state = the L2 projection of src's state onto dst's order."""
+    st = src._lib.fr_project_state(src._h, dst._h)
+    if st != FR_OK:
+        raise FRError(st, src._lib.fr_last_error(dst._h).decode())
 
 
 class Batch:
