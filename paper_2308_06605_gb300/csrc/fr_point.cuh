@@ -260,7 +260,10 @@ __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int 
       const int64_t o = t * 5 + v;
       if (stage < 3) {
         acc[o] = fma(bcoef[stage] * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
-        Qc[o] = Unc[o] + adt * (rv[v] * s);
+        // The stage increment in double-float; with a source term it comes from the FP64
+        // residual, which includes S.
+        const T inc = (dph.src_body || dph.src_sponge) ? from_double<T>(rd[v]) : rv[v] * s;
+        Qc[o] = Unc[o] + adt * inc;
       } else {
         const double nv = fma(bcoef[3] * dt, rd[v], Un[o] + acc[o]);
         Un[o] = nv;
