@@ -258,7 +258,8 @@ fr_status fr_set_closure(fr_mesh *mesh, const float *params, const float *scales
  *                                                S = -sigma (Q - Q_ref)
  * evaluated on the state the residual is computed from (the stage state in RK stages).  Host
  * arrays are copied; a later call replaces the previous settings.  sigma without Q_ref (or the
- * reverse), negative or non-finite values -> FR_EINVAL.
+ * reverse), negative or non-finite values -> FR_EINVAL.  A batch uses the settings its meshes had
+ * when fr_batch_create was called.
  */
 fr_status fr_set_source(fr_mesh *mesh, const double *accel, const double *sigma, const double *Q_ref);
 fr_status fr_closure_nu(fr_mesh *mesh, float *nu_host);
