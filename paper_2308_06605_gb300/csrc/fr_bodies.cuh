@@ -204,7 +204,13 @@ template <int N>
 constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
 // Resident blocks the register budget must allow (smem allows at least this many).
 template <int N>
-constexpr int volume_min_blocks() { return volume_threads<N>() <= 128 ? 3 : (volume_threads<N>() <= 256 ? 2 : 1); }
+constexpr int volume_min_blocks() {
+  // Measured on GB300: 16 warps per SM (128 registers, no spills) is fastest for the 32- and
+  // 64-thread blocks of p = 2, 3; p = 4 runs best at 3 blocks of 128 threads (168 registers);
+  // p = 1 keeps 8 blocks (16 would spill).
+  return N == 2 ? 8 : (N == 5 ? 3 : (volume_threads<N>() <= 128 ? 512 / volume_threads<N>()
+                                                                 : (volume_threads<N>() <= 256 ? 2 : 1)));
+}
 
 // Shared-memory values (of T) one element needs in the volume kernel.
 template <int N>
@@ -260,6 +266,46 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     invJ = met[9 * Np];
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v] = sQ[v * Np + m];
+    if (viscous) {
+      // One variable at a time: reference gradient, its correction, and both transformed to
+      // physical components at once (short live ranges; the same operations as a two-pass form).
+      T sj[9];   // S[d][jj] / |J|
+#pragma unroll
+      for (int c = 0; c < 9; ++c) sj[c] = S[c] * invJ;
+      const T nhm[3] = {-B.hm[i], -B.hm[j], -B.hm[k]};
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const T *sq = sQ + v * Np;
+        Dot<T> a0, a1, a2;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          a0.add(B.D[i * N + a], sq[a + N * j + N * N * k]);
+          a1.add(B.D[j * N + a], sq[i + N * a + N * N * k]);
+          a2.add(B.D[k * N + a], sq[i + N * j + N * N * a]);
+        }
+        const T gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
+        a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
+        a0.add(B.hp[i], sdQ[(1 * 5 + v) * Nf + j + N * k]);
+        a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
+        a1.add(B.hp[j], sdQ[(3 * 5 + v) * Nf + i + N * k]);
+        a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
+        a2.add(B.hp[k], sdQ[(5 * 5 + v) * Nf + i + N * j]);
+        const T gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          Dot<T> du, dc;
+          du.add(sj[0 * 3 + jj], gu0);
+          du.add(sj[1 * 3 + jj], gu1);
+          du.add(sj[2 * 3 + jj], gu2);
+          dc.add(sj[0 * 3 + jj], gc0);
+          dc.add(sj[1 * 3 + jj], gc1);
+          dc.add(sj[2 * 3 + jj], gc2);
+          G[jj * 5 + v] = dc.get();
+          // Face-gradient source: BR2 the uncorrected gradient (+ eta r_f), LDG the corrected one.
+          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();
+        }
+      }
+    }
     {
       // Inviscid flux F_j.
       const T ri = ph.one / q[0];
@@ -273,50 +319,6 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
         H[jj][3] = q[3] * u[jj];
         H[jj][1 + jj] = H[jj][1 + jj] + p;
         H[jj][4] = (q[4] + p) * u[jj];
-      }
-    }
-    if (viscous) {
-      T gu[3][5], gc[3][5];
-      const T nhm[3] = {-B.hm[i], -B.hm[j], -B.hm[k]};
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T *sq = sQ + v * Np;
-        Dot<T> a0, a1, a2;
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-          a0.add(B.D[i * N + a], sq[a + N * j + N * N * k]);
-          a1.add(B.D[j * N + a], sq[i + N * a + N * N * k]);
-          a2.add(B.D[k * N + a], sq[i + N * j + N * N * a]);
-        }
-        gu[0][v] = a0.get();
-        gu[1][v] = a1.get();
-        gu[2][v] = a2.get();
-        a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
-        a0.add(B.hp[i], sdQ[(1 * 5 + v) * Nf + j + N * k]);
-        a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
-        a1.add(B.hp[j], sdQ[(3 * 5 + v) * Nf + i + N * k]);
-        a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
-        a2.add(B.hp[k], sdQ[(5 * 5 + v) * Nf + i + N * j]);
-        gc[0][v] = a0.get();
-        gc[1][v] = a1.get();
-        gc[2][v] = a2.get();
-      }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          Dot<T> du, dc;
-          du.add(s0, gu[0][v]);
-          du.add(s1, gu[1][v]);
-          du.add(s2, gu[2][v]);
-          dc.add(s0, gc[0][v]);
-          dc.add(s1, gc[1][v]);
-          dc.add(s2, gc[2][v]);
-          G[jj * 5 + v] = dc.get();
-          // Face-gradient source: BR2 the uncorrected gradient (+ eta r_f), LDG the corrected one.
-          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();
-        }
       }
     }
   }

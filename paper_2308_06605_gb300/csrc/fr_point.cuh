@@ -248,24 +248,34 @@ __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int 
     if (bad) atomicOr(flag, 1);
     return;
   }
-  const double bcoef[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-  const double anext[3] = {0.5, 0.5, 1.0};
+  // RK44 weights b_k = (1/6, 1/3, 1/3, 1/6) and next-stage coefficients a = (1/2, 1/2, 1), picked
+  // with selects (a runtime-indexed local array would live in local memory).
+  const double bk = (stage == 0 || stage == 3) ? 1.0 / 6.0 : 1.0 / 3.0;
+  const double ak = stage < 2 ? 0.5 : 1.0;
   bool bad = false;
   if constexpr (std::is_same<T, df32>::value) {
     // Mixed path: acc and U_n are FP64; the next stage state, read only by the element
     // kernels, is formed in double-float from the df32 copy of U_n.
-    const T adt = from_double<T>(stage < 3 ? anext[stage] * dt : 0.0);
+    const T adt = from_double<T>(stage < 3 ? ak * dt : 0.0);
+    if (stage < 3 && (dph.src_body || dph.src_sponge)) {
+      // With a source term the stage increment comes from the FP64 residual, which includes S
+      // (a separate uniform branch: the conversion costs FP64 work the plain path does without).
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const int64_t o = t * 5 + v;
+        acc[o] = fma(bk * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
+        Qc[o] = Unc[o] + adt * from_double<T>(rd[v]);
+      }
+      return;
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const int64_t o = t * 5 + v;
       if (stage < 3) {
-        acc[o] = fma(bcoef[stage] * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
-        // The stage increment in double-float; with a source term it comes from the FP64
-        // residual, which includes S.
-        const T inc = (dph.src_body || dph.src_sponge) ? from_double<T>(rd[v]) : rv[v] * s;
-        Qc[o] = Unc[o] + adt * inc;
+        acc[o] = fma(bk * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
+        Qc[o] = Unc[o] + adt * (rv[v] * s);
       } else {
-        const double nv = fma(bcoef[3] * dt, rd[v], Un[o] + acc[o]);
+        const double nv = fma(bk * dt, rd[v], Un[o] + acc[o]);
         Un[o] = nv;
         Q[o] = nv;
         const T nc = from_double<T>(nv);
@@ -280,11 +290,11 @@ __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int 
       const int64_t o = t * 5 + v;
       const double un = Un[o];
       if (stage < 3) {
-        const double a_ = (stage == 0 ? 0.0 : acc[o]) + bcoef[stage] * dt * rd[v];
+        const double a_ = (stage == 0 ? 0.0 : acc[o]) + bk * dt * rd[v];
         acc[o] = a_;
-        Q[o] = un + anext[stage] * dt * rd[v];
+        Q[o] = un + ak * dt * rd[v];
       } else {
-        const double nv = un + acc[o] + bcoef[3] * dt * rd[v];
+        const double nv = un + acc[o] + bk * dt * rd[v];
         Un[o] = nv;
         Q[o] = nv;
         bad |= !isfinite(nv);
