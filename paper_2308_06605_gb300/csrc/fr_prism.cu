@@ -39,7 +39,7 @@ __global__ void k_prism_interp(const T *__restrict__ Q, const int32_t *__restric
 }
 
 template <int N, typename T>
-__global__ void __launch_bounds__(prism_threads<N>())
+__global__ void __launch_bounds__(prism_threads<N>(), prism_min_blocks<N, T>())
     k_prism_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef_p,
                    const T *__restrict__ Qtr, const T *__restrict__ tab, const int32_t *__restrict__ tri_slot,
                    T *__restrict__ Gtr, T *__restrict__ Rpart, DevPhys dph, const int8_t *__restrict__ if_up,

@@ -39,6 +39,14 @@ template <int N>
 __host__ __device__ constexpr int prism_points() { return N * (N + 1) / 2 * N; }
 template <int N>
 __host__ __device__ constexpr int prism_threads() { return ((prism_points<N>() + 31) / 32) * 32; }
+// Resident blocks the register budget must allow, per order and arithmetic (checked with ptxas):
+// up to 64 threads and for double-float at 96 threads about 170 registers per thread; FP64 at
+// 96 threads and larger blocks need more (a tighter bound spills), so only the block size binds.
+template <int N, typename T>
+__host__ __device__ constexpr int prism_min_blocks() {
+  return prism_threads<N>() <= 32 ? 12 : (prism_threads<N>() <= 64 ? 6 :
+         (prism_threads<N>() <= 96 ? (std::is_same<T, df32>::value ? 4 : 2) : 1));
+}
 // Shared-memory values (of T) of the volume kernel: Q 5, grad 15, flux 15, BR2 weights 15, quad
 // lifts 15 (per point) and the jumps of 5 faces x 5 variables x N^2 slots.
 template <int N>
@@ -151,25 +159,14 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
     invJ = met[9 * Np];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qv[v] = sQ[v * Np + m];
-    {
-      const T ri = ph.one / qv[0];
-      const T u[3] = {qv[1] * ri, qv[2] * ri, qv[3] * ri};
-      const T p = ph.gm1 * (qv[4] - ph.half * (qv[1] * u[0] + qv[2] * u[1] + qv[3] * u[2]));
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        H[jj][0] = qv[1 + jj];
-        H[jj][1] = qv[1] * u[jj];
-        H[jj][2] = qv[2] * u[jj];
-        H[jj][3] = qv[3] * u[jj];
-        H[jj][1 + jj] = H[jj][1 + jj] + p;
-        H[jj][4] = (qv[4] + p) * u[jj];
-      }
-    }
     if (viscous) {
       const T *Dr = tab + L.Dr + q * Nt, *Ds = tab + L.Ds + q * Nt, *D1 = tab + L.D1 + k * N;
       const T hmk = tab[L.hm + k], hpk = tab[L.hp + k];
       const T *LQ0 = tab + L.LQ + q * N, *LQ1 = LQ0 + Nt * N, *LQ2 = LQ1 + Nt * N;
-      T gu[3][5], gc[3][5];
+      T sj[9];   // S[d][jj] / |J|
+#pragma unroll
+      for (int c = 0; c < 9; ++c) sj[c] = S[c] * invJ;
+      // One variable at a time: reference gradient, liftings, correction, physical transform.
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const T *sq = sQ + v * Np;
@@ -182,9 +179,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         }
 #pragma unroll
         for (int c = 0; c < N; ++c) a2.add(D1[c], sq[q + Nt * c]);
-        gu[0][v] = a0.get();
-        gu[1][v] = a1.get();
-        gu[2][v] = a2.get();
+        const T gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
         // Lifted jumps: quadrilateral faces (edge e = f - 2) and the two triangles.
         Dot<T> l2, l3, l4;
 #pragma unroll
@@ -204,25 +199,22 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         a1.add(ph.one, L3);
         a2.add(-hmk, sdQ[(0 * 5 + v) * Nf + q]);
         a2.add(hpk, sdQ[(1 * 5 + v) * Nf + q]);
-        gc[0][v] = a0.get();
-        gc[1][v] = a1.get();
-        gc[2][v] = a2.get();
-      }
+        const T gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T s0 = S[0 * 3 + jj] * invJ, s1 = S[1 * 3 + jj] * invJ, s2 = S[2 * 3 + jj] * invJ;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
+        for (int jj = 0; jj < 3; ++jj) {
           Dot<T> du, dc;
-          du.add(s0, gu[0][v]);
-          du.add(s1, gu[1][v]);
-          du.add(s2, gu[2][v]);
-          dc.add(s0, gc[0][v]);
-          dc.add(s1, gc[1][v]);
-          dc.add(s2, gc[2][v]);
+          du.add(sj[0 * 3 + jj], gu0);
+          du.add(sj[1 * 3 + jj], gu1);
+          du.add(sj[2 * 3 + jj], gu2);
+          dc.add(sj[0 * 3 + jj], gc0);
+          dc.add(sj[1 * 3 + jj], gc1);
+          dc.add(sj[2 * 3 + jj], gc2);
           G[jj * 5 + v] = dc.get();
           sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();   // LDG: corrected
         }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
         const T ej = ph.eta * invJ;
         sW[(0 * 3 + jj) * Np + m] = -(ej * S[2 * 3 + jj]);
         sW[(1 * 3 + jj) * Np + m] = ej * S[2 * 3 + jj];
@@ -230,6 +222,22 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         sW[(3 * 3 + jj) * Np + m] = ej * (S[0 * 3 + jj] + S[1 * 3 + jj]);
         sW[(4 * 3 + jj) * Np + m] = -(ej * S[0 * 3 + jj]);
       }
+    }
+    {
+      const T ri = ph.one / qv[0];
+      const T u[3] = {qv[1] * ri, qv[2] * ri, qv[3] * ri};
+      const T p = ph.gm1 * (qv[4] - ph.half * (qv[1] * u[0] + qv[2] * u[1] + qv[3] * u[2]));
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        H[jj][0] = qv[1 + jj];
+        H[jj][1] = qv[1] * u[jj];
+        H[jj][2] = qv[2] * u[jj];
+        H[jj][3] = qv[3] * u[jj];
+        H[jj][1 + jj] = H[jj][1 + jj] + p;
+        H[jj][4] = (qv[4] + p) * u[jj];
+      }
+    }
+    if (viscous) {
       T Fv[3][5];
       viscous_flux<T>(qv, G, ph, visc_of(ph), Fv);
 #pragma unroll
