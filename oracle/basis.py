@@ -7,11 +7,20 @@ Gauss-Legendre point set:
     starting guesses),
   * Lagrange values l_j(x) as the literal product formula,
   * derivative values l_j'(x) by the product rule applied term by term,
-  * the DG-equivalent correction function of the section "FR Algorithm": g is the right Radau
-    polynomial g_R = (P_N + P_{N-1})/2 (g_R(1) = 1, g_R(-1) = 0, orthogonal to degree N-2),
-    g_L(x) = g_R(-x).  Its derivative comes from the Legendre derivative recurrence.
+  * the correction function of the section "FR Algorithm".  The paper takes the DG-equivalent
+    one, the right Radau polynomial g_R = (P_N + P_{N-1})/2 (g_R(1) = 1, g_R(-1) = 0, orthogonal
+    to degree N-2), g_L(x) = g_R(-x).  The energy-stable family of Vincent, Castonguay & Jameson
+    (J. Sci. Comput. 47, 2011) generalises it with one parameter c (c = 0: the Radau choice):
+    for degree p = N - 1,
+        g_L = (-1)^p / 2 [P_p - (eta P_{p-1} + P_{p+1}) / (1 + eta)],
+        eta = c (2p + 1) (a_p p!)^2 / 2,   a_p = (2p)! / (2^p (p!)^2),
+    which by P_k(-x) = (-1)^k P_k(x) is, mirrored,
+        g_R(x) = g_L(-x) = [P_p + (eta P_{p-1} + P_{p+1}) / (1 + eta)] / 2.
+    The family needs 1 + eta > 0.  Derivatives come from the Legendre derivative recurrence.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -80,25 +89,43 @@ def derivative_matrix(nodes):
     return lagrange_derivatives(nodes, nodes)
 
 
-def correction_right(N: int, x):
-    """g_R(x) = (P_N(x) + P_{N-1}(x)) / 2, the right Radau polynomial (DG-equivalent, c = 0)."""
-    PN, _ = legendre(N, x)
-    PM, _ = legendre(N - 1, x)
-    return 0.5 * (PN + PM)
+def vcjh_eta(p: int, c: float) -> float:
+    """eta_p = c (2p + 1) (a_p p!)^2 / 2 with a_p = (2p)! / (2^p (p!)^2), the leading coefficient
+    of P_p; raises if 1 + eta <= 0 (outside the family)."""
+    a_p = math.factorial(2 * p) / (2.0 ** p * math.factorial(p) ** 2)
+    eta = c * (2 * p + 1) * (a_p * math.factorial(p)) ** 2 / 2.0
+    if not np.isfinite(eta) or 1.0 + eta <= 0.0:
+        raise ValueError(f"VCJH parameter c = {c} is outside the family at p = {p} (1 + eta <= 0)")
+    return eta
 
 
-def correction_right_derivative(N: int, x):
-    """g_R'(x) = (P_N'(x) + P_{N-1}'(x)) / 2."""
-    _, dPN = legendre(N, x)
-    _, dPM = legendre(N - 1, x)
-    return 0.5 * (dPN + dPM)
+def correction_right(N: int, x, c: float = 0.0):
+    """g_R(x) = [P_p + (eta P_{p-1} + P_{p+1}) / (1 + eta)] / 2, p = N - 1; c = 0 gives the
+    right Radau polynomial (P_N + P_{N-1}) / 2 (DG-equivalent)."""
+    p = N - 1
+    eta = vcjh_eta(p, c)
+    Pp, _ = legendre(p, x)
+    Pm, _ = legendre(p - 1, x) if p >= 1 else (np.zeros_like(np.asarray(x, dtype=np.float64)), None)
+    Pq, _ = legendre(p + 1, x)
+    return 0.5 * (Pp + (eta * Pm + Pq) / (1.0 + eta))
+
+
+def correction_right_derivative(N: int, x, c: float = 0.0):
+    """g_R'(x) of `correction_right`, term by term."""
+    p = N - 1
+    eta = vcjh_eta(p, c)
+    _, dPp = legendre(p, x)
+    _, dPm = legendre(p - 1, x) if p >= 1 else (None, np.zeros_like(np.asarray(x, dtype=np.float64)))
+    _, dPq = legendre(p + 1, x)
+    return 0.5 * (dPp + (eta * dPm + dPq) / (1.0 + eta))
 
 
 class Basis1D:
     """All 1D arrays of an order-p GL element (N = p + 1 points)."""
 
-    def __init__(self, p: int):
+    def __init__(self, p: int, c: float = 0.0):
         self.p = p
+        self.c = c
         self.N = N = p + 1
         self.nodes, self.weights = gauss_legendre(N)
         self.D = derivative_matrix(self.nodes)                          # [N][N]
@@ -106,5 +133,5 @@ class Basis1D:
         self.l_plus = lagrange_values(self.nodes, [1.0])[0]             # l_j(+1)
         # Derivative of the correction attached to a face, evaluated at the solution points,
         # as a function of the outward sign s of that face: h_s(xi_i) = g_R'(s * xi_i).
-        self.h_plus = correction_right_derivative(N, self.nodes)
-        self.h_minus = correction_right_derivative(N, -self.nodes)
+        self.h_plus = correction_right_derivative(N, self.nodes, c)
+        self.h_minus = correction_right_derivative(N, -self.nodes, c)

@@ -1,7 +1,7 @@
 """1D FR for linear advection u_t + a u_x = 0 on a periodic uniform mesh (oracle; test infrastructure).
 
 It uses the same 1D building blocks as the hexahedral oracle (Gauss-Legendre points, Lagrange
-derivative matrix, boundary values, Radau correction derivative) and exists to pin them: with the
+derivative matrix, boundary values, correction derivative) and exists to pin them: with the
 correction g = right/left Radau polynomials the FR scheme reproduces nodal collocated DG (section
 "FR Algorithm" of arXiv 2308.06605, citing Huynh 2007), which the tests compare against an
 independent modal Legendre DG discretisation.
@@ -18,9 +18,10 @@ import numpy as np
 from .basis import Basis1D
 
 
-def residual_advection(u, a: float, h: float, p: int):
-    """u: [K][N] nodal values per element (K elements, periodic).  Returns du/dt [K][N]."""
-    b = Basis1D(p)
+def residual_advection(u, a: float, h: float, p: int, c: float = 0.0):
+    """u: [K][N] nodal values per element (K elements, periodic).  Returns du/dt [K][N].
+    c selects the correction function of the energy-stable family (basis.correction_right)."""
+    b = Basis1D(p, c)
     f = a * u
     uL = u @ b.l_minus                      # trace at xi = -1 of each element
     uR = u @ b.l_plus                       # trace at xi = +1

@@ -11,7 +11,10 @@ per-element operators built as Kronecker products of the 1D arrays of `basis`:
           F_perp is the interpolated transformed flux dotted with the outward reference normal,
           F^I_perp the common normal flux (Rusanov) times the area-scaled physical normal, and
           C_f the divergence of the face's correction field: along the face's normal line it
-          takes the values g_R'(s xi_i) (s = outward sign), the DG-equivalent choice.
+          takes the values g_R'(s xi_i) (s = outward sign); g is the DG-equivalent Radau
+          polynomial (the paper's choice) or, with phys.vcjh_c = c != 0, the member c of the
+          energy-stable family of Vincent, Castonguay & Jameson (basis.correction_right).  The
+          same correction fields correct the gradient (viscous part).
   Viscous part (BR2; the paper uses LDG, this build's reading takes BR2): the common solution
   Q^I = (Q- + Q+)/2 corrects the reference gradient with the same correction fields,
   grad_x Q = J^-T grad_xi Q; at each face the side gradient is the uncorrected gradient
@@ -143,7 +146,7 @@ class HexFR:
     def __init__(self, desc, phys, p: int):
         self.phys = phys
         self.p = p
-        self.b = b = Basis1D(p)
+        self.b = b = Basis1D(p, getattr(phys, "vcjh_c", 0.0))
         self.N = N = p + 1
         self.Np = N ** 3
         self.Nf = N * N

@@ -6,7 +6,9 @@ Rusanov flux, DG-equivalent correction) written with generic per-element-type op
   L_f       interpolation to the flux points of face f,
   C_f       divergence of face f's correction fields = DG lifting M^-1 E_f (exact mass matrix M,
             E_f[i][q] = integral over the reference face of phi_i times the face's nodal basis
-            function q) -- the c = 0 (DG) choice, for hexahedra equal to the Radau construction,
+            function q) -- the c = 0 (DG) choice, for hexahedra equal to the Radau construction;
+            hexahedra also take a member c != 0 of the energy-stable family (phys.vcjh_c,
+            basis.correction_right) through their 1D correction vectors, prisms only c = 0,
   N_f       outward reference normal of face f scaled by the reference face's measure per unit
             parameter area (the hypotenuse face of the prism: (1, 1, 0)).
 Then grad_xi Q^C = D Q + sum_f C_f (Q^I - Q_f) N_f, F_perp = L_f (N_f . F^), the common flux uses
@@ -37,8 +39,8 @@ class ElemType:
     pass
 
 
-def hex_type(p, curved=False):
-    b = Basis1D(p)
+def hex_type(p, curved=False, c=0.0):
+    b = Basis1D(p, c)
     N = p + 1
     I = np.eye(N)
     t = ElemType()
@@ -137,7 +139,10 @@ class MixedFR:
         hexa = np.asarray(desc.hex, dtype=np.int64)
         pri = np.zeros((0, 6), np.int64) if prism is None else np.asarray(prism, dtype=np.int64)
         # 27-node hexahedra / 18-node prisms: quadratic maps with curl-form metrics.
-        self.types = [hex_type(p, curved=hexa.ndim == 2 and hexa.shape[1] == 27),
+        c = getattr(phys, "vcjh_c", 0.0)
+        if c != 0.0 and len(pri) > 0:
+            raise ValueError("the VCJH family with c != 0 is defined here for hexahedra only")
+        self.types = [hex_type(p, curved=hexa.ndim == 2 and hexa.shape[1] == 27, c=c),
                       prism_type(p, curved=pri.ndim == 2 and pri.shape[1] == 18)]
         conn = [hexa.reshape(-1, self.types[0].nv), pri.reshape(-1, self.types[1].nv)]
         self.conn = conn
