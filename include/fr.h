@@ -117,6 +117,15 @@ typedef struct {
                            supplies the common solution, the other side the common gradient
                            (corrected gradients interpolated to the face), and the common
                            normal flux gains tau |n| (Q_0 - Q_1) (boundaries: tau |n| (Q- - Q_b)) */
+  double vcjh_c;        /* correction function (section "FR Algorithm"): 0 is the paper's
+                           DG-equivalent choice (right/left Radau polynomials); c != 0 selects the
+                           member c of the energy-stable family of Vincent, Castonguay & Jameson
+                           (2011), g_L = (-1)^p/2 [P_p - (eta P_{p-1} + P_{p+1}) / (1 + eta)],
+                           eta = c (2p+1) (a_p p!)^2 / 2, a_p = (2p)! / (2^p (p!)^2); the same
+                           correction fields correct the gradient of the viscous terms.  Needs
+                           1 + eta > 0 (FR_EINVAL otherwise); c != 0 is built for hexahedral meshes
+                           on the per-mesh path (fr_mesh_create with prisms, fr_batch_create and
+                           fr_residual_static return FR_EUNSUPPORTED) */
 } fr_physics;
 
 typedef struct {

@@ -26,6 +26,8 @@ struct fr_mesh {
   double *h_scalar = nullptr;   // pinned host scalar for dt / flags
   // Source term arrays (allocated by fr_set_source).
   double *d_sigma = nullptr, *d_qref = nullptr;
+  // 1D tables of a correction function c != 0 (device BasisT of the element arithmetic).
+  void *d_vc = nullptr;
   // Eddy-viscosity closure (allocated by fr_set_closure).
   void *d_cw = nullptr;
   float *d_cscale = nullptr;
@@ -109,6 +111,7 @@ static void release(fr_mesh *m) {
   if (m->d_cscale) cudaFree(m->d_cscale);
   if (m->d_sigma) cudaFree(m->d_sigma);
   if (m->d_qref) cudaFree(m->d_qref);
+  if (m->d_vc) cudaFree(m->d_vc);
   m->d_sigma = m->d_qref = nullptr;
   m->d_cw = nullptr;
   m->d_cscale = nullptr;
@@ -155,6 +158,10 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
     return fail(nullptr, FR_EINVAL, "LDG penalty must be non-negative");
   if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED)
     return fail(nullptr, FR_EINVAL, "unknown precision");
+  if (!vcjh_in_family(desc->p, phys->vcjh_c))
+    return fail(nullptr, FR_EINVAL, "correction parameter c outside the energy-stable family (1 + eta <= 0)");
+  if (phys->vcjh_c != 0.0 && desc->n_prism > 0)
+    return fail(nullptr, FR_EUNSUPPORTED, "correction functions with c != 0 are built for hexahedral meshes only");
   for (int k = 0; k < desc->n_bc; ++k) {
     const fr_bc &b = desc->bc[k];
     if (b.kind < FR_BC_WALL_ISOTHERMAL || b.kind > FR_BC_DIRICHLET)
@@ -176,7 +183,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   std::string err;
   fr_status st;
   try {
-    st = build_host_mesh(desc, m->host, err);
+    st = build_host_mesh(desc, m->host, err, phys->vcjh_c);
   } catch (const std::bad_alloc &) {
     st = FR_ENOMEM;
     err = "host allocation failed while building the mesh";
@@ -252,6 +259,14 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
                    (st = dalloc(m, &d.if_tri, h.if_tri.size()))))
     return bail(st);
   if ((st = dalloc(m, &d.if_up, h.if_up.size()))) return bail(st);
+  if (phys->vcjh_c != 0.0) {
+    ce = vcjh_basis_create(h.p, phys->vcjh_c, d.mixed, &m->d_vc);
+    if (ce != cudaSuccess) {
+      m->err = std::string("correction tables: ") + cudaGetErrorString(ce);
+      return bail(ce == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA);
+    }
+    dp.vc_basis = m->d_vc;
+  }
   if (d.mixed) {
     // Geometry in the element arithmetic's format: each double becomes a df32 (hi, lo) pair
     // stored in the same 8-byte slot.

@@ -51,41 +51,54 @@ template <typename T> __device__ __forceinline__ const BasisT<T> &cbasis(int N);
 template <> __device__ __forceinline__ const BasisT<double> &cbasis<double>(int N) { return c_basis_d[N - 1]; }
 template <> __device__ __forceinline__ const BasisT<df32> &cbasis<df32>(int N) { return c_basis_f[N - 1]; }
 
-// Upload of this translation unit's copy of the 1D basis tables (constant memory is per unit).
+// 1D tables of one order in both element arithmetics.
+inline void fill_basis(const Basis1D &b, BasisT<double> &d, BasisT<df32> &f) {
+  const int N = b.N;
+  d = BasisT<double>{};
+  f = BasisT<df32>{};
+  for (int i = 0; i < N; ++i) {
+    d.lm[i] = b.lm[i];
+    d.lp[i] = b.lp[i];
+    d.hm[i] = b.hm[i];
+    d.hp[i] = b.hp[i];
+    d.w[i] = b.w[i];
+    for (int a = 0; a < N; ++a) {
+      d.D[i * N + a] = b.D[i * N + a];
+      d.Dt[i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
+    }
+  }
+  for (int i = 0; i < kMaxN; ++i) {
+    f.lm[i] = df_split_host(d.lm[i]);
+    f.lp[i] = df_split_host(d.lp[i]);
+    f.hm[i] = df_split_host(d.hm[i]);
+    f.hp[i] = df_split_host(d.hp[i]);
+    f.w[i] = d.w[i];
+  }
+  for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    f.D[i] = df_split_host(d.D[i]);
+    f.Dt[i] = df_split_host(d.Dt[i]);
+  }
+}
+
+// Upload of this translation unit's copy of the 1D basis tables (constant memory is per unit);
+// DG-equivalent correction.
 cudaError_t upload_basis_local() {
   BasisT<double> hd[kMaxN] = {};
   BasisT<df32> hf[kMaxN] = {};
-  for (int p = 1; p < kMaxN; ++p) {
-    Basis1D b = make_basis(p);
-    const int N = p + 1;
-    BasisT<double> &d = hd[N - 1];
-    for (int i = 0; i < N; ++i) {
-      d.lm[i] = b.lm[i];
-      d.lp[i] = b.lp[i];
-      d.hm[i] = b.hm[i];
-      d.hp[i] = b.hp[i];
-      d.w[i] = b.w[i];
-      for (int a = 0; a < N; ++a) {
-        d.D[i * N + a] = b.D[i * N + a];
-        d.Dt[i * N + a] = b.D[i * N + a] - b.hp[i] * b.lp[a] + b.hm[i] * b.lm[a];
-      }
-    }
-    BasisT<df32> &f = hf[N - 1];
-    for (int i = 0; i < kMaxN; ++i) {
-      f.lm[i] = df_split_host(d.lm[i]);
-      f.lp[i] = df_split_host(d.lp[i]);
-      f.hm[i] = df_split_host(d.hm[i]);
-      f.hp[i] = df_split_host(d.hp[i]);
-      f.w[i] = d.w[i];
-    }
-    for (int i = 0; i < kMaxN * kMaxN; ++i) {
-      f.D[i] = df_split_host(d.D[i]);
-      f.Dt[i] = df_split_host(d.Dt[i]);
-    }
-  }
+  for (int p = 1; p < kMaxN; ++p) fill_basis(make_basis(p), hd[p], hf[p]);
   cudaError_t e = cudaMemcpyToSymbol(c_basis_d, hd, sizeof(hd));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_basis_f, hf, sizeof(hf));
+}
+
+// Tables of the kernels: the constant-memory DG-equivalent ones, or (VC) the mesh's own copy in
+// global memory for a correction function c != 0 of the energy-stable family.
+template <int N, typename T, bool VC>
+__device__ __forceinline__ const BasisT<T> &basis_ref(const DevPhys &dph) {
+  if constexpr (VC)
+    return *reinterpret_cast<const BasisT<T> *>(dph.vc_basis);
+  else
+    return cbasis<T>(N);
 }
 
 // Strides of the reference axes in the point index m = i + N j + N^2 k.
@@ -219,7 +232,7 @@ __host__ __device__ constexpr int volume_smem_values() { return 35 * N * N * N +
 // One element e handled by `nth` threads of the block (thread index tid in [0, nth)); every
 // thread of the block calls this together (it contains block barriers); inactive sub-blocks
 // (active = false) only take part in the barriers.
-template <int N, typename T>
+template <int N, typename T, bool VC = false>
 __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool active, double *sm_raw,
                                             const T *__restrict__ Q, const T *__restrict__ metrics,
                                             const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
@@ -234,7 +247,7 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
   T *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
   const PhysT<T> &ph = phys_of<T>(dph);
-  const BasisT<T> &B = cbasis<T>(N);
+  const BasisT<T> &B = basis_ref<N, T, VC>(dph);
   const bool viscous = dph.viscous != 0;
   if (active)
     for (int t = tid; t < 5 * Np; t += nth) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
@@ -685,7 +698,7 @@ __global__ void k_bc_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr, 
 // ------------------------------------------------------------------------------------------
 // 4. Correction by the common flux, scaling, and output / RK44 stage update (FP64).
 // ------------------------------------------------------------------------------------------
-template <int N, typename T>
+template <int N, typename T, bool VC = false>
 __device__ __forceinline__ void correct_body(int64_t t, const T *__restrict__ Rpart, const T *__restrict__ FI,
                                              const int32_t *__restrict__ ef, const T *__restrict__ metrics,
                                              int64_t E, int mode, int stage, double dt, double *__restrict__ Rout,
@@ -696,7 +709,7 @@ __device__ __forceinline__ void correct_body(int64_t t, const T *__restrict__ Rp
   if (t >= E * Np) return;
   const int64_t e = t / Np;
   const int m = (int)(t % Np), i = m % N, j = (m / N) % N, k = m / (N * N);
-  const BasisT<T> &B = cbasis<T>(N);
+  const BasisT<T> &B = basis_ref<N, T, VC>(dph);
   const PhysT<T> &ph = phys_of<T>(dph);
   Dot<T> r[5];
 #pragma unroll

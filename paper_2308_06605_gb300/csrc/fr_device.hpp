@@ -36,6 +36,9 @@ struct DevPhys {
   double accel[3];
   const double *sigma;     // [n_points] device
   const double *Q_ref;     // [n_points][5] device
+  // Correction function c != 0 of the energy-stable family: the mesh's 1D tables (a BasisT of
+  // the element arithmetic, device); null for the DG-equivalent tables in constant memory.
+  const void *vc_basis;
 };
 
 // Device buffers of one mesh (all owned by the mesh).
@@ -160,6 +163,11 @@ fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg);
 cudaError_t launch_prism_phase(const DevMesh &m, const DevPhys &ph, int phase, int mode, int stage, double dt,
                                double *Rout, cudaStream_t st);
 // Per-prism time-step bound into m.dtbuf[E + ep] (same formula as the hexahedra).
+// Hexahedral volume (phase 1) and correction (phase 3) kernels reading the mesh's own 1D tables
+// (correction function c != 0); vcjh_basis_create builds and uploads those tables.
+cudaError_t launch_vcjh_phase(const DevMesh &m, const DevPhys &ph, int phase, int mode, int stage, double dt,
+                              double *Rout, cudaStream_t st);
+cudaError_t vcjh_basis_create(int p, double c, int mixed, void **out);
 cudaError_t launch_prism_dt(const DevMesh &m, const DevPhys &ph, double cfl, cudaStream_t st);
 
 // Mixed path: refresh the df32 copy of the state after it was set from outside.

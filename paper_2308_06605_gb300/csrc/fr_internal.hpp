@@ -26,7 +26,10 @@ struct Basis1D {
   double lm[kMaxN], lp[kMaxN];   // l_a(-1), l_a(+1)
   double hm[kMaxN], hp[kMaxN];   // correction divergence on the normal line of the -/+ face
 };
-Basis1D make_basis(int p);
+// Order-p Gauss-Legendre basis; c selects the correction function of the energy-stable family
+// (0: DG-equivalent Radau).  The caller checks vcjh_in_family(p, c) first.
+Basis1D make_basis(int p, double c = 0.0);
+bool vcjh_in_family(int p, double c);
 
 // Nodal triangle basis of order p (prism elements): warp-and-blend nodes, operators from the
 // orthonormal Proriol-Koornwinder-Dubiner modes, all computed in long double.
@@ -127,7 +130,7 @@ struct HostMesh {
   std::vector<int32_t> tri_slot;  // [6][Nt] side-0 slot of a side-1 node for each code
 };
 
-fr_status build_host_mesh(const fr_mesh_desc *d, HostMesh &m, std::string &err);
+fr_status build_host_mesh(const fr_mesh_desc *d, HostMesh &m, std::string &err, double vcjh_c = 0.0);
 
 // Slot (side-0 ordering) of the local face point (a, b) for an orientation code.
 FRX_HD inline int orient_slot(int code, int a, int b, int N) {

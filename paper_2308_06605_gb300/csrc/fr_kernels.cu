@@ -86,9 +86,12 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
-    if (E > 0)
+    if (E > 0 && ph.vc_basis) {
+      if ((err = launch_vcjh_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
+    } else if (E > 0) {
       k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu, m.if_up,
                                                          m.n_interior);
+    }
     if ((err = launch_prism_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(1);
   }
@@ -114,7 +117,9 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   {
     const int64_t n = E * Np;
     FR_EV_BEGIN(3);
-    if (n > 0)
+    if (n > 0 && ph.vc_basis) {
+      if ((err = launch_vcjh_phase(m, ph, 3, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
+    } else if (n > 0)
       k_correct<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Rpart, FI, m.ef, met, E, mode, stage, dt, Rout,
                                                                    m.Q, Qc, m.Un, reinterpret_cast<T *>(m.Unc),
                                                                    m.acc, m.flag, ph);

@@ -70,7 +70,16 @@ static void legendre_pd(int n, ld x, ld &P, ld &dP) {
   dP = n * (p0 - x * p1) / (1.0L - x * x);   // valid inside (-1, 1)
 }
 
-Basis1D make_basis(int p) {
+// eta_p = c (2p + 1) (a_p p!)^2 / 2 of the energy-stable family, a_p p! = (2p)! / (2^p p!) the
+// leading coefficient of P_p times p!.
+static ld vcjh_eta(int p, double c) {
+  ld apf = 1.0L;
+  for (int k = p + 1; k <= 2 * p; ++k) apf *= (ld)k;   // (2p)! / p!
+  for (int k = 0; k < p; ++k) apf *= 0.5L;
+  return (ld)c * (2 * p + 1) * apf * apf / 2;
+}
+
+Basis1D make_basis(int p, double c) {
   Basis1D b;
   const int N = p + 1;
   b.p = p;
@@ -143,7 +152,26 @@ Basis1D make_basis(int p) {
     b.hp[i] = (double)(lpv / w[i]);
     b.hm[i] = (double)(lmv / w[i]);
   }
+  // Energy-stable family (Vincent, Castonguay & Jameson 2011): relative to the Radau member the
+  // right correction changes by eta/(2(1+eta)) (P_{p-1} - P_{p+1}), whose derivative is
+  // -kappa P_p with kappa = (2p+1) eta / (2 (1 + eta)) (Legendre: P'_{p+1} - P'_{p-1} = (2p+1) P_p).
+  // hp = g_R'(x_i) and hm = g_R'(-x_i) = -g_L'(x_i), P_p(-x) = (-1)^p P_p(x).
+  if (c != 0.0) {
+    const ld eta = vcjh_eta(p, c), kap = (2 * p + 1) * eta / (2 * (1 + eta));
+    for (int i = 0; i < N; ++i) {
+      ld P, dP;
+      legendre_pd(p, x[i], P, dP);
+      b.hp[i] = (double)((ld)b.hp[i] - kap * P);
+      b.hm[i] = (double)((ld)b.hm[i] - kap * ((p % 2) ? -P : P));
+    }
+  }
   return b;
+}
+
+bool vcjh_in_family(int p, double c) {
+  if (!std::isfinite(c)) return false;
+  const ld eta = vcjh_eta(p, c);
+  return std::isfinite((double)eta) && 1 + eta > 0;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -320,7 +348,7 @@ static void parallel_for(int64_t n, F body) {
   for (std::thread &x : th) x.join();
 }
 
-fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &err) {
+fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &err, double vcjh_c) {
   char buf[256];
   const int p = desc->p;
   const int N = p + 1, Np = N * N * N, Nf = N * N;
@@ -597,7 +625,7 @@ fr_status build_host_mesh(const fr_mesh_desc *desc, HostMesh &m, std::string &er
   // Geometry at solution and flux points, element by element on host threads (every element
   // writes only its own metrics, points and lift factors, and the normals of the interfaces whose
   // side 0 it is).
-  Basis1D b = make_basis(p);
+  Basis1D b = make_basis(p, vcjh_c);   // correction vectors enter the BR2 lift factors
   m.metrics.assign((size_t)E * 10 * Np, 0.0);
   m.liftfac.assign((size_t)E * 6 * 3 * Nf, 0.0);
   m.normals.assign((size_t)m.n_if * 4 * Nf, 0.0);

@@ -48,6 +48,8 @@ extern "C" fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, d
   if (!Q_device || !R_device) return frx_mesh_fail(mesh, FR_EINVAL, "fr_residual_static: NULL state or residual");
   if (dev.mixed) return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: FP64 meshes only");
   if (dev.Ep > 0) return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: hexahedral meshes only");
+  if (phys.vc_basis)
+    return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: DG-equivalent correction (c = 0) only");
   const size_t Nf = (size_t)dev.Nf;
   const size_t n_qtr = (size_t)dev.n_if * 2 * 5 * Nf;
   const size_t n_gtr = (size_t)dev.n_if * 2 * 15 * Nf;

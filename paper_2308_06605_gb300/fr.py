@@ -54,7 +54,7 @@ class fr_mesh_desc(C.Structure):
 class fr_physics(C.Structure):
     _fields_ = [("gamma", C.c_double), ("R", C.c_double), ("mu", C.c_double), ("Pr", C.c_double),
                 ("inviscid", C.c_int32), ("viscous", C.c_int32), ("br2_eta", C.c_double),
-                ("precision", C.c_int32), ("ldg_tau", C.c_double)]
+                ("precision", C.c_int32), ("ldg_tau", C.c_double), ("vcjh_c", C.c_double)]
 
 
 class fr_batch_info(C.Structure):
@@ -186,7 +186,7 @@ class Mesh:
                          hex_nodes=hexa.shape[1], prism_nodes=pri.shape[1])
         ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
                         viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision,
-                        ldg_tau=getattr(phys, "ldg_tau", 0.1))
+                        ldg_tau=getattr(phys, "ldg_tau", 0.1), vcjh_c=getattr(phys, "vcjh_c", 0.0))
         h = C.c_void_p()
         st = lib.fr_mesh_create(C.byref(d), C.byref(ph), stream, C.byref(h))
         if st != FR_OK:

@@ -54,3 +54,23 @@ def assert_state_parity(got, want, scale, elapsed, rel=1e-12):
     err = (np.abs(np.asarray(got) - want) / den).reshape(-1, 5).max(axis=0)
     assert np.all(err <= rel), f"state error {err} > {rel}"
     return err
+
+
+def vcjh_c(p, which):
+    """Members of the energy-stable correction family (Vincent, Castonguay & Jameson 2011) at
+    degree p: dg (c = 0), sd (c_SD = 2p / ((2p+1)(p+1)(a_p p!)^2)), hu (c_HU = 2(p+1) /
+    ((2p+1) p (a_p p!)^2)), neg (half the lower limit c_- = -2 / ((2p+1)(a_p p!)^2)), big (10 c_HU);
+    a_p p! = (2p)! / (2^p p!)."""
+    import math
+    apf = math.factorial(2 * p) / (2.0 ** p * math.factorial(p))
+    if which == "dg":
+        return 0.0
+    if which == "sd":
+        return 2.0 * p / ((2 * p + 1) * (p + 1) * apf ** 2)
+    if which == "hu":
+        return 2.0 * (p + 1) / ((2 * p + 1) * p * apf ** 2)
+    if which == "neg":
+        return -1.0 / ((2 * p + 1) * apf ** 2)
+    if which == "big":
+        return 10.0 * vcjh_c(p, "hu")
+    raise ValueError(which)

@@ -25,6 +25,8 @@ from oracle.hexfr import HexFR
 from oracle.mixedfr import MixedFR
 from paper_2308_06605_gb300 import inputs as I
 
+from helpers import vcjh_c
+
 G = 1.4
 
 
@@ -33,18 +35,7 @@ def _apf(p):
     return math.factorial(2 * p) / (2.0 ** p * math.factorial(p))
 
 
-def c_named(p, which):
-    if which == "dg":
-        return 0.0
-    if which == "sd":
-        return 2.0 * p / ((2 * p + 1) * (p + 1) * _apf(p) ** 2)
-    if which == "hu":
-        return 2.0 * (p + 1) / ((2 * p + 1) * p * _apf(p) ** 2)
-    if which == "neg":       # half of the family's lower limit c_- = -2 / ((2p+1) (a_p p!)^2)
-        return -1.0 / ((2 * p + 1) * _apf(p) ** 2)
-    if which == "big":
-        return 10.0 * c_named(p, "hu")
-    raise ValueError(which)
+c_named = vcjh_c
 
 
 MEMBERS = ["dg", "sd", "hu", "neg", "big"]
