@@ -142,7 +142,7 @@ DF_FP32_FLOPS_PER_FLOP = 18.0
 class Case:
     """One mesh + state on the device, stepping with RK44 on the torch current stream."""
 
-    def __init__(self, n_edge, p, precision, dt=None, prisms=None):
+    def __init__(self, n_edge, p, precision, dt=None, prisms=None, vcjh_c=0.0):
         import numpy as np
         import torch
         from paper_2308_06605_gb300 import fr, inputs as I
@@ -150,6 +150,7 @@ class Case:
         self.stream = torch.cuda.current_stream()
         phys = I.tgv_physics()
         phys.precision = 1 if precision == "mixed" else 0
+        phys.vcjh_c = vcjh_c
         self.mesh = fr.Mesh(I.hex_box_mesh((n_edge, n_edge, n_edge), prisms=prisms), phys, p,
                             stream=self.stream.cuda_stream)
         x = self.mesh.solution_points()
@@ -285,6 +286,25 @@ def run_prisms(steps, fp64_peak, df_peak, cases=None):
             c.close()
         out[f"{split}_{n}cube_p{p}"] = row
     return out
+
+
+def run_vcjh(steps, n=48, p=4):
+    """Correction function c_HU (energy-stable family, Huynh's g2) against the DG-equivalent c = 0
+    on the TGV box, both precisions: updates/s of RK44 steps."""
+    import math
+    apf = math.factorial(2 * p) / (2.0 ** p * math.factorial(p))
+    c_hu = 2.0 * (p + 1) / ((2 * p + 1) * p * apf ** 2)
+    row = {"n_edge": n, "p": p, "c": c_hu, "n_points": n ** 3 * (p + 1) ** 3}
+    for prec in ("fp64", "mixed"):
+        dt = None
+        for tag, c in (("c0", 0.0), ("c_hu", c_hu)):
+            cs = Case(n, p, prec, dt=dt, vcjh_c=c)
+            dt = cs.dt
+            cs.step()
+            ms = cs.timed(max(2, steps))
+            row[f"{prec}_{tag}"] = cs.n_pts * 4 * max(2, steps) / (ms * 1e-3)
+            cs.close()
+    return row
 
 
 def run_cascade(steps, fp64_peak, df_peak, nz=40, p=7):
@@ -455,6 +475,8 @@ def run_ours(args):
         cases = [(args.prism_edge, args.prism_order, "all")] if args.prism_edge else None
         prisms = run_prisms(args.steps, fp64_peak, df_peak, cases)
 
+    vcjh = run_vcjh(args.steps) if not args.no_vcjh else {}
+
     ensemble = {}
     if not args.no_ensemble:
         es = torch.cuda.Stream()
@@ -482,7 +504,7 @@ def run_ours(args):
             "config": config("mixed"), "clocks": clocks, "e2e": e2e,
             "gpu_launches": 4 * 4 * args.steps, "roofline": roofline, "kernels": k_mx,
             "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
-            "ensemble_64_vortex": ensemble, "prisms_tgv": prisms,
+            "ensemble_64_vortex": ensemble, "prisms_tgv": prisms, "vcjh_hu_48cube_p4": vcjh,
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}
     if args.cascade:
         line["cascade_p7"] = run_cascade(args.steps, fp64_peak, df_peak)
@@ -512,6 +534,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the p = 3..7 sweep")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-case batched vortex ensemble")
     ap.add_argument("--no-prisms", action="store_true", help="skip the prismatic / mixed-mesh measurements")
+    ap.add_argument("--no-vcjh", action="store_true", help="skip the c != 0 correction-function measurement")
     ap.add_argument("--prism-edge", type=int, default=0, help="only an all-prism box of this edge (profiling)")
     ap.add_argument("--prism-order", type=int, default=4)
     ap.add_argument("--cascade", action="store_true",
