@@ -112,6 +112,31 @@ def oracle_rate(budget_s=12.0, max_steps=None, n=8, p=ORDER):
     return rate, f"oracle RK44 on {n}^3 hex p={p} TGV ({m.E * m.Np} points), {steps} steps in {el:.1f} s", 1
 
 
+def _oracle_worker(budget_s):
+    return oracle_rate(budget_s=budget_s)[:2]
+
+
+def oracle_rate_procs(budget_s=12.0, procs=1):
+    """The oracle as it stands in `procs` spawned processes at once, one independent replica of
+    the same workload each, BLAS and OpenMP threads pinned to 1 so a replica uses one core.
+    Returns (aggregate updates/s, sample of one replica, processes)."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [budget_s] * procs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sum(r for r, _ in res), res[0][1], procs
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -509,8 +534,12 @@ def run_ours(args):
     if args.cascade:
         line["cascade_p7"] = run_cascade(args.steps, fp64_peak, df_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample, cores = oracle_rate(budget_s=12.0)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        r1, sample1, _ = oracle_rate_procs(12.0, 1)
+        ncpu = os.cpu_count() or 1
+        rn, sample, cores = oracle_rate_procs(12.0, ncpu)
+        line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{cores} replicas at once, one per host core, each: {sample}",
+                                "single_thread": {"value": r1, "unit": UNIT, "cores": 1, "sample": sample1}}
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:

@@ -210,6 +210,55 @@ __global__ void k_interp_faces(const T *__restrict__ Q, const int32_t *__restric
   interp_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Q, ef, Qtr, E);
 }
 
+// The same interpolation with the elements' states staged through shared memory: a block of
+// kInterpThreads threads loads interp_epb<N>() consecutive elements with coalesced reads (the
+// point-major [pt][v] layout of consecutive elements is one contiguous range), then computes
+// their face traces from shared memory.
+constexpr int kInterpThreads = 256;
+template <int N>
+__host__ __device__ constexpr int interp_epb() {
+  return (2 * kInterpThreads) / (6 * N * N) < 1 ? 1
+         : ((2 * kInterpThreads) / (6 * N * N) > 16 ? 16 : (2 * kInterpThreads) / (6 * N * N));
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(kInterpThreads)
+    k_interp_faces_smem(const T *__restrict__ Q, const int32_t *__restrict__ ef, T *__restrict__ Qtr, int64_t E) {
+  constexpr int Np = N * N * N, Nf = N * N, EPB = interp_epb<N>();
+  __shared__ T sq[EPB * 5 * Np];     // [element][v][point]
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int ne = (int)(E - e0 < EPB ? E - e0 : EPB);
+  const T *src = Q + e0 * Np * 5;
+  for (int idx = threadIdx.x; idx < ne * Np * 5; idx += kInterpThreads) {
+    const int le = idx / (Np * 5), rem = idx - le * Np * 5;
+    sq[(le * 5 + rem % 5) * Np + rem / 5] = src[idx];
+  }
+  __syncthreads();
+  const BasisT<T> &B = cbasis<T>(N);
+  for (int t = threadIdx.x; t < ne * 6 * Nf; t += kInterpThreads) {
+    const int le = t / (6 * Nf), fr_ = t - le * 6 * Nf;
+    const int f = fr_ / Nf, r = fr_ % Nf;
+    const T *l = (f & 1) ? B.lp : B.lm;
+    int base, sd;
+    face_line<N>(f, r, base, sd);
+    const T *q = sq + le * 5 * Np + base;
+    Dot<T> acc[5];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const T lc = l[c];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v].add(lc, q[v * Np + c * sd]);
+    }
+    const int packed = ef[(e0 + le) * 6 + f];
+    const int64_t I = packed >> 4;
+    const int side = (packed >> 3) & 1;
+    const int slot = slot_of(packed & 7, r % N, r / N, N);
+    T *dst = Qtr + (I * 2 + side) * 5 * Nf + slot;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dst[v * Nf] = acc[v].get();
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // 2. Volume kernel.  One block per element, one thread per solution point.
 // ------------------------------------------------------------------------------------------
@@ -408,8 +457,10 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   __syncthreads();
   if (viscous && active) {
     // Gradient traces: uncorrected gradient interpolated to the face + eta * own lifting.
-    for (int t = tid; t < 6 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
+    // One item per (gradient component jj, face point): 3 * 6 * Nf items keep the block busy.
+    for (int t = tid; t < 18 * Nf; t += nth) {
+      const int jj = t / (6 * Nf), fr_ = t - jj * 6 * Nf;
+      const int f = fr_ / Nf, r = fr_ % Nf;
       const T *l = (f & 1) ? B.lp : B.lm;
       int base, sd;
       face_line<N>(f, r, base, sd);
@@ -418,26 +469,22 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
       const int side = (packed >> 3) & 1;
       const int slot = slot_of(packed & 7, r % N, r / N, N);
       T *dst = Gtr + (I * 2 + side) * 15 * Nf + slot;
-      const T *lf = liftfac + (e * 6 + f) * 3 * Nf + r;
+      const T lj = ph.eta * liftfac[((e * 6 + f) * 3 + jj) * Nf + r];
+#pragma unroll 1
+      for (int v = 0; v < 5; ++v) {
+        const T *sg = sG + (jj * 5 + v) * Np + base;
+        Dot<T> acc;
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const T lj = ph.eta * lf[jj * Nf];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const T *sg = sG + (jj * 5 + v) * Np + base;
-          Dot<T> acc;
-#pragma unroll
-          for (int c = 0; c < N; ++c) acc.add(l[c], sg[c * sd]);
-          acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
-          dst[(jj * 5 + v) * Nf] = acc.get();
-        }
+        for (int c = 0; c < N; ++c) acc.add(l[c], sg[c * sd]);
+        acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
+        dst[(jj * 5 + v) * Nf] = acc.get();
       }
     }
   }
   if (active && tid < Np) {
     const int m = tid, i = m % N, j = (m / N) % N, k = m / (N * N);
     T *out = Rpart + (e * Np + m) * 5;
-#pragma unroll
+#pragma unroll 1
     for (int v = 0; v < 5; ++v) {
       const T *h0 = sH + (0 * 5 + v) * Np, *h1 = sH + (1 * 5 + v) * Np, *h2 = sH + (2 * 5 + v) * Np;
       Dot<T> acc;

@@ -69,7 +69,15 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   {
     const int64_t n = E * 6 * Nf;
     FR_EV_BEGIN(0);
-    if (n > 0) k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
+    // Double-float: staged through shared memory (measured 35 % faster at 48^3, p = 4); FP64: one
+    // thread per face point reading the state directly (the staged form was 7 % slower there).
+    if constexpr (std::is_same<T, df32>::value) {
+      constexpr int epb = interp_epb<N>();
+      if (n > 0)
+        k_interp_faces_smem<N, T><<<(unsigned)((E + epb - 1) / epb), kInterpThreads, 0, st>>>(Qin, m.ef, Qtr, E);
+    } else if (n > 0) {
+      k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
+    }
     if ((err = launch_prism_phase(m, ph, 0, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     const int64_t nb = (m.n_if - m.n_interior) * Nf;
     if (nb > 0 && !tri)

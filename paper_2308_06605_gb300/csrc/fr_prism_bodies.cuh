@@ -258,9 +258,11 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
   }
   __syncthreads();
   if (viscous && active) {
-    // Gradient traces: interpolated uncorrected gradient + eta * own lifting, per face point.
-    for (int t = tid; t < 5 * Nf; t += nth) {
-      const int f = t / Nf, r = t % Nf;
+    // Gradient traces: interpolated uncorrected gradient + eta * own lifting.  One item per
+    // (gradient component jj, face point) keeps the block busy.
+    for (int t = tid; t < 15 * Nf; t += nth) {
+      const int jj = t / (5 * Nf), fr_ = t - jj * 5 * Nf;
+      const int f = fr_ / Nf, r = fr_ % Nf;
       if (f < 2 && r >= Nt) continue;
       const int packed = ef_p[e * 5 + f];
       const int64_t I = packed >> 4;
@@ -268,38 +270,32 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
       T *dst = Gtr + (I * 2 + side) * 15 * Nf + prism_slot<N>(f, r, packed & 7, tri_slot);
       if (f < 2) {
         const T *l = tab + (f ? L.lp : L.lm), *hh = tab + (f ? L.hp : L.hm);
+        Dot<T> lf;
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          Dot<T> lf;
+        for (int c = 0; c < N; ++c) lf.add(l[c] * hh[c], sW[(f * 3 + jj) * Np + r + Nt * c]);
+        const T lfac = lf.get();
+#pragma unroll 1
+        for (int v = 0; v < 5; ++v) {
+          Dot<T> acc;
 #pragma unroll
-          for (int c = 0; c < N; ++c) lf.add(l[c] * hh[c], sW[(f * 3 + jj) * Np + r + Nt * c]);
-          const T lfac = lf.get();
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            Dot<T> acc;
-#pragma unroll
-            for (int c = 0; c < N; ++c) acc.add(l[c], sG[(jj * 5 + v) * Np + r + Nt * c]);
-            acc.add(lfac, sdQ[(f * 5 + v) * Nf + r]);
-            dst[(jj * 5 + v) * Nf] = acc.get();
-          }
+          for (int c = 0; c < N; ++c) acc.add(l[c], sG[(jj * 5 + v) * Np + r + Nt * c]);
+          acc.add(lfac, sdQ[(f * 5 + v) * Nf + r]);
+          dst[(jj * 5 + v) * Nf] = acc.get();
         }
       } else {
         const int a = r % N, b = r / N;
         const T *Ea = tab + L.E + (f - 2) * N * Nt + a * Nt;
         const T *lq = sL + ((f - 2) * 5) * Np + Nt * b;
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const T *w = sW + (f * 3 + jj) * Np + Nt * b;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const T *g = sG + (jj * 5 + v) * Np + Nt * b;
-            Dot<T> acc;
-            for (int j = 0; j < Nt; ++j) {
-              acc.add(Ea[j], g[j]);
-              acc.add(Ea[j] * w[j], lq[v * Np + j]);
-            }
-            dst[(jj * 5 + v) * Nf] = acc.get();
+        const T *w = sW + (f * 3 + jj) * Np + Nt * b;
+#pragma unroll 1
+        for (int v = 0; v < 5; ++v) {
+          const T *g = sG + (jj * 5 + v) * Np + Nt * b;
+          Dot<T> acc;
+          for (int j = 0; j < Nt; ++j) {
+            acc.add(Ea[j], g[j]);
+            acc.add(Ea[j] * w[j], lq[v * Np + j]);
           }
+          dst[(jj * 5 + v) * Nf] = acc.get();
         }
       }
     }
