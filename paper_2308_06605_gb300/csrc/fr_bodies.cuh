@@ -267,10 +267,11 @@ constexpr int volume_threads() { return ((N * N * N + 31) / 32) * 32; }
 // Resident blocks the register budget must allow (smem allows at least this many).
 template <int N>
 constexpr int volume_min_blocks() {
-  // Measured on GB300: 16 warps per SM (128 registers, no spills) is fastest for the 32- and
-  // 64-thread blocks of p = 2, 3; p = 4 runs best at 3 blocks of 128 threads (168 registers);
-  // p = 1 keeps 8 blocks (16 would spill).
-  return N == 2 ? 8 : (N == 5 ? 3 : (volume_threads<N>() <= 128 ? 512 / volume_threads<N>()
+  // Measured on GB300: 16 warps per SM (128 registers) is fastest for the 32- and 64-thread
+  // blocks of p = 2, 3 and, with the per-variable gradient and the contravariant fluxes, for the
+  // 128-thread blocks of p = 4 (4 blocks, no spills in double-float; 3 blocks of 168 registers
+  // were 3 % slower); p = 1 keeps 8 blocks (16 would spill).
+  return N == 2 ? 8 : (N == 5 ? 4 : (volume_threads<N>() <= 128 ? 512 / volume_threads<N>()
                                                                  : (volume_threads<N>() <= 256 ? 2 : 1)));
 }
 
@@ -320,7 +321,7 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   __syncthreads();
   const bool pt = active && tid < Np;
   const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
-  T S[9], invJ, q[5], H[3][5], G[15];
+  T S[9], invJ, q[5], G[15];
   if (pt) {
     const T *met = metrics + e * 10 * Np + m;
 #pragma unroll
@@ -366,21 +367,6 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
           // Face-gradient source: BR2 the uncorrected gradient (+ eta r_f), LDG the corrected one.
           sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();
         }
-      }
-    }
-    {
-      // Inviscid flux F_j.
-      const T ri = ph.one / q[0];
-      const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
-      const T p = ph.gm1 * (q[4] - ph.half * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        H[jj][0] = q[1 + jj];
-        H[jj][1] = q[1] * u[jj];
-        H[jj][2] = q[2] * u[jj];
-        H[jj][3] = q[3] * u[jj];
-        H[jj][1 + jj] = H[jj][1 + jj] + p;
-        H[jj][4] = (q[4] + p) * u[jj];
       }
     }
   }
@@ -435,24 +421,19 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     if (pt) rho_nu = q[0] * from_double<T>((double)red[10 * Np]);
   }
   if (pt) {
-    if (viscous) {
-      T Fv[3][5];
-      viscous_flux<T>(q, G, ph, visc_with(ph, rho_nu, dph), Fv);
+    // Transformed fluxes per reference direction from the contravariant velocity.
+    const T ri = ph.one / q[0];
+    const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+    const T p = ph.gm1 * (q[4] - ph.half * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+    T tau[3][3], hq[3];
+    if (viscous) viscous_stress<T>(q, u, ri, G, ph, visc_with(ph, rho_nu, dph), tau, hq);
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj)
+    for (int d = 0; d < 3; ++d) {
+      T f[5];
+      contravariant_flux<T>(q, u, p, S + 3 * d, viscous, tau, hq, f);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) H[jj][v] -= Fv[jj][v];
+      for (int v = 0; v < 5; ++v) sH[(d * 5 + v) * Np + m] = f[v];
     }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Dot<T> h;
-        h.add(S[d * 3 + 0], H[0][v]);
-        h.add(S[d * 3 + 1], H[1][v]);
-        h.add(S[d * 3 + 2], H[2][v]);
-        sH[(d * 5 + v) * Np + m] = h.get();
-      }
   }
   __syncthreads();
   if (viscous && active) {

@@ -174,6 +174,56 @@ __device__ __forceinline__ void viscous_flux(const T q[5], const T *G, const Phy
   }
 }
 
+// Viscous stress tau[i][j] = mu (du_i/dx_j + du_j/dx_i) + delta_ij lambda div u and heat-flux
+// term hq[j] = kappa dT/dx_j of state q with gradient G[j*5 + v] = dQ_v/dx_j (the entries of
+// viscous_flux: Fv[j][1+i] = tau[i][j], Fv[j][4] = sum_i u_i tau[i][j] + hq[j]).
+template <typename T>
+__device__ __forceinline__ void viscous_stress(const T q[5], const T u[3], T ri, const T *G, const PhysT<T> &ph,
+                                               const Visc<T> &vc, T tau[3][3], T hq[3]) {
+  const T eo = q[4] * ri;
+  T du[3][3];   // du[i][j] = du_i/dx_j
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) du[i][j] = (G[j * 5 + 1 + i] - u[i] * G[j * 5]) * ri;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    hq[j] = vc.kappa * (ph.cT * ((G[j * 5 + 4] - eo * G[j * 5]) * ri -
+                                 (u[0] * du[0][j] + u[1] * du[1][j] + u[2] * du[2][j])));
+  const T lam = vc.m2mu3 * (du[0][0] + du[1][1] + du[2][2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      tau[i][j] = vc.mu * (du[i][j] + du[j][i]);
+      if (i == j) tau[i][j] = tau[i][j] + lam;
+      tau[j][i] = tau[i][j];
+    }
+}
+
+// Transformed flux of reference direction d, F^_d = sum_j S[d][j] (F_j - Fv_j) (Eq. 1), formed
+// from the contravariant velocity U_d = sum_j S[d][j] u_j: inviscid (rho U_d, rho u_i U_d +
+// S[d][i] p, (E + p) U_d); viscous rows sigma_i = sum_j S[d][j] tau[i][j] and
+// sum_i u_i sigma_i + sum_j S[d][j] hq[j].  Sd = S[d][0..2].
+template <typename T>
+__device__ __forceinline__ void contravariant_flux(const T q[5], const T u[3], T p, const T Sd[3], bool viscous,
+                                                   const T tau[3][3], const T hq[3], T f[5]) {
+  const T Ud = Sd[0] * u[0] + Sd[1] * u[1] + Sd[2] * u[2];
+  f[0] = q[0] * Ud;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) f[1 + i] = q[1 + i] * Ud + Sd[i] * p;
+  f[4] = (q[4] + p) * Ud;
+  if (viscous) {
+    T sig[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      sig[i] = Sd[0] * tau[i][0] + Sd[1] * tau[i][1] + Sd[2] * tau[i][2];
+      f[1 + i] = f[1 + i] - sig[i];
+    }
+    f[4] = f[4] - (u[0] * sig[0] + u[1] * sig[1] + u[2] * sig[2] + (Sd[0] * hq[0] + Sd[1] * hq[1] + Sd[2] * hq[2]));
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Output or RK44 stage update of solution point t (flat point index over all elements): rv is the
 // bracket of Eq. 3 at the point, s = -1/|J|.  MODE_RESIDUAL writes R; MODE_RK updates the FP64
