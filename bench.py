@@ -550,7 +550,7 @@ def run_ours(args):
 # DRAM traffic per launch of the dominant kernel from ncu captures (precision, p, n_edge, kernel)
 # -> bytes; scaled from a 32^3 capture by the element count.  Only valid for the kernel version
 # that was profiled.
-TRAFFIC = {("fp64", 4, 64, "volume"): 8 * 1.5202e9, ("mixed", 4, 64, "volume"): 8 * 1.5214e9}
+TRAFFIC = {("fp64", 4, 64, "volume"): 8 * 1.5228e9, ("mixed", 4, 64, "volume"): 8 * 1.5197e9}
 
 
 def main():
