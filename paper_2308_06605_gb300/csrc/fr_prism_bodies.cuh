@@ -40,12 +40,13 @@ __host__ __device__ constexpr int prism_points() { return N * (N + 1) / 2 * N; }
 template <int N>
 __host__ __device__ constexpr int prism_threads() { return ((prism_points<N>() + 31) / 32) * 32; }
 // Resident blocks the register budget must allow, per order and arithmetic (checked with ptxas):
-// up to 64 threads and for double-float at 96 threads about 170 registers per thread; FP64 at
-// 96 threads and larger blocks need more (a tighter bound spills), so only the block size binds.
+// up to 64 threads, for double-float at 96 threads and at 128 threads (p = 5) about 170
+// registers per thread without spills; FP64 at 96 threads fits 4 blocks unbounded; the larger
+// blocks are bound by shared memory.
 template <int N, typename T>
 __host__ __device__ constexpr int prism_min_blocks() {
   return prism_threads<N>() <= 32 ? 12 : (prism_threads<N>() <= 64 ? 6 :
-         (prism_threads<N>() <= 96 ? (std::is_same<T, df32>::value ? 4 : 2) : 1));
+         (prism_threads<N>() <= 96 ? (std::is_same<T, df32>::value ? 4 : 2) : (prism_threads<N>() <= 128 ? 3 : 1)));
 }
 // Shared-memory values (of T) of the volume kernel: Q 5, grad 15, flux 15, BR2 weights 15, quad
 // lifts 15 (per point) and the jumps of 5 faces x 5 variables x N^2 slots.
@@ -152,7 +153,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
   const bool pt = active && tid < Np;
   const int m = tid < Np ? tid : 0, q = m % Nt, k = m / Nt;
   if (pt) {
-    T S[9], invJ, qv[5], H[3][5], G[15];
+    T S[9], invJ, qv[5], G[15];
     const T *met = metrics + e * 10 * Np + m;
 #pragma unroll
     for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
@@ -224,37 +225,20 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
       }
     }
     {
+      // Transformed fluxes per reference direction from the contravariant velocity.
       const T ri = ph.one / qv[0];
       const T u[3] = {qv[1] * ri, qv[2] * ri, qv[3] * ri};
       const T p = ph.gm1 * (qv[4] - ph.half * (qv[1] * u[0] + qv[2] * u[1] + qv[3] * u[2]));
+      T tau[3][3], hq[3];
+      if (viscous) viscous_stress<T>(qv, u, ri, G, ph, visc_of(ph), tau, hq);
 #pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        H[jj][0] = qv[1 + jj];
-        H[jj][1] = qv[1] * u[jj];
-        H[jj][2] = qv[2] * u[jj];
-        H[jj][3] = qv[3] * u[jj];
-        H[jj][1 + jj] = H[jj][1 + jj] + p;
-        H[jj][4] = (qv[4] + p) * u[jj];
+      for (int d = 0; d < 3; ++d) {
+        T f[5];
+        contravariant_flux<T>(qv, u, p, S + 3 * d, viscous, tau, hq, f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sH[(d * 5 + v) * Np + m] = f[v];
       }
     }
-    if (viscous) {
-      T Fv[3][5];
-      viscous_flux<T>(qv, G, ph, visc_of(ph), Fv);
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) H[jj][v] -= Fv[jj][v];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Dot<T> h;
-        h.add(S[d * 3 + 0], H[0][v]);
-        h.add(S[d * 3 + 1], H[1][v]);
-        h.add(S[d * 3 + 2], H[2][v]);
-        sH[(d * 5 + v) * Np + m] = h.get();
-      }
   }
   __syncthreads();
   if (viscous && active) {
