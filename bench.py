@@ -490,8 +490,19 @@ def run_ours(args):
         cmx.mesh.get_state(out=Out)
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - te0)
+    # Plain copy rates of the same pinned buffers (context for the end-to-end number).
+    Qd = torch.empty(Qh.shape, dtype=Qh.dtype, device="cuda")
+    rates = {}
+    for name, dst, src in (("h2d_gbs", Qd, Qh), ("d2h_gbs", Out, Qd)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        rates[name] = Qh.numel() * 8 / (time.perf_counter() - t0) / 1e9
+    del Qd
     e2e = {"value": world * n_pts * 4 * k_e2e / te, "unit": UNIT,
-           "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8)}
+           "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8),
+           "copy_rates_gbs": rates}
     cmx.close()
     del Qh, Out
 

@@ -567,8 +567,10 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
   for (int v = 0; v < 5; ++v) FI[(I * 5 + v) * Nf + q] = F[v];
 }
 
+// 5 resident blocks of 128 threads (96 registers, a few spills): the double-float interface
+// kernel measured 4 % faster than with 128 registers and 4 blocks; the FP64 one is unchanged.
 template <int N, typename T>
-__global__ void k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
+__global__ void __launch_bounds__(128, 5) k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                              const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph,
                              const int32_t *__restrict__ if_elem, const float *__restrict__ nu,
                              const int8_t *__restrict__ if_up) {
