@@ -43,6 +43,24 @@ def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def _dist_barrier(world):
+    """Barrier over the replicas (no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _dist_max(v, world, device):
+    """Max of a timing scalar over the replicas (all-reduce of one number; no data-path exchange)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([v], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        v = float(tt.item())
+    return v
+
+
 # ------------------------------------------------------------------------------ clocks sampling
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -420,15 +438,10 @@ def run_ours(args):
         return 0
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        _dist_barrier(world)
 
     def max_over_ranks(v):
-        if world > 1:
-            tt = torch.tensor([v], device=f"cuda:{dev}", dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            v = float(tt.item())
-        return v
+        return _dist_max(v, world, f"cuda:{dev}")
 
     # Headline workload: both precisions on the same initial state and the same dt.
     c64 = Case(N_EDGE, ORDER, "fp64")
