@@ -158,17 +158,21 @@ def test_nonfinite_state_reported():
     g.close()
 
 
-def test_full_size_64cube_p4_sampled():
-    """The 64^3, p = 4 TGV (32.8 M points) in the benchmark's launch configuration, checked on
-    sampled elements: BR2 is compact, so an element's residual depends only on itself and its
-    six face neighbours; the oracle evaluates each sample on a 3x3x3 periodic patch holding the
-    same data and geometry, whose centre element is the sample."""
+@pytest.mark.parametrize("precision,rel", [(0, 1e-12), (1, 1e-9)])
+def test_full_size_64cube_p4_sampled(precision, rel):
+    """The 64^3, p = 4 TGV (32.8 M points) in the benchmark's launch configuration, both
+    precisions (the double-float one is the headline path), checked on sampled elements: BR2 is
+    compact, so an element's residual depends only on itself and its six face neighbours; the
+    oracle evaluates each sample on a 3x3x3 periodic patch holding the same data and geometry,
+    whose centre element is the sample."""
     n, p = 64, 4
     L = 2 * np.pi
     h = L / n
     d = I.hex_box_mesh((n, n, n))
     phys = I.tgv_physics()
-    g = fr.Mesh(d, phys, p)
+    gphys = I.tgv_physics()
+    gphys.precision = precision
+    g = fr.Mesh(d, gphys, p)
     # Solution points from the oracle's own geometry (never from the library).
     xi = Basis1D(p).nodes
     K, Jj, Ii = np.meshgrid(xi, xi, xi, indexing="ij")
@@ -194,12 +198,14 @@ def test_full_size_64cube_p4_sampled():
         Rp = ora.residual(Qp)
         Sp = ora.residual(Qp, magnitude=True)
         e_c = i + n * (j + n * k)
-        assert_residual_parity(R[e_c], Rp[13], Sp[13])
+        assert_residual_parity(R[e_c], Rp[13], Sp[13], rel=rel)
     # Discrete conservation at full size: quadrature weights (library Gauss-Legendre rule) on
     # congruent affine cubes, so the constant |J| drops out.
     w = np.polynomial.legendre.leggauss(p + 1)[1]
     W = np.kron(w, np.kron(w, w))
     s = np.abs(np.einsum('m,emv->v', W, R))
     a = np.einsum('m,emv->v', W, np.abs(R))
-    assert np.all(s <= 1e-12 * a), s / a
+    # Double-float: the per-entry bar is 1e-9 of the magnitude scale S, and at Ma 0.1 S exceeds |R|
+    # by up to ~1e2 (cancelling terms), so the sum is held to 1e-7 of sum |W R|.
+    assert np.all(s <= (1e-12 if precision == 0 else 1e-7) * a), s / a
     g.close()
