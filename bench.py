@@ -507,11 +507,14 @@ def run_ours(args):
     Qd = torch.empty(Qh.shape, dtype=Qh.dtype, device="cuda")
     rates = {}
     for name, dst, src in (("h2d_gbs", Qd, Qh), ("d2h_gbs", Out, Qd)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dst.copy_(src, non_blocking=True)
-        torch.cuda.synchronize()
-        rates[name] = Qh.numel() * 8 / (time.perf_counter() - t0) / 1e9
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = max(best, Qh.numel() * 8 / (time.perf_counter() - t0) / 1e9)
+        rates[name] = best
     del Qd
     e2e = {"value": world * n_pts * 4 * k_e2e / te, "unit": UNIT,
            "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8),
