@@ -494,6 +494,10 @@ def run_ours(args):
     Qh = torch.from_numpy(cmx.Q0).pin_memory()
     Out = torch.empty_like(Qh).pin_memory()
     k_e2e = max(1, args.steps)
+    # One untimed pass first: the first transfers from freshly pinned buffers pay one-time costs.
+    cmx.mesh.set_state(Qh)
+    cmx.step()
+    cmx.mesh.get_state(out=Out)
     torch.cuda.synchronize()
     barrier()
     te0 = time.perf_counter()
