@@ -38,10 +38,11 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
-def _create(desc, phys, p):
+def _create(desc, phys, p, vcjh_c=0.0):
     lib = fr.load()
     xyz = np.ascontiguousarray(desc.xyz)
     hexa = np.ascontiguousarray(desc.hex)
+    pri = np.ascontiguousarray(desc.prism if getattr(desc, "prism", None) is not None else np.zeros((0, 6), np.int64))
     bn = np.ascontiguousarray(desc.bface_nodes)
     bt = np.ascontiguousarray(desc.bface_tag)
     per = (fr.fr_periodic * max(1, len(desc.periodic)))()
@@ -52,9 +53,10 @@ def _create(desc, phys, p):
     d = fr.fr_mesh_desc(n_nodes=xyz.shape[0], xyz=fr._ptr(xyz, C.c_double), n_hex=hexa.shape[0],
                         hex=fr._ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
                         bface_nodes=fr._ptr(bn, C.c_int64), bface_tag=fr._ptr(bt, C.c_int32),
-                        n_bc=0, bc=None, n_periodic=len(desc.periodic), periodic=per)
+                        n_bc=0, bc=None, n_periodic=len(desc.periodic), periodic=per,
+                        n_prism=pri.shape[0], prism=fr._ptr(pri, C.c_int64))
     ph = fr.fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=0, viscous=phys.viscous,
-                       br2_eta=6.0, precision=0)
+                       br2_eta=6.0, precision=0, vcjh_c=vcjh_c)
     h = C.c_void_p()
     st = lib.fr_mesh_create(C.byref(d), C.byref(ph), 0, C.byref(h))
     return st, lib.fr_last_error(None).decode()
@@ -102,3 +104,14 @@ def test_face_shared_by_three_elements_is_mesh_error(lib):
     d.hex = np.concatenate([d.hex, d.hex[:1]])
     st, msg = _create(d, I.tgv_physics(), 2)
     assert st == fr.FR_EMESH and "shared by" in msg
+
+
+def test_correction_parameter_checked_before_device_work(lib):
+    """c must keep 1 + eta > 0 (eta = c (2p+1) (a_p p!)^2 / 2; at p = 2, a_p p! = 3, so the
+    limit is c_- = -2/45); c != 0 is refused on meshes with prisms."""
+    d = I.hex_box_mesh((2, 2, 2))
+    for c in (-2.0 / 45.0 * 1.000001, -1.0, float("nan"), float("inf")):
+        st, msg = _create(d, I.tgv_physics(), 2, vcjh_c=c)
+        assert st == fr.FR_EINVAL and "correction parameter" in msg, (c, msg)
+    st, msg = _create(I.hex_box_mesh((2, 2, 2), prisms="checker"), I.tgv_physics(), 2, vcjh_c=0.01)
+    assert st == fr.FR_EUNSUPPORTED and "hexahedral" in msg
