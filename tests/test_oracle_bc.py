@@ -98,3 +98,81 @@ def test_orientation_invariance_with_walls():
     from scipy.spatial import cKDTree
     idx = cKDTree(mb.x.reshape(-1, 3)).query(ma.x.reshape(-1, 3))[1]
     np.testing.assert_allclose(Rb.reshape(-1, 5)[idx], Ra.reshape(-1, 5), rtol=0, atol=1e-12 * np.abs(Ra).max())
+
+
+def _prim(Q, g):
+    rho = Q[..., 0]
+    u = Q[..., 1:4] / rho[..., None]
+    p = (g - 1.0) * (Q[..., 4] - 0.5 * rho * np.sum(u * u, axis=-1))
+    return rho, u, p
+
+
+def _random_subsonic(rng, n, g, Rg):
+    rho = rng.uniform(0.8, 1.2, n)
+    p = rng.uniform(0.7, 1.3, n)
+    c = np.sqrt(g * p / rho)
+    u = rng.normal(size=(n, 3)) * 0.15 * c[:, None]
+    Q = np.concatenate([rho[:, None], rho[:, None] * u, (p / (g - 1.0) + 0.5 * rho * np.sum(u * u, -1))[:, None]], 1)
+    nrm = rng.normal(size=(n, 3)) * rng.uniform(0.5, 2.0, (n, 1))
+    return Q, nrm
+
+
+def test_characteristic_outflow_state_obeys_its_defining_relations():
+    """Static pressure imposed; entropy p / rho^gamma, tangential velocity and the outgoing
+    Riemann invariant u.n + 2c/(gamma-1) carried from the interior (checked with formulas
+    written here); imposing the interior's own pressure returns the interior state."""
+    from oracle.hexfr import boundary_states
+    g, Rg = 1.4, 287.0 / 1000.0
+    rng = np.random.default_rng(3)
+    Qm, n = _random_subsonic(rng, 64, g, Rg)
+    nh = n / np.linalg.norm(n, axis=-1, keepdims=True)
+    pb = 0.93
+    Qg, Qi = boundary_states(I.BC_CHAR_OUTFLOW, np.array([pb, 0, 0, 0, 0, 0, 0, 0.0]), Qm, n, g, Rg)
+    assert np.array_equal(Qg, Qi)
+    r0, u0, p0 = _prim(Qm, g)
+    rb, ub, pbb = _prim(Qg, g)
+    np.testing.assert_allclose(pbb, pb, rtol=1e-13)
+    np.testing.assert_allclose(pbb / rb ** g, p0 / r0 ** g, rtol=1e-12)
+    tang = lambda u: u - np.sum(u * nh, -1)[:, None] * nh  # noqa: E731
+    np.testing.assert_allclose(tang(ub), tang(u0), atol=1e-13)
+    inv = lambda r, u, p: np.sum(u * nh, -1) + 2.0 * np.sqrt(g * p / r) / (g - 1.0)  # noqa: E731
+    np.testing.assert_allclose(inv(rb, ub, pbb), inv(r0, u0, p0), rtol=1e-13)
+    for k in range(4):
+        Qs, _ = boundary_states(I.BC_CHAR_OUTFLOW, np.array([p0[k], 0, 0, 0, 0, 0, 0, 0.0]), Qm[k:k + 1], n[k:k + 1], g, Rg)
+        np.testing.assert_allclose(Qs[0], Qm[k], rtol=1e-13, atol=1e-14)
+
+
+def test_characteristic_inflow_state_obeys_isentropic_total_conditions():
+    """Total temperature T0 = T + |u|^2 / (2 cp), total pressure p0 = p (T0 / T)^(gamma/(gamma-1)),
+    velocity along the prescribed direction, and the outgoing invariant carried from the
+    interior (formulas written here)."""
+    from oracle.hexfr import boundary_states
+    g, Rg = 1.4, 0.287
+    cp = g * Rg / (g - 1.0)
+    rng = np.random.default_rng(4)
+    p0, T0, M = 1.2, 3.9, 0.3
+    d = np.array([1.0, 0.3, -0.2])
+    dh = d / np.linalg.norm(d)
+    # Interior states: the isentropic state of (p0, T0) at Mach 0.3 along d, perturbed by ~2 %.
+    nq = 64
+    T = T0 / (1.0 + 0.5 * (g - 1.0) * M * M) * rng.uniform(0.98, 1.02, nq)
+    pr = p0 * (T / T0) ** (g / (g - 1.0)) * rng.uniform(0.98, 1.02, nq)
+    rho = pr / (Rg * T)
+    u = (M * np.sqrt(g * Rg * T))[:, None] * dh[None, :] * rng.uniform(0.9, 1.1, (nq, 1)) + \
+        0.02 * rng.normal(size=(nq, 3))
+    Qm = np.concatenate([rho[:, None], rho[:, None] * u, (pr / (g - 1.0) + 0.5 * rho * np.sum(u * u, -1))[:, None]], 1)
+    # Inflow faces: the outward normal points against the flow direction, tilted.
+    n = rng.uniform(0.5, 2.0, (nq, 1)) * (-dh[None, :] + 0.3 * rng.normal(size=(nq, 3)))
+    nh = n / np.linalg.norm(n, axis=-1, keepdims=True)
+    Qg, Qi = boundary_states(I.BC_CHAR_INFLOW, np.array([p0, T0, *d, 0, 0, 0.0]), Qm, n, g, Rg)
+    assert np.array_equal(Qg, Qi)
+    rb, ub, pb = _prim(Qg, g)
+    Tb = pb / (rb * Rg)
+    V = np.linalg.norm(ub, axis=-1)
+    np.testing.assert_allclose(Tb + V * V / (2.0 * cp), T0, rtol=1e-13)
+    np.testing.assert_allclose(pb * (T0 / Tb) ** (g / (g - 1.0)), p0, rtol=1e-12)
+    np.testing.assert_allclose(np.cross(ub, dh), 0.0, atol=1e-13)
+    assert np.all(ub @ dh > 0)
+    r0, u0, pm = _prim(Qm, g)
+    inv = lambda r, u, p: np.sum(u * nh, -1) + 2.0 * np.sqrt(g * p / r) / (g - 1.0)  # noqa: E731
+    np.testing.assert_allclose(inv(rb, ub, pb), inv(r0, u0, pm), rtol=1e-12)
