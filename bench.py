@@ -159,6 +159,9 @@ def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
+    # One core, as reported: BLAS / OpenMP threads pinned before NumPy is first imported.
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
     for _ in range(args.warmup):
         oracle_rate(max_steps=1)
     t0 = time.perf_counter()
