@@ -166,6 +166,18 @@ fr_status fr_mesh_query(const fr_mesh *mesh, fr_mesh_info *info);
 fr_status fr_solution_points(fr_mesh *mesh, double *xyz_host);
 
 /*
+ * fr_basis_1d — the 1D tables of order p that the element kernels apply along each reference
+ * line (Eq. 2 and the correction term of Eq. 3), computed on the host, no device work: the
+ * N = p + 1 Gauss-Legendre nodes x and weights w, the nodal derivative matrix D[i*N + a] =
+ * l_a'(x_i), the boundary values lm[a] = l_a(-1), lp[a] = l_a(+1), and the correction
+ * divergences hm[i] = g_R'(-x_i), hp[i] = g_R'(x_i) of the correction function with parameter c
+ * (vcjh_c of fr_physics; 0 = DG-equivalent).  Arrays are caller-owned host buffers of N (D:
+ * N*N) doubles; any of them may be NULL.  p outside 1..7 or c outside the family -> FR_EINVAL.
+ */
+fr_status fr_basis_1d(int32_t p, double c, double *x, double *w, double *D, double *lm, double *lp,
+                      double *hm, double *hp);
+
+/*
  * fr_set_state / fr_get_state — copy the solution Q (canonical layout, n_points*5 doubles)
  * into / out of the mesh.  `where` = FR_HOST or FR_DEVICE.  fr_set_state also resets the
  * Runge–Kutta registers (the solution becomes the start of a new step).

@@ -174,6 +174,28 @@ bool vcjh_in_family(int p, double c) {
   return std::isfinite((double)eta) && 1 + eta > 0;
 }
 
+}  // namespace frx
+
+extern "C" fr_status fr_basis_1d(int32_t p, double c, double *x, double *w, double *D, double *lm, double *lp,
+                                 double *hm, double *hp) {
+  if (p < 1 || p > 7 || !frx::vcjh_in_family(p, c)) return FR_EINVAL;
+  const frx::Basis1D b = frx::make_basis(p, c);
+  const int N = p + 1;
+  for (int i = 0; i < N; ++i) {
+    if (x) x[i] = b.x[i];
+    if (w) w[i] = b.w[i];
+    if (lm) lm[i] = b.lm[i];
+    if (lp) lp[i] = b.lp[i];
+    if (hm) hm[i] = b.hm[i];
+    if (hp) hp[i] = b.hp[i];
+    for (int a = 0; a < N; ++a)
+      if (D) D[i * N + a] = b.D[i * N + a];
+  }
+  return FR_OK;
+}
+
+namespace frx {
+
 // ------------------------------------------------------------------------------------------
 // Geometry of the trilinear hexahedron.
 // ------------------------------------------------------------------------------------------

@@ -103,6 +103,7 @@ SIGNATURES = {
     "fr_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_free": (None, [C.c_void_p]),
     "fr_last_error": (C.c_char_p, [C.c_void_p]),
+    "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
 }
 
 _lib = None
@@ -137,6 +138,18 @@ def _data_ptr(x):
     if not (x.is_contiguous() and str(x.dtype) == "torch.float64"):
         raise ValueError("state tensors must be contiguous float64")
     return C.c_void_p(x.data_ptr()), (FR_DEVICE if x.is_cuda else FR_HOST)
+
+
+def basis_1d(p: int, c: float = 0.0) -> dict:
+    """fr_basis_1d: the library's 1D tables of order p (host computation, no device work)."""
+    lib = load()
+    N = p + 1
+    out = {k: np.zeros(N * N if k == "D" else N) for k in ("x", "w", "D", "lm", "lp", "hm", "hp")}
+    st = lib.fr_basis_1d(p, c, *[_ptr(out[k], C.c_double) for k in ("x", "w", "D", "lm", "lp", "hm", "hp")])
+    if st != FR_OK:
+        raise FRError(st, "fr_basis_1d: order or correction parameter out of range")
+    out["D"] = out["D"].reshape(N, N)
+    return out
 
 
 def probe_fma(precision: int = 0, iters: int = 20000) -> float:
