@@ -178,6 +178,21 @@ fr_status fr_basis_1d(int32_t p, double c, double *x, double *w, double *D, doub
                       double *hm, double *hp);
 
 /*
+ * fr_tri_basis — the nodal triangle tables of order p that the prism kernels apply (host
+ * computation, no device work): the Nt = (p+1)(p+2)/2 warp-and-blend nodes rs[Nt][2] in the
+ * canonical prism order, the derivative matrices Dr, Ds [Nt][Nt] and the inverse mass matrix
+ * Minv [Nt][Nt] of the nodal basis.  Caller-owned host buffers, any may be NULL; p outside 1..7
+ * -> FR_EINVAL.
+ *
+ * fr_transfer_matrix — the L2-projection operator of fr_project_state from order p to order q
+ * (host computation): kind 0 the line [q+1][p+1] (Legendre coefficients through the Gauss
+ * points, truncated or zero-padded), kind 1 the triangle [Nt_q][Nt_p] (orthonormal modes of
+ * total degree <= min(p, q)).  p, q in 1..7, else FR_EINVAL.
+ */
+fr_status fr_tri_basis(int32_t p, double *rs, double *Dr, double *Ds, double *Minv);
+fr_status fr_transfer_matrix(int32_t kind, int32_t p, int32_t q, double *T);
+
+/*
  * fr_set_state / fr_get_state — copy the solution Q (canonical layout, n_points*5 doubles)
  * into / out of the mesh.  `where` = FR_HOST or FR_DEVICE.  fr_set_state also resets the
  * Runge–Kutta registers (the solution becomes the start of a new step).

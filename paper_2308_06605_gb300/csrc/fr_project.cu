@@ -76,6 +76,17 @@ __global__ void k_project(const double *__restrict__ src, double *__restrict__ d
 
 using namespace frx;
 
+extern "C" fr_status fr_transfer_matrix(int32_t kind, int32_t p, int32_t q, double *T) {
+  if (!T || p < 1 || p > 7 || q < 1 || q > 7 || (kind != 0 && kind != 1)) return FR_EINVAL;
+  std::vector<double> M;
+  if (kind == 0)
+    line_transfer(p, q, M);
+  else if (!tri_transfer(p, q, M))
+    return FR_EINVAL;
+  for (size_t i = 0; i < M.size(); ++i) T[i] = M[i];
+  return FR_OK;
+}
+
 extern "C" fr_status fr_project_state(fr_mesh *src, fr_mesh *dst) {
   DevMesh a, b;
   DevPhys pa, pb;

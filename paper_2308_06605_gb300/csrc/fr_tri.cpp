@@ -317,3 +317,22 @@ bool make_tri_basis(int p, TriBasis &T) {
 }
 
 }  // namespace frx
+
+extern "C" fr_status fr_tri_basis(int32_t p, double *rs, double *Dr, double *Ds, double *Minv) {
+  if (p < 1 || p > 7) return FR_EINVAL;
+  frx::TriBasis T;
+  if (!frx::make_tri_basis(p, T)) return FR_EINVAL;
+  const size_t Nt = (size_t)T.Nt;
+  for (size_t i = 0; i < Nt; ++i) {
+    if (rs) {
+      rs[2 * i] = T.r[i];
+      rs[2 * i + 1] = T.s[i];
+    }
+    for (size_t j = 0; j < Nt; ++j) {
+      if (Dr) Dr[i * Nt + j] = T.Dr[i * Nt + j];
+      if (Ds) Ds[i * Nt + j] = T.Ds[i * Nt + j];
+      if (Minv) Minv[i * Nt + j] = T.Minv[i * Nt + j];
+    }
+  }
+  return FR_OK;
+}

@@ -104,6 +104,8 @@ SIGNATURES = {
     "fr_free": (None, [C.c_void_p]),
     "fr_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
+    "fr_tri_basis": (C.c_int, [C.c_int32] + [C.POINTER(C.c_double)] * 4),
+    "fr_transfer_matrix": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -150,6 +152,28 @@ def basis_1d(p: int, c: float = 0.0) -> dict:
         raise FRError(st, "fr_basis_1d: order or correction parameter out of range")
     out["D"] = out["D"].reshape(N, N)
     return out
+
+
+def tri_basis(p: int) -> dict:
+    """fr_tri_basis: the library's triangle tables of order p (host computation)."""
+    lib = load()
+    Nt = (p + 1) * (p + 2) // 2
+    out = {"rs": np.zeros((Nt, 2)), "Dr": np.zeros((Nt, Nt)), "Ds": np.zeros((Nt, Nt)), "Minv": np.zeros((Nt, Nt))}
+    st = lib.fr_tri_basis(p, *[_ptr(out[k], C.c_double) for k in ("rs", "Dr", "Ds", "Minv")])
+    if st != FR_OK:
+        raise FRError(st, "fr_tri_basis: order out of range")
+    return out
+
+
+def transfer_matrix(kind: int, p: int, q: int) -> np.ndarray:
+    """fr_transfer_matrix: the order-p -> order-q projection operator (0 line, 1 triangle)."""
+    lib = load()
+    n = (lambda k: k + 1) if kind == 0 else (lambda k: (k + 1) * (k + 2) // 2)
+    T = np.zeros((n(q), n(p)))
+    st = lib.fr_transfer_matrix(kind, p, q, _ptr(T, C.c_double))
+    if st != FR_OK:
+        raise FRError(st, "fr_transfer_matrix: bad kind or order")
+    return T
 
 
 def probe_fma(precision: int = 0, iters: int = 20000) -> float:
