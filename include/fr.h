@@ -156,6 +156,17 @@ typedef struct {
 fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
                          fr_mesh **out);
 
+/*
+ * fr_mesh_inspect — the host half of fr_mesh_create without any device work: validates the
+ * description and builds connectivity and geometry (same checks and statuses as fr_mesh_create
+ * for the mesh itself), then fills *info (device_bytes = 0) and, where the pointers are not NULL,
+ * the solution points xyz_host [n_points][3] in the canonical order and the metric terms
+ * metrics_host: hexahedra [n_elem][10][n_pts] then prisms [n_prism][10][n_pts_prism], per point
+ * S = |J| J^-1 row-major (reference direction, physical component) and then 1/|J| (Eq. 1).
+ * Call once with NULL arrays for the sizes.  Caller-owned host buffers.
+ */
+fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *info, double *xyz_host, double *metrics_host);
+
 /* fr_mesh_query — sizes of a created mesh (host struct filled). */
 fr_status fr_mesh_query(const fr_mesh *mesh, fr_mesh_info *info);
 

@@ -327,6 +327,45 @@ extern "C" fr_status fr_mesh_query(const fr_mesh *m, fr_mesh_info *info) {
   return FR_OK;
 }
 
+extern "C" fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *info, double *xyz_host,
+                                     double *metrics_host) {
+  if (!desc || !info) return fail(nullptr, FR_EINVAL, "desc or info is NULL");
+  if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
+  if (desc->n_hex < 0 || desc->n_prism < 0 || desc->n_hex + desc->n_prism <= 0 || (desc->n_hex > 0 && !desc->hex) ||
+      (desc->n_prism > 0 && !desc->prism) || desc->n_nodes <= 0 || !desc->xyz)
+    return fail(nullptr, FR_EINVAL, "empty mesh or NULL arrays");
+  if (desc->n_bface < 0 || (desc->n_bface > 0 && (!desc->bface_nodes || !desc->bface_tag)))
+    return fail(nullptr, FR_EINVAL, "bad boundary-face arrays");
+  if (desc->n_bc < 0 || (desc->n_bc > 0 && !desc->bc) || desc->n_periodic < 0 ||
+      (desc->n_periodic > 0 && !desc->periodic))
+    return fail(nullptr, FR_EINVAL, "bad boundary-condition or periodic arrays");
+  HostMesh h;
+  std::string err;
+  fr_status st;
+  try {
+    st = build_host_mesh(desc, h, err);
+  } catch (const std::bad_alloc &) {
+    st = FR_ENOMEM;
+    err = "host allocation failed while building the mesh";
+  }
+  if (st != FR_OK) return fail(nullptr, st, err);
+  info->n_elem = h.E;
+  info->p = h.p;
+  info->n_pts = h.Np;
+  info->n_iface = h.n_interior;
+  info->n_bface = h.n_if - h.n_interior;
+  info->device_bytes = 0;
+  info->n_prism = h.Ep;
+  info->n_pts_prism = h.Npp;
+  info->n_points = h.E * h.Np + h.Ep * h.Npp;
+  if (xyz_host) std::memcpy(xyz_host, h.xsol.data(), h.xsol.size() * sizeof(double));
+  if (metrics_host) {
+    std::memcpy(metrics_host, h.metrics.data(), h.metrics.size() * sizeof(double));
+    std::memcpy(metrics_host + h.metrics.size(), h.metrics_p.data(), h.metrics_p.size() * sizeof(double));
+  }
+  return FR_OK;
+}
+
 extern "C" fr_status fr_solution_points(fr_mesh *m, double *xyz) {
   fr_status st = check_mesh(m);
   if (st) return st;

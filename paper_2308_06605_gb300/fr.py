@@ -106,6 +106,7 @@ SIGNATURES = {
     "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
     "fr_tri_basis": (C.c_int, [C.c_int32] + [C.POINTER(C.c_double)] * 4),
     "fr_transfer_matrix": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "fr_mesh_inspect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -185,6 +186,58 @@ def probe_fma(precision: int = 0, iters: int = 20000) -> float:
     return v.value
 
 
+def _describe(desc: MeshDesc, p: int):
+    """The C mesh description of `desc` at order p, and the arrays it points into (keep alive)."""
+    xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
+    hexa = np.asarray(desc.hex, dtype=np.int64)
+    hexa = np.ascontiguousarray(hexa if hexa.ndim == 2 else hexa.reshape(-1, 8))    # 8 or 27 nodes each
+    pri = getattr(desc, "prism", None)
+    pri = np.asarray(np.zeros((0, 6)) if pri is None else pri, dtype=np.int64)
+    pri = np.ascontiguousarray(pri if pri.ndim == 2 else pri.reshape(-1, 6))           # 6 or 18 nodes each
+    bn = np.ascontiguousarray(desc.bface_nodes, dtype=np.int64).reshape(-1, 4)
+    bt = np.ascontiguousarray(desc.bface_tag, dtype=np.int32)
+    bcs = (fr_bc * max(1, len(desc.bcs)))()
+    for i, bc in enumerate(desc.bcs):
+        bcs[i].tag, bcs[i].kind = bc.tag, bc.kind
+        for k, v in enumerate(bc.params[:8]):
+            bcs[i].params[k] = v
+    per = (fr_periodic * max(1, len(desc.periodic)))()
+    for i, pp in enumerate(desc.periodic):
+        per[i].tag_a, per[i].tag_b = pp.tag_a, pp.tag_b
+        for k in range(3):
+            per[i].t[k] = pp.t[k]
+    d = fr_mesh_desc(n_nodes=xyz.shape[0], xyz=_ptr(xyz, C.c_double), n_hex=hexa.shape[0],
+                     hex=_ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
+                     bface_nodes=_ptr(bn, C.c_int64), bface_tag=_ptr(bt, C.c_int32),
+                     n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per,
+                     n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64),
+                     hex_nodes=hexa.shape[1], prism_nodes=pri.shape[1])
+    return d, [xyz, hexa, pri, bn, bt, bcs, per]
+
+
+def inspect(desc: MeshDesc, p: int) -> dict:
+    """fr_mesh_inspect: sizes, solution points and metric terms of the host mesh build (no device
+    work).  Points are [n_points][3]; metrics split into hexahedra [n_elem][10][n_pts] and prisms
+    [n_prism][10][n_pts_prism]."""
+    lib = load()
+    d, keep = _describe(desc, p)
+    info = fr_mesh_info()
+    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None)
+    if st != FR_OK:
+        raise FRError(st, lib.fr_last_error(None).decode())
+    x = np.zeros((info.n_points, 3))
+    nh, nph = info.n_elem * 10 * info.n_pts, info.n_prism * 10 * info.n_pts_prism
+    met = np.zeros(nh + nph)
+    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), C.c_void_p(x.ctypes.data), C.c_void_p(met.ctypes.data))
+    if st != FR_OK:
+        raise FRError(st, lib.fr_last_error(None).decode())
+    del keep
+    return {"n_elem": info.n_elem, "n_pts": info.n_pts, "n_iface": info.n_iface, "n_bface": info.n_bface,
+            "n_prism": info.n_prism, "n_pts_prism": info.n_pts_prism, "n_points": info.n_points, "x": x,
+            "metrics_hex": met[:nh].reshape(info.n_elem, 10, info.n_pts),
+            "metrics_prism": met[nh:].reshape(info.n_prism, 10, info.n_pts_prism)}
+
+
 class Mesh:
     """One FR discretisation living on the current CUDA device (owns the C-side fr_mesh).
 
@@ -196,31 +249,8 @@ class Mesh:
         lib = load()
         self._lib = lib
         self._keep = []
-        xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
-        hexa = np.asarray(desc.hex, dtype=np.int64)
-        hexa = np.ascontiguousarray(hexa if hexa.ndim == 2 else hexa.reshape(-1, 8))    # 8 or 27 nodes each
-        pri = getattr(desc, "prism", None)
-        pri = np.asarray(np.zeros((0, 6)) if pri is None else pri, dtype=np.int64)
-        pri = np.ascontiguousarray(pri if pri.ndim == 2 else pri.reshape(-1, 6))           # 6 or 18 nodes each
-        bn = np.ascontiguousarray(desc.bface_nodes, dtype=np.int64).reshape(-1, 4)
-        bt = np.ascontiguousarray(desc.bface_tag, dtype=np.int32)
-        bcs = (fr_bc * max(1, len(desc.bcs)))()
-        for i, bc in enumerate(desc.bcs):
-            bcs[i].tag, bcs[i].kind = bc.tag, bc.kind
-            for k, v in enumerate(bc.params[:8]):
-                bcs[i].params[k] = v
-        per = (fr_periodic * max(1, len(desc.periodic)))()
-        for i, pp in enumerate(desc.periodic):
-            per[i].tag_a, per[i].tag_b = pp.tag_a, pp.tag_b
-            for k in range(3):
-                per[i].t[k] = pp.t[k]
-        self._keep += [xyz, hexa, pri, bn, bt, bcs, per]
-        d = fr_mesh_desc(n_nodes=xyz.shape[0], xyz=_ptr(xyz, C.c_double), n_hex=hexa.shape[0],
-                         hex=_ptr(hexa, C.c_int64), p=p, n_bface=bn.shape[0],
-                         bface_nodes=_ptr(bn, C.c_int64), bface_tag=_ptr(bt, C.c_int32),
-                         n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per,
-                         n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64),
-                         hex_nodes=hexa.shape[1], prism_nodes=pri.shape[1])
+        d, keep = _describe(desc, p)
+        self._keep += keep
         ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
                         viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision,
                         ldg_tau=getattr(phys, "ldg_tau", 0.1), vcjh_c=getattr(phys, "vcjh_c", 0.0))
