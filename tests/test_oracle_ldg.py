@@ -118,3 +118,40 @@ def test_shear_wave_residual_converges(scheme, p):
         want[..., 4] = mu * A * A * np.cos(2 * X)
         errs.append(np.abs(R - want).max() / (mu * A))
     assert errs[1] < 0.8 and np.log2(errs[0] / errs[1]) > p - 1.5, errs
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_penalty_dissipates_the_squared_jumps_exactly(p):
+    """Changing tau only changes the penalty tau |n| (Q_0 - Q_1) of the common normal flux; with
+    the DG-equivalent lifting its contribution to sum_e sum_m W |J| Q . R is exactly
+    -dtau sum_faces sum_fp w_fp |n| |Q_0 - Q_1|^2 (computed here from the basis values on an
+    axis-aligned periodic 4x1x1 box, where every jump is known by construction)."""
+    from oracle.basis import Basis1D
+    hx, hy, hz = 0.7, 1.3, 0.9
+    d = I.hex_box_mesh((4, 1, 1), hi=(4 * hx, hy, hz))
+    rng = np.random.default_rng(p)
+    N = p + 1
+    R = []
+    for tau in (0.1, 0.35):
+        ph = I.Physics(gamma=G, R=1.0, mu=0.03, Pr=0.71, viscous=2, ldg_tau=tau)
+        m = HexFR(d, ph, p)
+        if not R:
+            # element e spans [e hx, (e+1) hx] with xi along +x (unrotated, unshuffled box)
+            assert np.allclose(m.x[:, 0, 0], np.arange(4) * hx + hx / 2 * (1 + Basis1D(p).nodes[0]))
+            Q = I.uniform_state(m.x.shape[:2]) * (1 + 0.05 * rng.standard_normal(m.x.shape[:2] + (5,)))
+        R.append(m.residual(Q))
+    dE = np.einsum('m,em,emv,emv->', m.W, m.detJ, Q, R[1] - R[0])
+    b = Basis1D(p)
+    q = Q.reshape(4, N, N, N, 5)            # [e][k][j][i][v]
+    wf = np.outer(b.weights, b.weights)     # face quadrature weights over the two tangential axes
+    jump2 = 0.0
+    for e in range(4):                      # x faces: element e's +x trace against e+1's -x trace
+        right = np.einsum('i,kjiv->kjv', b.l_plus, q[e])
+        left = np.einsum('i,kjiv->kjv', b.l_minus, q[(e + 1) % 4])
+        jump2 += hy * hz / 4 * np.sum(wf[:, :, None] * (right - left) ** 2)
+        # y and z faces: the element meets itself through the periodic pairs
+        yj = np.einsum('j,kjiv->kiv', b.l_plus, q[e]) - np.einsum('j,kjiv->kiv', b.l_minus, q[e])
+        zj = np.einsum('k,kjiv->jiv', b.l_plus, q[e]) - np.einsum('k,kjiv->jiv', b.l_minus, q[e])
+        jump2 += hx * hz / 4 * np.sum(wf[:, :, None] * yj ** 2) + hx * hy / 4 * np.sum(wf[:, :, None] * zj ** 2)
+    want = -(0.35 - 0.1) * jump2
+    assert want < 0 and abs(dE - want) <= 1e-10 * abs(want), (dE, want)
