@@ -162,10 +162,17 @@ fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintp
  * for the mesh itself), then fills *info (device_bytes = 0) and, where the pointers are not NULL,
  * the solution points xyz_host [n_points][3] in the canonical order and the metric terms
  * metrics_host: hexahedra [n_elem][10][n_pts] then prisms [n_prism][10][n_pts_prism], per point
- * S = |J| J^-1 row-major (reference direction, physical component) and then 1/|J| (Eq. 1).
- * Call once with NULL arrays for the sizes.  Caller-owned host buffers.
+ * S = |J| J^-1 row-major (reference direction, physical component) and then 1/|J| (Eq. 1);
+ * the hexahedra's face table ef_host [n_elem][6] (interface << 4 | side << 3 | orientation
+ * code; faces ordered xi-, xi+, eta-, eta+, zeta-, zeta+; interfaces: the n_iface two-sided ones,
+ * then the boundary faces) and normals_host [n_iface + n_bface][4][(p+1)^2]: side 0's outward
+ * area-scaled normal at each flux point in side 0's point order, then its length.  A side-1 face
+ * point (a, b) sits in slot a' + (p+1) b' with (a', b') = (b, a) if code & 4, then a' reversed if
+ * code & 1 and b' reversed if code & 2.  Call once with NULL arrays for the sizes.
+ * Caller-owned host buffers.
  */
-fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *info, double *xyz_host, double *metrics_host);
+fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *info, double *xyz_host, double *metrics_host,
+                          int32_t *ef_host, double *normals_host);
 
 /* fr_mesh_query — sizes of a created mesh (host struct filled). */
 fr_status fr_mesh_query(const fr_mesh *mesh, fr_mesh_info *info);

@@ -106,7 +106,7 @@ SIGNATURES = {
     "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
     "fr_tri_basis": (C.c_int, [C.c_int32] + [C.POINTER(C.c_double)] * 4),
     "fr_transfer_matrix": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
-    "fr_mesh_inspect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_mesh_inspect": (C.c_int, [C.c_void_p] * 6),
 }
 
 _lib = None
@@ -216,26 +216,31 @@ def _describe(desc: MeshDesc, p: int):
 
 
 def inspect(desc: MeshDesc, p: int) -> dict:
-    """fr_mesh_inspect: sizes, solution points and metric terms of the host mesh build (no device
-    work).  Points are [n_points][3]; metrics split into hexahedra [n_elem][10][n_pts] and prisms
-    [n_prism][10][n_pts_prism]."""
+    """fr_mesh_inspect: sizes, solution points, metric terms, face table and interface normals of
+    the host mesh build (no device work).  Points are [n_points][3]; metrics split into hexahedra
+    [n_elem][10][n_pts] and prisms [n_prism][10][n_pts_prism]; ef [n_elem][6]; normals
+    [n_iface + n_bface][4][(p+1)^2]."""
     lib = load()
     d, keep = _describe(desc, p)
     info = fr_mesh_info()
-    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None)
+    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None, None, None)
     if st != FR_OK:
         raise FRError(st, lib.fr_last_error(None).decode())
     x = np.zeros((info.n_points, 3))
     nh, nph = info.n_elem * 10 * info.n_pts, info.n_prism * 10 * info.n_pts_prism
     met = np.zeros(nh + nph)
-    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), C.c_void_p(x.ctypes.data), C.c_void_p(met.ctypes.data))
+    Nf = (p + 1) ** 2
+    ef = np.zeros((info.n_elem, 6), dtype=np.int32)
+    nrm = np.zeros((info.n_iface + info.n_bface, 4, Nf))
+    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), C.c_void_p(x.ctypes.data), C.c_void_p(met.ctypes.data),
+                             C.c_void_p(ef.ctypes.data), C.c_void_p(nrm.ctypes.data))
     if st != FR_OK:
         raise FRError(st, lib.fr_last_error(None).decode())
     del keep
     return {"n_elem": info.n_elem, "n_pts": info.n_pts, "n_iface": info.n_iface, "n_bface": info.n_bface,
             "n_prism": info.n_prism, "n_pts_prism": info.n_pts_prism, "n_points": info.n_points, "x": x,
             "metrics_hex": met[:nh].reshape(info.n_elem, 10, info.n_pts),
-            "metrics_prism": met[nh:].reshape(info.n_prism, 10, info.n_pts_prism)}
+            "metrics_prism": met[nh:].reshape(info.n_prism, 10, info.n_pts_prism), "ef": ef, "normals": nrm}
 
 
 class Mesh:

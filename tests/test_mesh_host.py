@@ -72,3 +72,48 @@ def test_inspect_reports_mesh_errors():
         fr.inspect(d, 2)
     with pytest.raises(fr.FRError, match="FR_EINVAL"):
         fr.inspect(I.hex_box_mesh((2, 2, 2)), 0)
+
+
+def _slot(code, a, b, N):
+    if code & 4:
+        a, b = b, a
+    if code & 1:
+        a = N - 1 - a
+    if code & 2:
+        b = N - 1 - b
+    return a + N * b
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_face_table_orientation_and_normals(p):
+    """Every element face point maps through the library's face table and orientation code to an
+    interface slot where (i) the stored side-0 normal equals the oracle's outward area-scaled
+    normal of that face point, negated on side 1, and (ii) both sides' oracle flux points
+    coincide (modulo the periodic translation); every slot of every interface is used once per
+    side."""
+    N, Nf = p + 1, (p + 1) ** 2
+    L = 2 * np.pi
+    d = I.hex_box_mesh((3, 3, 2), seed=10 + p, rotate=True, shuffle=True, perturb=0.1)
+    r = fr.inspect(d, p)
+    ora = HexFR(d, I.tgv_physics(), p)
+    n_if = r["n_iface"] + r["n_bface"]
+    seen = {}
+    for e in range(r["n_elem"]):
+        for f in range(6):
+            packed = int(r["ef"][e, f])
+            iface, side, code = packed >> 4, (packed >> 3) & 1, packed & 7
+            assert 0 <= iface < n_if
+            for q in range(Nf):
+                s = _slot(code, q % N, q // N, N)
+                want = ora.nf[e, f, q] * (1.0 if side == 0 else -1.0)
+                np.testing.assert_allclose(r["normals"][iface, :3, s], want, rtol=0, atol=1e-13)
+                assert abs(r["normals"][iface, 3, s] - np.linalg.norm(want)) <= 1e-13
+                key = (iface, s, side)
+                assert key not in seen
+                seen[key] = ora.xf[e, f, q]
+    for iface in range(r["n_iface"]):
+        for s in range(Nf):
+            dx = seen[(iface, s, 0)] - seen[(iface, s, 1)]
+            dx -= L * np.round(dx / L)
+            assert np.abs(dx).max() <= 1e-12
+    assert len(seen) == 2 * r["n_iface"] * Nf
