@@ -328,7 +328,8 @@ extern "C" fr_status fr_mesh_query(const fr_mesh *m, fr_mesh_info *info) {
 }
 
 extern "C" fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *info, double *xyz_host,
-                                     double *metrics_host, int32_t *ef_host, double *normals_host) {
+                                     double *metrics_host, int32_t *ef_host, double *normals_host,
+                                     int32_t *ef_prism_host, int32_t *tri_slot_host) {
   if (!desc || !info) return fail(nullptr, FR_EINVAL, "desc or info is NULL");
   if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
   if (desc->n_hex < 0 || desc->n_prism < 0 || desc->n_hex + desc->n_prism <= 0 || (desc->n_hex > 0 && !desc->hex) ||
@@ -365,6 +366,9 @@ extern "C" fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *inf
   }
   if (ef_host) std::memcpy(ef_host, h.ef.data(), h.ef.size() * sizeof(int32_t));
   if (normals_host) std::memcpy(normals_host, h.normals.data(), h.normals.size() * sizeof(double));
+  if (ef_prism_host) std::memcpy(ef_prism_host, h.ef_p.data(), h.ef_p.size() * sizeof(int32_t));
+  if (tri_slot_host && !h.tri_slot.empty())
+    std::memcpy(tri_slot_host, h.tri_slot.data(), h.tri_slot.size() * sizeof(int32_t));
   return FR_OK;
 }
 

@@ -106,7 +106,7 @@ SIGNATURES = {
     "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
     "fr_tri_basis": (C.c_int, [C.c_int32] + [C.POINTER(C.c_double)] * 4),
     "fr_transfer_matrix": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
-    "fr_mesh_inspect": (C.c_int, [C.c_void_p] * 6),
+    "fr_mesh_inspect": (C.c_int, [C.c_void_p] * 8),
 }
 
 _lib = None
@@ -223,7 +223,7 @@ def inspect(desc: MeshDesc, p: int) -> dict:
     lib = load()
     d, keep = _describe(desc, p)
     info = fr_mesh_info()
-    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None, None, None)
+    st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None, None, None, None, None)
     if st != FR_OK:
         raise FRError(st, lib.fr_last_error(None).decode())
     x = np.zeros((info.n_points, 3))
@@ -232,15 +232,19 @@ def inspect(desc: MeshDesc, p: int) -> dict:
     Nf = (p + 1) ** 2
     ef = np.zeros((info.n_elem, 6), dtype=np.int32)
     nrm = np.zeros((info.n_iface + info.n_bface, 4, Nf))
+    ef_p = np.zeros((info.n_prism, 5), dtype=np.int32)
+    tri_slot = np.zeros((6, (p + 1) * (p + 2) // 2), dtype=np.int32)
     st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), C.c_void_p(x.ctypes.data), C.c_void_p(met.ctypes.data),
-                             C.c_void_p(ef.ctypes.data), C.c_void_p(nrm.ctypes.data))
+                             C.c_void_p(ef.ctypes.data), C.c_void_p(nrm.ctypes.data),
+                             C.c_void_p(ef_p.ctypes.data), C.c_void_p(tri_slot.ctypes.data))
     if st != FR_OK:
         raise FRError(st, lib.fr_last_error(None).decode())
     del keep
     return {"n_elem": info.n_elem, "n_pts": info.n_pts, "n_iface": info.n_iface, "n_bface": info.n_bface,
             "n_prism": info.n_prism, "n_pts_prism": info.n_pts_prism, "n_points": info.n_points, "x": x,
             "metrics_hex": met[:nh].reshape(info.n_elem, 10, info.n_pts),
-            "metrics_prism": met[nh:].reshape(info.n_prism, 10, info.n_pts_prism), "ef": ef, "normals": nrm}
+            "metrics_prism": met[nh:].reshape(info.n_prism, 10, info.n_pts_prism), "ef": ef, "normals": nrm,
+            "ef_prism": ef_p, "tri_slot": tri_slot}
 
 
 class Mesh:

@@ -117,3 +117,42 @@ def test_face_table_orientation_and_normals(p):
             dx -= L * np.round(dx / L)
             assert np.abs(dx).max() <= 1e-12
     assert len(seen) == 2 * r["n_iface"] * Nf
+
+
+@pytest.mark.parametrize("curved", [False, True])
+@pytest.mark.parametrize("prisms", ["all", "checker"])
+def test_mixed_face_tables_orientation_and_normals(prisms, curved):
+    """As above on meshes with prisms (triangular faces through the triangle slot map, the
+    quadrilateral faces of prisms through the same orientation codes as hexahedra), straight and
+    curved, against the mixed-element oracle's face geometry."""
+    p = 3
+    N, Nf, Nt = p + 1, (p + 1) ** 2, (p + 1) * (p + 2) // 2
+    L = 2 * np.pi
+    d = (I.curved_box_mesh((2, 2, 2), prisms=prisms, warp=0.1, seed=6, rotate=True, shuffle=True) if curved else
+         I.hex_box_mesh((3, 2, 2), prisms=prisms, seed=6, rotate=True, shuffle=True, perturb=0.1))
+    r = fr.inspect(d, p)
+    ora = MixedFR(d, I.tgv_physics(), p)
+    seen = {}
+    tables = [(0, r["ef"], 6), (1, r["ef_prism"], 5)]
+    for t, ef, nfaces in tables:
+        for e in range(ef.shape[0]):
+            for f in range(nfaces):
+                packed = int(ef[e, f])
+                iface, side, code = packed >> 4, (packed >> 3) & 1, packed & 7
+                tri = t == 1 and f < 2
+                for q in range(Nt if tri else Nf):
+                    s = int(r["tri_slot"][code, q]) if tri else _slot(code, q % N, q // N, N)
+                    want = ora.nf[t][f][e][q] * (1.0 if side == 0 else -1.0)
+                    np.testing.assert_allclose(r["normals"][iface, :3, s], want, rtol=0,
+                                               atol=1e-12 * np.abs(want).max())
+                    key = (iface, s, side)
+                    assert key not in seen
+                    seen[key] = ora.xf[t][f][e][q]
+    pairs = 0
+    for (iface, s, side), x0 in seen.items():
+        if side == 0 and iface < r["n_iface"]:
+            dx = x0 - seen[(iface, s, 1)]
+            dx -= L * np.round(dx / L)
+            assert np.abs(dx).max() <= 1e-12
+            pairs += 1
+    assert pairs * 2 == sum(1 for k in seen if k[0] < r["n_iface"])
