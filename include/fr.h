@@ -166,9 +166,9 @@ fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintp
  * the hexahedra's face table ef_host [n_elem][6] (interface << 4 | side << 3 | orientation
  * code; faces ordered xi-, xi+, eta-, eta+, zeta-, zeta+; interfaces: the n_iface two-sided ones,
  * then the boundary faces) and normals_host [n_iface + n_bface][4][(p+1)^2]: side 0's outward
- * area-scaled normal at each flux point in side 0's point order, then its length.  A side-1 face
- * point (a, b) sits in slot a' + (p+1) b' with (a', b') = (b, a) if code & 4, then a' reversed if
- * code & 1 and b' reversed if code & 2.  Prisms: ef_prism_host [n_prism][5] packed the same way
+ * area-scaled normal at each flux point in side 0's point order, then its length.  A face point
+ * (a, b) of either side sits in slot a' + (p+1) b' with (a', b') = (b, a) if code & 4, then a'
+ * reversed if code & 1 and b' reversed if code & 2 (side 0 carries code 0).  Prisms: ef_prism_host [n_prism][5] packed the same way
  * (faces zeta-, zeta+ (triangles), then s = -1, r + s = 0, r = -1 (quadrilaterals, points
  * a + (p+1) b with a along the edge and b along zeta)); a triangular face's node q sits in slot
  * tri_slot_host[code][q] ([6][(p+1)(p+2)/2], code 0 the identity).  Call once with NULL arrays for
