@@ -144,6 +144,34 @@ def test_device_pointers_and_state_roundtrip():
     g.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_is_bit_identical(precision):
+    """Checkpoint at a step boundary: get_state after one RK44 step, a new mesh set_state from it
+    and two more steps give exactly the state of three uninterrupted steps (the FP64 state is the
+    whole RK state at a step boundary; the double-float copies are rebuilt from it the same way)."""
+    d = I.hex_box_mesh((3, 3, 2), seed=5, rotate=True, shuffle=True, perturb=0.1)
+    phys = I.tgv_physics(Ma=0.2, Re=300.0)
+    phys.precision = precision
+    ora = HexFR(d, I.tgv_physics(Ma=0.2, Re=300.0), 3)
+    Q0 = np.ascontiguousarray(I.tgv_state(ora.x, Ma=0.2, perturb=1e-2, seed=5))
+    dt = 0.5 * ora.max_dt(Q0, 0.3)
+    with fr.Mesh(d, phys, 3) as a:
+        a.set_state(Q0)
+        for s in range(3):
+            a.rk_step(s * dt, dt)
+        Qa = a.get_state()
+    with fr.Mesh(d, phys, 3) as b:
+        b.set_state(Q0)
+        b.rk_step(0.0, dt)
+        Q1 = b.get_state()
+    with fr.Mesh(d, phys, 3) as c:
+        c.set_state(Q1)
+        for s in range(1, 3):
+            c.rk_step(s * dt, dt)
+        Qc = c.get_state()
+    assert np.array_equal(Qa, Qc)
+
+
 def test_nonfinite_state_reported():
     d = I.hex_box_mesh((2, 2, 2))
     phys = I.tgv_physics()
