@@ -98,6 +98,11 @@ typedef struct {
   int32_t prism_nodes;          /* nodes per prism: 6 (0 means 6) or 18 (quadratic: the 6 corners,
                                    edge midpoints 01 12 20 34 45 53 03 14 25, centres of the
                                    quadrilateral faces 0143 1254 2035) */
+  const int8_t *elem_p;         /* NULL (every element at order p) or [n_hex + n_prism] per-element
+                                   orders, hexahedra first (host).  Only uniform orders are built:
+                                   an entry outside 1..7 gives FR_EINVAL, an entry that differs from p
+                                   FR_EUNSUPPORTED (interfaces between elements of different orders
+                                   are not built; ensembles of different orders run as batches) */
 } fr_mesh_desc;
 
 typedef struct {
@@ -137,6 +142,7 @@ typedef struct {
   int64_t n_prism;      /* prisms (after the n_elem hexahedra in every per-point array) */
   int32_t n_pts_prism;  /* solution points per prism: (p+1)(p+2)/2 triangle nodes x (p+1) */
   int64_t n_points;     /* all solution points: n_elem n_pts + n_prism n_pts_prism */
+  int32_t device;       /* CUDA device the mesh lives on (fr_mesh_query; -1 from fr_mesh_inspect) */
 } fr_mesh_info;
 
 /*
@@ -279,15 +285,18 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
  * residual) live in one static device array of 32 MiB that every device loading this library
  * holds until the process exits; no cudaMalloc, cudaFree or allocating library routine is
  * called.  Q_device (input, [n_elem][n_pts][5] canonical layout) and R_device (output, same
- * layout) are caller-owned device pointers; the mesh's own state is not read or changed.
+ * layout) are caller-owned device pointers on the mesh's device, which must be the current
+ * device (otherwise FR_EINVAL, and the mesh stays usable); the mesh's state arrays are not read
+ * or changed (its geometry and connectivity are read).
  * Meshes whose intermediates exceed 32 MiB (8 bytes x (45 n_iface_total N^2 + 5 n_elem N^3),
  * N = p + 1) are rejected with FR_EINVAL and a message giving both sizes.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) — make that first call
  * before any stream capture.  All calls share the one array and it keeps the last call's
  * contents; nothing in it needs to start at zero, but calls whose work overlaps on the GPU
  * (other streams, other meshes, other threads) race on it: serialise them.  Work is enqueued
- * on the mesh's stream and the call returns without synchronising.  FP64 hexahedral meshes only
- * (FR_EUNSUPPORTED for FR_PREC_MIXED or a mesh with prisms).
+ * on the mesh's stream and the call returns without synchronising.  FP64 hexahedral meshes with
+ * the DG-equivalent correction (c = 0) and without the eddy-viscosity closure only
+ * (FR_EUNSUPPORTED for FR_PREC_MIXED, a mesh with prisms, c != 0 or the closure switched on).
  */
 fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, double *R_device);
 

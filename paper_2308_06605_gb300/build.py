@@ -42,9 +42,17 @@ def build(verbose: bool = False, extra=()) -> str:
     common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
+    # An object is rebuilt when it is older than its source or than any header (headers are shared).
+    headers = [os.path.join(d, f) for d in (CSRC, os.path.join(ROOT, "include")) for f in os.listdir(d)
+               if f.endswith((".h", ".hpp", ".cuh"))]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(unit):
         src, tag, flags = unit if isinstance(unit, tuple) else (unit, "", [])
         obj = os.path.join(objdir, src + (("." + tag) if tag else "") + ".o")
+        if (not verbose and not extra and os.path.exists(obj) and os.path.exists(LIB)
+                and os.path.getmtime(obj) > max(newest_header, os.path.getmtime(os.path.join(CSRC, src)))):
+            return obj
         cmd = common + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []

@@ -133,6 +133,28 @@ static fr_status dalloc(fr_mesh *m, T **p, size_t count) {
   return FR_OK;
 }
 
+// Per-element orders (fr_mesh_desc.elem_p): NULL, or every entry in 1..7 and equal to p.
+static fr_status check_elem_orders(const fr_mesh_desc *desc) {
+  if (!desc->elem_p) return FR_OK;
+  const int64_t n = desc->n_hex + desc->n_prism;
+  for (int64_t e = 0; e < n; ++e)
+    if (desc->elem_p[e] < 1 || desc->elem_p[e] > 7) {
+      char buf[120];
+      snprintf(buf, sizeof buf, "elem_p[%lld] = %d is outside 1..7", (long long)e, (int)desc->elem_p[e]);
+      return fail(nullptr, FR_EINVAL, buf);
+    }
+  for (int64_t e = 0; e < n; ++e)
+    if (desc->elem_p[e] != desc->p) {
+      char buf[200];
+      snprintf(buf, sizeof buf,
+               "elem_p[%lld] = %d differs from p = %d: meshes of mixed orders (p-nonconforming interfaces) are "
+               "not built",
+               (long long)e, (int)desc->elem_p[e], (int)desc->p);
+      return fail(nullptr, FR_EUNSUPPORTED, buf);
+    }
+  return FR_OK;
+}
+
 extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
                                     fr_mesh **out) {
   if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
@@ -147,6 +169,7 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
   if (desc->n_bc < 0 || (desc->n_bc > 0 && !desc->bc) || desc->n_periodic < 0 ||
       (desc->n_periodic > 0 && !desc->periodic))
     return fail(nullptr, FR_EINVAL, "bad boundary-condition or periodic arrays");
+  if (fr_status so = check_elem_orders(desc); so != FR_OK) return so;
   if (!(phys->gamma > 1.0) || !(phys->R > 0.0) || !(phys->mu >= 0.0) || !(phys->Pr > 0.0) ||
       !(phys->br2_eta >= 0.0))
     return fail(nullptr, FR_EINVAL, "bad physical parameters");
@@ -324,6 +347,7 @@ extern "C" fr_status fr_mesh_query(const fr_mesh *m, fr_mesh_info *info) {
   info->n_prism = m->host.Ep;
   info->n_pts_prism = m->host.Npp;
   info->n_points = m->host.E * m->host.Np + m->host.Ep * m->host.Npp;
+  info->device = m->device;
   return FR_OK;
 }
 
@@ -340,6 +364,7 @@ extern "C" fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *inf
   if (desc->n_bc < 0 || (desc->n_bc > 0 && !desc->bc) || desc->n_periodic < 0 ||
       (desc->n_periodic > 0 && !desc->periodic))
     return fail(nullptr, FR_EINVAL, "bad boundary-condition or periodic arrays");
+  if (fr_status so = check_elem_orders(desc); so != FR_OK) return so;
   HostMesh h;
   std::string err;
   fr_status st;
@@ -359,6 +384,7 @@ extern "C" fr_status fr_mesh_inspect(const fr_mesh_desc *desc, fr_mesh_info *inf
   info->n_prism = h.Ep;
   info->n_pts_prism = h.Npp;
   info->n_points = h.E * h.Np + h.Ep * h.Npp;
+  info->device = -1;
   if (xyz_host) std::memcpy(xyz_host, h.xsol.data(), h.xsol.size() * sizeof(double));
   if (metrics_host) {
     std::memcpy(metrics_host, h.metrics.data(), h.metrics.size() * sizeof(double));

@@ -50,6 +50,10 @@ extern "C" fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, d
   if (dev.Ep > 0) return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: hexahedral meshes only");
   if (phys.vc_basis)
     return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: DG-equivalent correction (c = 0) only");
+  // The closure writes each element's eddy viscosity into a mesh-owned array, which would make
+  // this call change the mesh; it is refused instead.
+  if (phys.closure)
+    return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: meshes without the eddy-viscosity closure only");
   const size_t Nf = (size_t)dev.Nf;
   const size_t n_qtr = (size_t)dev.n_if * 2 * 5 * Nf;
   const size_t n_gtr = (size_t)dev.n_if * 2 * 15 * Nf;
@@ -65,7 +69,13 @@ extern "C" fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, d
   }
   int current = -1;
   cudaError_t e = cudaGetDevice(&current);
-  if (e == cudaSuccess && current != device) e = cudaErrorInvalidDevice;
+  if (e == cudaSuccess && current != device) {
+    // A caller error, not a failed CUDA call: nothing ran, so the mesh stays usable.
+    char buf[160];
+    snprintf(buf, sizeof buf, "fr_residual_static: current device %d differs from the mesh's device %d", current,
+             device);
+    return frx_mesh_fail(mesh, FR_EINVAL, buf);
+  }
   double *base = nullptr;
   if (e == cudaSuccess) e = scratch_address(device, &base);
   if (e != cudaSuccess)

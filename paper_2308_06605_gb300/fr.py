@@ -48,7 +48,8 @@ class fr_mesh_desc(C.Structure):
                 ("n_bc", C.c_int32), ("bc", C.POINTER(fr_bc)),
                 ("n_periodic", C.c_int32), ("periodic", C.POINTER(fr_periodic)),
                 ("n_prism", C.c_int64), ("prism", C.POINTER(C.c_int64)),
-                ("hex_nodes", C.c_int32), ("prism_nodes", C.c_int32)]
+                ("hex_nodes", C.c_int32), ("prism_nodes", C.c_int32),
+                ("elem_p", C.POINTER(C.c_int8))]
 
 
 class fr_physics(C.Structure):
@@ -65,7 +66,8 @@ class fr_batch_info(C.Structure):
 class fr_mesh_info(C.Structure):
     _fields_ = [("n_elem", C.c_int64), ("p", C.c_int32), ("n_pts", C.c_int32),
                 ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("device_bytes", C.c_int64),
-                ("n_prism", C.c_int64), ("n_pts_prism", C.c_int32), ("n_points", C.c_int64)]
+                ("n_prism", C.c_int64), ("n_pts_prism", C.c_int32), ("n_points", C.c_int64),
+                ("device", C.c_int32)]
 
 
 # Exported functions: name -> (restype, argtypes)
@@ -186,8 +188,9 @@ def probe_fma(precision: int = 0, iters: int = 20000) -> float:
     return v.value
 
 
-def _describe(desc: MeshDesc, p: int):
-    """The C mesh description of `desc` at order p, and the arrays it points into (keep alive)."""
+def _describe(desc: MeshDesc, p: int, elem_p=None):
+    """The C mesh description of `desc` at order p, and the arrays it points into (keep alive).
+    elem_p: optional per-element orders (hexahedra first); the library builds uniform orders only."""
     xyz = np.ascontiguousarray(desc.xyz, dtype=np.float64)
     hexa = np.asarray(desc.hex, dtype=np.int64)
     hexa = np.ascontiguousarray(hexa if hexa.ndim == 2 else hexa.reshape(-1, 8))    # 8 or 27 nodes each
@@ -212,16 +215,23 @@ def _describe(desc: MeshDesc, p: int):
                      n_bc=len(desc.bcs), bc=bcs, n_periodic=len(desc.periodic), periodic=per,
                      n_prism=pri.shape[0], prism=_ptr(pri, C.c_int64),
                      hex_nodes=hexa.shape[1], prism_nodes=pri.shape[1])
-    return d, [xyz, hexa, pri, bn, bt, bcs, per]
+    keep = [xyz, hexa, pri, bn, bt, bcs, per]
+    if elem_p is not None:
+        ep = np.ascontiguousarray(elem_p, dtype=np.int8)
+        if ep.size != hexa.shape[0] + pri.shape[0]:
+            raise ValueError(f"elem_p has {ep.size} entries, the mesh has {hexa.shape[0] + pri.shape[0]} elements")
+        d.elem_p = _ptr(ep, C.c_int8)
+        keep.append(ep)
+    return d, keep
 
 
-def inspect(desc: MeshDesc, p: int) -> dict:
+def inspect(desc: MeshDesc, p: int, elem_p=None) -> dict:
     """fr_mesh_inspect: sizes, solution points, metric terms, face table and interface normals of
     the host mesh build (no device work).  Points are [n_points][3]; metrics split into hexahedra
     [n_elem][10][n_pts] and prisms [n_prism][10][n_pts_prism]; ef [n_elem][6]; normals
     [n_iface + n_bface][4][(p+1)^2]."""
     lib = load()
-    d, keep = _describe(desc, p)
+    d, keep = _describe(desc, p, elem_p)
     info = fr_mesh_info()
     st = lib.fr_mesh_inspect(C.byref(d), C.byref(info), None, None, None, None, None, None)
     if st != FR_OK:
@@ -254,11 +264,11 @@ class Mesh:
     are [n_points][5], the hexahedral points first (see `split`).
     """
 
-    def __init__(self, desc: MeshDesc, phys: Physics, p: int, stream: int = 0):
+    def __init__(self, desc: MeshDesc, phys: Physics, p: int, stream: int = 0, elem_p=None):
         lib = load()
         self._lib = lib
         self._keep = []
-        d, keep = _describe(desc, p)
+        d, keep = _describe(desc, p, elem_p)
         self._keep += keep
         ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
                         viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision,
@@ -274,6 +284,7 @@ class Mesh:
         self.n_iface, self.n_bface, self.device_bytes = info.n_iface, info.n_bface, info.device_bytes
         self.n_prism, self.n_pts_prism, self.n_points = info.n_prism, info.n_pts_prism, info.n_points
         self.shape = (self.n_elem, self.n_pts, 5) if self.n_prism == 0 else (self.n_points, 5)
+        self.device = info.device
 
     def _check(self, st):
         if st != FR_OK:
@@ -315,6 +326,12 @@ class Mesh:
         r, wr = _data_ptr(R_device)
         if wq != FR_DEVICE or wr != FR_DEVICE:
             raise ValueError("fr_residual_static takes device tensors")
+        n = int(np.prod(self.shape))
+        for name, x in (("Q_device", Q_device), ("R_device", R_device)):
+            if x.numel() != n:
+                raise ValueError(f"fr_residual_static: {name} has {x.numel()} values, the mesh's state has {n}")
+            if x.device.index != self.device:
+                raise ValueError(f"fr_residual_static: {name} is on cuda:{x.device.index}, the mesh on cuda:{self.device}")
         self._check(self._lib.fr_residual_static(self._h, q, r))
 
     def rk_stage(self, stage: int, t: float, dt: float, scheme: int = FR_RK44):

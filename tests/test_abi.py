@@ -115,3 +115,24 @@ def test_correction_parameter_checked_before_device_work(lib):
         assert st == fr.FR_EINVAL and "correction parameter" in msg, (c, msg)
     st, msg = _create(I.hex_box_mesh((2, 2, 2), prisms="checker"), I.tgv_physics(), 2, vcjh_c=0.01)
     assert st == fr.FR_EUNSUPPORTED and "hexahedral" in msg
+
+
+def test_per_element_orders_uniform_only(lib):
+    """fr_mesh_desc.elem_p: uniform orders are accepted, an order outside 1..7 is FR_EINVAL and
+    differing orders are FR_EUNSUPPORTED, all decided on the host before any device work."""
+    d = I.hex_box_mesh((2, 2, 2))
+    n = 8
+    info = fr.inspect(d, 3, elem_p=np.full(n, 3, np.int8))
+    assert info["n_elem"] == n
+    ep = np.full(n, 3, np.int8)
+    ep[5] = 4
+    for call in (lambda: fr.inspect(d, 3, elem_p=ep), lambda: fr.Mesh(d, I.tgv_physics(), 3, elem_p=ep)):
+        with pytest.raises(fr.FRError) as ei:
+            call()
+        assert ei.value.status == fr.FR_EUNSUPPORTED and "elem_p[5] = 4" in str(ei.value)
+    ep[5] = 9
+    with pytest.raises(fr.FRError) as ei:
+        fr.inspect(d, 3, elem_p=ep)
+    assert ei.value.status == fr.FR_EINVAL and "outside 1..7" in str(ei.value)
+    with pytest.raises(ValueError):
+        fr.inspect(d, 3, elem_p=np.full(n - 1, 3, np.int8))
