@@ -167,10 +167,13 @@ def run_reference(args):
     t0 = time.perf_counter()
     rate, sample, cores = oracle_rate(max_steps=args.steps)
     el = time.perf_counter() - t0
+    cfg = dict(config("mixed"))
+    cfg["reference_sample"] = ("each step: one oracle RK44 step on the 8^3 periodic hex TGV at p=4 (64 000 points; "
+                               "same case, order and per-point work as the 64^3 workload, 1/512 of its points)")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -431,7 +434,7 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    from paper_2308_06605_gb300 import fr
+    from paper_2308_06605_gb300 import fr, perfmodel
     if not os.path.exists(fr.LIB_PATH):
         from paper_2308_06605_gb300 import build as B
         B.build()
@@ -474,7 +477,6 @@ def run_ours(args):
     fp32_peak = fr.probe_fma(1, 200000)
     df_peak = fp32_peak / DF_FP32_FLOPS_PER_FLOP
     dom = max(k_mx, key=lambda n_: k_mx[n_]["share"])
-    from paper_2308_06605_gb300 import perfmodel
     fl = perfmodel.flops_per_point(ORDER)
     by = perfmodel.bytes_per_point(ORDER)
     ach = k_mx[dom]["gflops"] * 1e9
@@ -503,11 +505,19 @@ def run_ours(args):
     cmx.mesh.get_state(out=Out)
     torch.cuda.synchronize()
     barrier()
+    phase = [0.0, 0.0, 0.0]          # host wall time of set_state, the four stages, get_state
     te0 = time.perf_counter()
     for _ in range(k_e2e):
-        cmx.mesh.set_state(Qh)
-        cmx.step()
-        cmx.mesh.get_state(out=Out)
+        t0 = time.perf_counter()
+        cmx.mesh.set_state(Qh)        # returns after the host buffer has been read
+        t1 = time.perf_counter()
+        cmx.step()                    # the last stage reads the non-finite flag back (synchronises)
+        t2 = time.perf_counter()
+        cmx.mesh.get_state(out=Out)   # returns after the result is in host memory
+        t3 = time.perf_counter()
+        phase[0] += t1 - t0
+        phase[1] += t2 - t1
+        phase[2] += t3 - t2
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - te0)
     # Plain copy rates of the same pinned buffers (context for the end-to-end number).
@@ -525,7 +535,9 @@ def run_ours(args):
     del Qd
     e2e = {"value": world * n_pts * 4 * k_e2e / te, "unit": UNIT,
            "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8),
-           "copy_rates_gbs": rates}
+           "copy_rates_gbs": rates,
+           "phase_ms_per_step": {"set_state": 1e3 * phase[0] / k_e2e, "stages": 1e3 * phase[1] / k_e2e,
+                                 "get_state": 1e3 * phase[2] / k_e2e}}
     cmx.close()
     del Qh, Out
 
@@ -554,6 +566,15 @@ def run_ours(args):
                 c.step()
                 ms = c.timed(2)
                 row[prec] = n ** 3 * (p + 1) ** 3 * 4 * 2 / (ms * 1e-3)
+                # Per-kernel CUDA-event times and each kernel's fraction of the arithmetic peak of
+                # its precision (FP64: the DFMA rate; double-float: the FP32 FMA rate / 18).
+                peak = fp64_peak if prec == "fp64" else df_peak
+                k = c.kernels(2, p)
+                row[prec + "_kernels"] = {name: {"avg_ms": v["avg_ms"], "share": v["share"],
+                                                 "frac_of_alu_peak": v["gflops"] * 1e9 / peak if v["gflops"] else None}
+                                          for name, v in k.items()}
+                row[prec + "_volume_frac"] = k["volume"]["gflops"] * 1e9 / peak
+                row[prec + "_step_frac"] = (sum(perfmodel.flops_per_point(p).values()) * row[prec] / peak)
                 c.close()
             sweep[f"p{p}"] = row
 
@@ -574,6 +595,14 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{cores} replicas at once, one per host core, each: {sample}",
                                 "single_thread": {"value": r1, "unit": UNIT, "cores": 1, "sample": sample1}}
+        # The small benchmark case in full (8^3 hexahedra, p = 3, 10 RK44 steps) and one RK44 step
+        # per order on 4^3 meshes (the oracle's dense operators make larger sweeps take minutes).
+        r_c1, s_c1, _ = oracle_rate(max_steps=10, n=8, p=3)
+        line["cpu_baseline"]["tgv_8cube_p3_10_steps"] = {"value": r_c1, "unit": UNIT, "cores": 1, "sample": s_c1}
+        line["cpu_baseline"]["p_sweep_4cube"] = {}
+        for (_, pp) in SWEEP:
+            r_p, s_p, _ = oracle_rate(max_steps=1, n=4, p=pp)
+            line["cpu_baseline"]["p_sweep_4cube"][f"p{pp}"] = {"value": r_p, "unit": UNIT, "cores": 1, "sample": s_p}
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:

@@ -74,3 +74,22 @@ def vcjh_c(p, which):
     if which == "big":
         return 10.0 * vcjh_c(p, "hu")
     raise ValueError(which)
+
+
+def load_g13_reference():
+    """The 40-digit low-Mach residual fixture (tests/golden/g13_tgv_ma01_reference.txt):
+    {(p, n1): (Q [n1][N^3][5], R [n1][N^3][5])}."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "g13_tgv_ma01_reference.txt")
+    rows = np.loadtxt(path, comments="#")
+    out = {}
+    for p, n1 in sorted({(int(r[0]), int(r[1])) for r in rows}):
+        sel = rows[(rows[:, 0] == p) & (rows[:, 1] == n1)]
+        Np = (p + 1) ** 3
+        Q = np.zeros((n1, Np, 5))
+        R = np.zeros((n1, Np, 5))
+        for r in sel:
+            e, m = int(r[2]), int(r[3])
+            Q[e, m] = r[4:9]
+            R[e, m] = r[9:14]
+        out[(p, n1)] = (Q, R)
+    return out

@@ -1,0 +1,56 @@
+"""Evidence for the per-entry residual tolerance (the reading of "relative error per residual
+entry"): at Ma 0.1 the energy entries of Eq. 3 are sums of large terms that cancel, so even the
+FP64 oracle cannot reproduce them to 1e-12 of their own size, while its error against an exact
+(40-digit) evaluation stays a few ulps of the entry's magnitude scale S (the sum of the
+magnitudes of the terms forming the entry).
+
+The 40-digit values come from `oracle.weakdg_mp` (an independent weak-form DG restatement),
+stored in tests/golden/g13_tgv_ma01_reference.txt by tests/golden/make_g13_reference.py.
+"""
+import numpy as np
+import pytest
+
+from oracle.hexfr import HexFR
+from paper_2308_06605_gb300 import inputs as I
+
+from helpers import load_g13_reference
+
+
+def _case_setup(p, n1):
+    """The fixture's mesh and physics (as in tests/golden/make_g13_reference.py)."""
+    L = 2 * np.pi
+    return I.hex_box_mesh((n1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(L, L, L)), I.tgv_physics(Ma=0.1, Re=1600.0)
+
+
+@pytest.mark.parametrize("case", [(2, 2), (3, 1)])
+def test_fp64_oracle_error_is_ulps_of_magnitude_scale_not_of_entry(case):
+    p, n1 = case
+    Q, Rx = load_g13_reference()[case]
+    desc, phys = _case_setup(p, n1)
+    ora = HexFR(desc, phys, p)
+    R = ora.residual(Q)
+    S = ora.residual(Q, magnitude=True)
+    err = np.abs(R - Rx)
+    per_S = (err / S).reshape(-1, 5).max(axis=0)
+    per_R = (err / np.abs(Rx)).reshape(-1, 5).max(axis=0)
+    # Error of the FP64 evaluation: a few ulps of S in every variable ...
+    assert np.all(per_S <= 1e-14), per_S
+    # ... but above 1e-12 of |R| at the cancelling entries (no FP64 order can do better than
+    # its own rounding of the large terms), so a bar relative to |R| alone is unattainable.
+    assert per_R.max() > 1e-12, per_R
+    # The cancellation itself: |R| / S reaches below 1e-4 in the energy equation.
+    assert (np.abs(Rx) / S).reshape(-1, 5)[:, 4].min() < 1e-4
+
+
+@pytest.mark.slow
+def test_fixture_reproduces_from_the_40_digit_oracle():
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.weakdg_mp import brute_force_residual
+    ref = load_g13_reference()
+    for (p, n1), (Q, Rx) in ref.items():
+        desc, phys = _case_setup(p, n1)
+        L = 2 * np.pi
+        R = brute_force_residual(Q, p, n1, [[1, 0, 0], [0, 1, 0], [0, 0, 1]], (L / n1, L, L),
+                                 mpmath.mp.mpf(14) / 10, mpmath.mp.mpf(phys.R), mpmath.mp.mpf(phys.mu),
+                                 mpmath.mp.mpf(71) / 100, 6, True)
+        np.testing.assert_array_equal(R, Rx)

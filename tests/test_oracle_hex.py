@@ -167,21 +167,24 @@ def test_tgv_energy_and_dissipation():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_isentropic_vortex_convergence(p):
-    """Euler, exact advected vortex: L2 error after a short time converges at >= p + 1 - 0.2."""
+    """Euler, exact advected vortex: L2 error after a short time converges at >= p + 1 - 0.2.
+    At p = 4, 5 the time step shrinks (CFL 0.05, 0.03 instead of 0.1) so that RK44's
+    fourth-order error stays below the spatial error (measured rates 4.8, 6.2)."""
     phys = I.Physics(gamma=1.4, R=1.0, mu=0.0, viscous=0)
     Lh = 7.0                      # periodic images of the Gaussian tail are below 1e-10
-    levels = {1: (8, 16, 32), 2: (8, 16, 32), 3: (6, 12, 24)}[p]
+    levels = {1: (8, 16, 32), 2: (8, 16, 32), 3: (6, 12, 24), 4: (4, 8, 16), 5: (4, 8, 16)}[p]
+    cfl = {4: 0.05, 5: 0.03}.get(p, 0.1)
     errs = []
-    t_end = 0.2
+    t_end = 0.1 if p == 5 else 0.2
     for n in levels:
         h = 2 * Lh / n
         d = I.hex_box_mesh((n, n, 1), lo=(-Lh, -Lh, 0.0), hi=(Lh, Lh, h))
         m = HexFR(d, phys, p)
         kw = dict(beta=5.0, Ma=0.5, centre=(0.0, 0.0), period=(2 * Lh, 2 * Lh))
         Q = I.isentropic_vortex_state(m.x, 0.0, **kw)
-        nsteps = int(np.ceil(t_end / (0.1 * h / (p + 1))))
+        nsteps = int(np.ceil(t_end / (cfl * h / (p + 1))))
         dt = t_end / nsteps
         for s in range(nsteps):
             Q = m.rk44_step(Q, s * dt, dt)
