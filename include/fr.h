@@ -55,6 +55,7 @@ enum {                                                     /* explicit Runge–K
   FR_SSPRK33 = 1,   /* three-stage third-order SSP (Shu–Osher form), SSP coefficient 1 */
   FR_SSPRK104 = 2   /* Ketcheson's ten-stage fourth-order SSP scheme (two registers), coefficient 6 */
 };
+enum { FR_RESIDUAL_ONLY = -1 };                            /* fr_part_phase: write R, no stage update */
 enum {                                                     /* boundary-condition kinds */
   FR_BC_WALL_ISOTHERMAL = 1,  /* params[0] = wall temperature */
   FR_BC_CHAR_INFLOW = 2,      /* params = total pressure, total temperature, flow direction (3) */
@@ -273,6 +274,82 @@ fr_status fr_rk_stage(fr_mesh *mesh, int32_t scheme, int32_t stage, double t, do
  * h_e = volume^(1/3): an explicit-stability estimate (not specified by the paper).
  */
 fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
+
+/*
+ * Domain decomposition (paper, section "Pre-processing": the mesh is distributed over processes,
+ * the faces on partition boundaries are paired (Algorithm 2, "MatchMPIFaces"), and every step
+ * exchanges the data of those faces).  Hexahedral meshes.  A part holds its own elements and
+ * every interface touching them; an interface shared with another part (a halo interface) keeps
+ * the global mesh's record, so each part writes its own side's traces and receives the other
+ * side's from the peer.  BR2 and LDG are compact, so one exchange of solution traces (before the
+ * volume kernel needs the jumps) and one of gradient traces (before the interface fluxes) per
+ * stage make each part's residual equal to the residual of the whole mesh restricted to the part.
+ */
+typedef struct {
+  int64_t n_elem;       /* elements of the part */
+  int64_t n_iface;      /* two-sided interfaces touching them (including halo interfaces) */
+  int64_t n_bface;      /* boundary-condition faces of the part */
+  int32_t n_peers;      /* parts sharing interfaces with this one */
+  int64_t n_halo;       /* halo interfaces */
+} fr_part_info;
+
+/*
+ * fr_partition — host only: recursive coordinate bisection of the element centroids (mean of the
+ * corner vertices) into n_parts parts of near-equal solution-point count; each cut is across the
+ * longest extent, ties ordered by element index, so the result is deterministic.  part: [n_hex +
+ * n_prism] caller-owned host array, written with ids 0..n_parts-1 (elements in input order).
+ * FR_EINVAL for n_parts < 1 or > the element count, FR_EMESH for a vertex id out of range.
+ */
+fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part);
+
+/*
+ * fr_part_inspect — host only: what fr_mesh_create_part would build for part `rank` (no device
+ * work).  info is filled; each array may be NULL: peers [n_peers] (ascending), peer_begin
+ * [n_peers + 1] (halo entries of peer k are [peer_begin[k], peer_begin[k+1])), gid [n_halo] (the
+ * global interface number of each halo entry; ascending within a peer), elem_global [n_elem] (the
+ * input index of each local element; local elements are in input order).  The halo entries a part
+ * sends to a peer and those the peer receives from it are the same interfaces in the same order.
+ * FR_EUNSUPPORTED for meshes with prisms; FR_EINVAL for a negative part id or an empty part.
+ */
+fr_status fr_part_inspect(const fr_mesh_desc *desc, const int32_t *part, int32_t rank, fr_part_info *info,
+                          int32_t *peers, int64_t *peer_begin, int64_t *gid, int64_t *elem_global);
+
+/*
+ * fr_mesh_create_part — the mesh of part `rank` of the partition `part` ([n_hex] host array, ids
+ * >= 0), on the current device.  States, residuals and fr_solution_points are in the part's local
+ * element order (elem_global of fr_halo_query maps them to input indices).  A part without halo
+ * interfaces behaves like fr_mesh_create; a part with them runs its stages through fr_part_phase
+ * (fr_residual, fr_rk_stage, fr_residual_static and fr_batch_create return FR_EUNSUPPORTED for it)
+ * and refuses the eddy-viscosity closure (the remote elements' eddy viscosity is not exchanged).
+ * fr_max_dt is the part's own minimum (reduce it over the parts).
+ */
+fr_status fr_mesh_create_part(const fr_mesh_desc *desc, const fr_physics *phys, const int32_t *part, int32_t rank,
+                              uintptr_t stream, fr_mesh **out);
+
+/* fr_halo_query — the part's sizes and halo lists, as fr_part_inspect (any array may be NULL). */
+fr_status fr_halo_query(const fr_mesh *mesh, fr_part_info *info, int32_t *peers, int64_t *peer_begin, int64_t *gid,
+                        int64_t *elem_global);
+
+/*
+ * fr_part_phase — one third of a residual evaluation or RK stage of a part, enqueued on the mesh's
+ * stream.  Halo buffers are caller-owned device arrays of n_halo entries, entry k holding
+ * nv x (p+1)^2 8-byte values (nv = 5 solution, 15 gradient; FP64 or, on FR_PREC_MIXED meshes,
+ * double-float pairs: the caller only moves them).  Between phases the caller moves the entries of
+ * peer k ([peer_begin[k], peer_begin[k+1]) of its send buffer) into that peer's receive buffer at
+ * the peer's entries for this part (same count, same order), after the phase's work is complete
+ * on the stream.
+ *   phase 0: face traces and boundary states; writes the solution halo to send_device (nv = 5).
+ *   phase 1: reads the received solution halo from recv_device, runs the volume kernel, writes the
+ *            gradient halo to send_device (nv = 15).
+ *   phase 2: reads the received gradient halo from recv_device, interface and boundary fluxes,
+ *            correction; scheme = FR_RESIDUAL_ONLY writes R to R_device ([n_elem][n_pts][5] device)
+ *            at the current state, otherwise applies stage `stage` of the scheme with step dt as
+ *            fr_rk_stage does (FR_ENONFINITE at the last stage).
+ * A part without halo interfaces may pass NULL buffers.  FR_EINVAL for a bad phase, stage, scheme
+ * or NULL pointer.
+ */
+fr_status fr_part_phase(fr_mesh *mesh, int32_t phase, int32_t scheme, int32_t stage, double t, double dt,
+                        const double *recv_device, double *send_device, double *R_device);
 
 /*
  * fr_residual_static — the residual of a caller-supplied state, computed without allocating

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fr_device.hpp"
+#include "fr_part.hpp"
 
 using namespace frx;
 
@@ -31,6 +32,10 @@ struct fr_mesh {
   // Eddy-viscosity closure (allocated by fr_set_closure).
   void *d_cw = nullptr;
   float *d_cscale = nullptr;
+  // Domain decomposition (fr_mesh_create_part): halo lists and the device slot codes.
+  bool is_part = false;
+  HaloLists halo;
+  int64_t *d_halo = nullptr;   // [n_halo] 2 I + side
   // Instrumentation: one event set per recorded residual evaluation.
   bool profiling = false;
   std::vector<PhaseEvents> ev_pool;
@@ -91,6 +96,14 @@ static fr_status check_mesh(fr_mesh *m) {
   return FR_OK;
 }
 
+// A part of a domain-decomposed mesh that shares interfaces with other parts needs their traces
+// between the phases of a stage (fr_part_phase); whole-stage calls would read stale halo slots.
+static fr_status refuse_halo(fr_mesh *m, const char *what) {
+  if (m->is_part && !m->halo.iface.empty())
+    return fail(m, FR_EUNSUPPORTED, std::string(what) + ": this part shares interfaces with other parts; use fr_part_phase");
+  return FR_OK;
+}
+
 static void release(fr_mesh *m) {
   DevMesh &d = m->dev;
   double *dbl[] = {d.Q,  d.Un, d.acc, d.Rpart, d.metrics, d.liftfac, d.normals, d.Qtr,
@@ -112,6 +125,8 @@ static void release(fr_mesh *m) {
   if (m->d_sigma) cudaFree(m->d_sigma);
   if (m->d_qref) cudaFree(m->d_qref);
   if (m->d_vc) cudaFree(m->d_vc);
+  if (m->d_halo) cudaFree(m->d_halo);
+  m->d_halo = nullptr;
   m->d_sigma = m->d_qref = nullptr;
   m->d_cw = nullptr;
   m->d_cscale = nullptr;
@@ -155,10 +170,8 @@ static fr_status check_elem_orders(const fr_mesh_desc *desc) {
   return FR_OK;
 }
 
-extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
-                                    fr_mesh **out) {
-  if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
-  *out = nullptr;
+// Checks of a mesh description and physics before anything is allocated.
+static fr_status validate_create(const fr_mesh_desc *desc, const fr_physics *phys) {
   if (!desc || !phys) return fail(nullptr, FR_EINVAL, "desc or phys is NULL");
   if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
   if (desc->n_hex < 0 || desc->n_prism < 0 || desc->n_hex + desc->n_prism <= 0 || (desc->n_hex > 0 && !desc->hex) ||
@@ -201,6 +214,16 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
       return fail(nullptr, FR_EINVAL, "Dirichlet density must be positive");
   }
 
+  return FR_OK;
+}
+
+static fr_status finish_create(fr_mesh *m, const fr_physics *phys, uintptr_t stream, fr_mesh **out);
+
+extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *phys, uintptr_t stream,
+                                    fr_mesh **out) {
+  if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (fr_status sv = validate_create(desc, phys); sv != FR_OK) return sv;
   fr_mesh *m = new (std::nothrow) fr_mesh();
   if (!m) return fail(nullptr, FR_ENOMEM, "host allocation failed");
   std::string err;
@@ -215,6 +238,13 @@ extern "C" fr_status fr_mesh_create(const fr_mesh_desc *desc, const fr_physics *
     delete m;
     return fail(nullptr, st, err);
   }
+  return finish_create(m, phys, stream, out);
+}
+
+// Device set-up of a mesh whose host part (m->host) is built: physics constants, buffers,
+// uploads.  Takes ownership of m (freed on failure).
+static fr_status finish_create(fr_mesh *m, const fr_physics *phys, uintptr_t stream, fr_mesh **out) {
+  fr_status st = FR_OK;
   m->phys = *phys;
   m->stream = (cudaStream_t)stream;
   DevPhys &dp = m->dphys;
@@ -442,6 +472,7 @@ extern "C" fr_status fr_residual(fr_mesh *m, double t, double *R, int32_t where)
   (void)t;
   fr_status st = check_mesh(m);
   if (st) return st;
+  if ((st = refuse_halo(m, "fr_residual"))) return st;
   if (!R || (where != FR_HOST && where != FR_DEVICE)) return fail(m, FR_EINVAL, "bad residual pointer or where");
   double *dst = (where == FR_DEVICE) ? R : m->dev.acc;   // acc is free outside an RK step
   FR_CUDA(m, launch_residual(m->dev, m->dphys, MODE_RESIDUAL, 0, 0.0, dst, m->stream, next_events(m)));
@@ -457,6 +488,7 @@ extern "C" fr_status fr_rk_stage(fr_mesh *m, int32_t scheme, int32_t stage, doub
   (void)t;
   fr_status st = check_mesh(m);
   if (st) return st;
+  if ((st = refuse_halo(m, "fr_rk_stage"))) return st;
   int mode, last;
   switch (scheme) {
     case FR_RK44: mode = MODE_RK; last = 3; break;
@@ -502,6 +534,8 @@ static uint16_t bf16_bits(float f) {
 extern "C" fr_status fr_set_closure(fr_mesh *m, const float *params, const float *scales, int32_t enable) {
   fr_status st = check_mesh(m);
   if (st) return st;
+  if (m->is_part)
+    return fail(m, FR_EUNSUPPORTED, "fr_set_closure: the closure needs the eddy viscosity of remote elements; not built for parts");
   if (!enable) {
     m->dphys.closure = 0;
     return FR_OK;
@@ -605,6 +639,212 @@ extern "C" void fr_free(fr_mesh *m) {
   delete m;
 }
 
+// ------------------------------------------------------------------ domain decomposition
+
+// Element centroids (mean of the corner vertices) and work weights (solution points).
+static void element_centroids(const fr_mesh_desc *d, std::vector<double> &cent, std::vector<double> &w) {
+  const int hn = d->hex_nodes == 0 ? 8 : d->hex_nodes, pn = d->prism_nodes == 0 ? 6 : d->prism_nodes;
+  const int N = d->p + 1;
+  const int64_t n = d->n_hex + d->n_prism;
+  cent.assign((size_t)n * 3, 0.0);
+  w.assign((size_t)n, 0.0);
+  for (int64_t e = 0; e < n; ++e) {
+    const bool hex = e < d->n_hex;
+    const int64_t *v = hex ? d->hex + e * hn : d->prism + (e - d->n_hex) * pn;
+    const int nc = hex ? 8 : 6;
+    for (int k = 0; k < nc; ++k)
+      for (int c = 0; c < 3; ++c) cent[e * 3 + c] += d->xyz[v[k] * 3 + c] / nc;
+    w[e] = hex ? (double)N * N * N : (double)N * N * (N + 1) / 2;
+  }
+}
+
+static fr_status check_vertex_ids(const fr_mesh_desc *d) {
+  const int hn = d->hex_nodes == 0 ? 8 : d->hex_nodes, pn = d->prism_nodes == 0 ? 6 : d->prism_nodes;
+  for (int64_t i = 0; i < d->n_hex * hn; ++i)
+    if (d->hex[i] < 0 || d->hex[i] >= d->n_nodes) return fail(nullptr, FR_EMESH, "vertex id out of range");
+  for (int64_t i = 0; i < d->n_prism * pn; ++i)
+    if (d->prism[i] < 0 || d->prism[i] >= d->n_nodes) return fail(nullptr, FR_EMESH, "vertex id out of range");
+  return FR_OK;
+}
+
+static fr_status check_desc_arrays(const fr_mesh_desc *desc) {
+  if (desc->p < 1 || desc->p > 7) return fail(nullptr, FR_EINVAL, "p must be in 1..7");
+  if (desc->n_hex < 0 || desc->n_prism < 0 || desc->n_hex + desc->n_prism <= 0 || (desc->n_hex > 0 && !desc->hex) ||
+      (desc->n_prism > 0 && !desc->prism) || desc->n_nodes <= 0 || !desc->xyz)
+    return fail(nullptr, FR_EINVAL, "empty mesh or NULL arrays");
+  if (desc->n_bface < 0 || (desc->n_bface > 0 && (!desc->bface_nodes || !desc->bface_tag)))
+    return fail(nullptr, FR_EINVAL, "bad boundary-face arrays");
+  if (desc->n_bc < 0 || (desc->n_bc > 0 && !desc->bc) || desc->n_periodic < 0 ||
+      (desc->n_periodic > 0 && !desc->periodic))
+    return fail(nullptr, FR_EINVAL, "bad boundary-condition or periodic arrays");
+  return FR_OK;
+}
+
+extern "C" fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part) {
+  if (!desc || !part) return fail(nullptr, FR_EINVAL, "desc or part is NULL");
+  if (fr_status sv = check_desc_arrays(desc); sv != FR_OK) return sv;
+  if (fr_status sv = check_vertex_ids(desc); sv != FR_OK) return sv;
+  std::vector<double> cent, w;
+  std::vector<int32_t> pv;
+  std::string err;
+  element_centroids(desc, cent, w);
+  fr_status st = partition_elements(cent, w, n_parts, pv, err);
+  if (st != FR_OK) return fail(nullptr, st, err);
+  std::memcpy(part, pv.data(), pv.size() * sizeof(int32_t));
+  return FR_OK;
+}
+
+// Host build of part `rank`: the global connectivity, then the part and its halo lists.
+static fr_status build_part(const fr_mesh_desc *desc, const int32_t *part, int32_t rank, HostMesh &local,
+                            HaloLists &halo) {
+  if (!part || rank < 0) return fail(nullptr, FR_EINVAL, "part is NULL or rank negative");
+  const int64_t n = desc->n_hex + desc->n_prism;
+  for (int64_t e = 0; e < n; ++e)
+    if (part[e] < 0) return fail(nullptr, FR_EINVAL, "negative part id");
+  if (desc->n_prism > 0) return fail(nullptr, FR_EUNSUPPORTED, "domain decomposition is built for hexahedral meshes");
+  HostMesh g;
+  std::string err;
+  fr_status st;
+  try {
+    st = build_host_mesh(desc, g, err, 0.0);
+    if (st == FR_OK) st = extract_part(g, std::vector<int32_t>(part, part + n), rank, local, halo, err);
+  } catch (const std::bad_alloc &) {
+    st = FR_ENOMEM;
+    err = "host allocation failed while building the part";
+  }
+  return st == FR_OK ? FR_OK : fail(nullptr, st, err);
+}
+
+static void fill_part_info(const HostMesh &h, const HaloLists &halo, fr_part_info *info) {
+  info->n_elem = h.E;
+  info->n_iface = h.n_interior;
+  info->n_bface = h.n_if - h.n_interior;
+  info->n_peers = (int32_t)halo.peers.size();
+  info->n_halo = (int64_t)halo.iface.size();
+}
+
+static void copy_halo(const HaloLists &halo, int32_t *peers, int64_t *peer_begin, int64_t *gid, int64_t *elem_global) {
+  if (peers && !halo.peers.empty()) std::memcpy(peers, halo.peers.data(), halo.peers.size() * sizeof(int32_t));
+  if (peer_begin) std::memcpy(peer_begin, halo.peer_begin.data(), halo.peer_begin.size() * sizeof(int64_t));
+  if (gid && !halo.gid.empty()) std::memcpy(gid, halo.gid.data(), halo.gid.size() * sizeof(int64_t));
+  if (elem_global) std::memcpy(elem_global, halo.elem_global.data(), halo.elem_global.size() * sizeof(int64_t));
+}
+
+extern "C" fr_status fr_part_inspect(const fr_mesh_desc *desc, const int32_t *part, int32_t rank, fr_part_info *info,
+                                     int32_t *peers, int64_t *peer_begin, int64_t *gid, int64_t *elem_global) {
+  if (!desc || !info) return fail(nullptr, FR_EINVAL, "desc or info is NULL");
+  if (fr_status sv = check_desc_arrays(desc); sv != FR_OK) return sv;
+  HostMesh h;
+  HaloLists halo;
+  if (fr_status st = build_part(desc, part, rank, h, halo); st != FR_OK) return st;
+  fill_part_info(h, halo, info);
+  copy_halo(halo, peers, peer_begin, gid, elem_global);
+  return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_create_part(const fr_mesh_desc *desc, const fr_physics *phys, const int32_t *part,
+                                         int32_t rank, uintptr_t stream, fr_mesh **out) {
+  if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (fr_status sv = validate_create(desc, phys); sv != FR_OK) return sv;
+  fr_mesh *m = new (std::nothrow) fr_mesh();
+  if (!m) return fail(nullptr, FR_ENOMEM, "host allocation failed");
+  if (fr_status st = build_part(desc, part, rank, m->host, m->halo); st != FR_OK) {
+    delete m;
+    return st;
+  }
+  m->is_part = true;
+  fr_mesh *made = nullptr;
+  if (fr_status st = finish_create(m, phys, stream, &made); st != FR_OK) return st;   // m freed on failure
+  const HaloLists &halo = made->halo;
+  const int64_t n_halo = (int64_t)halo.iface.size();
+  if (n_halo > 0) {
+    std::vector<int64_t> code((size_t)n_halo);
+    for (int64_t k = 0; k < n_halo; ++k) code[k] = 2 * halo.iface[k] + halo.side[k];
+    fr_status st = dalloc(made, &made->d_halo, (size_t)n_halo);
+    cudaError_t ce = cudaSuccess;
+    if (st == FR_OK) {
+      ce = cudaMemcpy(made->d_halo, code.data(), code.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+      if (ce != cudaSuccess) st = FR_ECUDA;
+    }
+    if (st != FR_OK) {
+      std::string msg = ce != cudaSuccess ? std::string("halo upload: ") + cudaGetErrorString(ce) : made->err;
+      fr_free(made);
+      return fail(nullptr, st, msg);
+    }
+  }
+  *out = made;
+  return FR_OK;
+}
+
+extern "C" fr_status fr_halo_query(const fr_mesh *m, fr_part_info *info, int32_t *peers, int64_t *peer_begin,
+                                   int64_t *gid, int64_t *elem_global) {
+  if (!m || !info) return FR_EINVAL;
+  if (!m->is_part) {
+    info->n_elem = m->host.E;
+    info->n_iface = m->host.n_interior;
+    info->n_bface = m->host.n_if - m->host.n_interior;
+    info->n_peers = 0;
+    info->n_halo = 0;
+    if (peer_begin) peer_begin[0] = 0;
+    if (elem_global)
+      for (int64_t e = 0; e < m->host.E; ++e) elem_global[e] = e;
+    return FR_OK;
+  }
+  fill_part_info(m->host, m->halo, info);
+  copy_halo(m->halo, peers, peer_begin, gid, elem_global);
+  return FR_OK;
+}
+
+extern "C" fr_status fr_part_phase(fr_mesh *m, int32_t phase, int32_t scheme, int32_t stage, double t, double dt,
+                                   const double *recv_device, double *send_device, double *R_device) {
+  (void)t;
+  fr_status st = check_mesh(m);
+  if (st) return st;
+  if (phase < 0 || phase > 2) return fail(m, FR_EINVAL, "phase must be 0, 1 or 2");
+  const int64_t n_halo = (int64_t)m->halo.iface.size();
+  if (n_halo > 0 && ((phase < 2 && !send_device) || (phase > 0 && !recv_device)))
+    return fail(m, FR_EINVAL, "NULL halo buffer");
+  DevMesh &d = m->dev;
+  const int Nf = d.Nf;
+  double *recv = const_cast<double *>(recv_device);
+  if (phase == 0) {
+    FR_CUDA(m, launch_residual(d, m->dphys, MODE_RESIDUAL, 0, 0.0, nullptr, m->stream, nullptr, 1));
+    FR_CUDA(m, launch_halo_copy(d.Qtr, send_device, m->d_halo, n_halo, 5, Nf, 0, m->stream));
+    return FR_OK;
+  }
+  if (phase == 1) {
+    FR_CUDA(m, launch_halo_copy(d.Qtr, recv, m->d_halo, n_halo, 5, Nf, 1, m->stream));
+    FR_CUDA(m, launch_residual(d, m->dphys, MODE_RESIDUAL, 0, 0.0, nullptr, m->stream, nullptr, 2));
+    FR_CUDA(m, launch_halo_copy(d.Gtr, send_device, m->d_halo, n_halo, 15, Nf, 0, m->stream));
+    return FR_OK;
+  }
+  int mode, last;
+  switch (scheme) {
+    case FR_RESIDUAL_ONLY: mode = MODE_RESIDUAL; last = -1; break;
+    case FR_RK44: mode = MODE_RK; last = 3; break;
+    case FR_SSPRK33: mode = MODE_SSP33; last = 2; break;
+    case FR_SSPRK104: mode = MODE_SSP104; last = 9; break;
+    default: return fail(m, FR_EINVAL, "unknown Runge-Kutta scheme");
+  }
+  if (mode == MODE_RESIDUAL && !R_device) return fail(m, FR_EINVAL, "NULL residual pointer");
+  if (mode != MODE_RESIDUAL && (stage < 0 || stage > last || !std::isfinite(dt)))
+    return fail(m, FR_EINVAL, "bad stage or dt");
+  FR_CUDA(m, launch_halo_copy(d.Gtr, recv, m->d_halo, n_halo, 15, Nf, 1, m->stream));
+  FR_CUDA(m, launch_residual(d, m->dphys, mode, mode == MODE_RESIDUAL ? 0 : stage, dt, R_device, m->stream, nullptr,
+                             4 | 8));
+  if (mode != MODE_RESIDUAL && stage == last) {
+    int *hflag = reinterpret_cast<int *>(m->h_scalar);
+    FR_CUDA(m, cudaMemcpyAsync(hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    FR_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (*hflag) {
+      FR_CUDA(m, cudaMemsetAsync(d.flag, 0, sizeof(int), m->stream));
+      return fail(m, FR_ENONFINITE, "non-finite value in the updated state");
+    }
+  }
+  return FR_OK;
+}
+
 extern "C" const char *fr_last_error(const fr_mesh *m) {
   if (m) return m->err.c_str();
   return g_create_error.c_str();
@@ -623,5 +863,7 @@ fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *s
 }
 
 fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg) { return fail(m, st, msg); }
+
+bool frx_mesh_has_halo(const fr_mesh *m) { return m && m->is_part && !m->halo.iface.empty(); }
 
 }  // namespace frx

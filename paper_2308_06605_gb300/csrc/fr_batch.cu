@@ -192,6 +192,10 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
     }
+    if (frx_mesh_has_halo(meshes[i])) {
+      delete b;
+      return bfail(nullptr, FR_EUNSUPPORTED, "parts that share interfaces with other parts cannot be batched");
+    }
     if (c.ph.vc_basis) {
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with a correction function c != 0 cannot be batched");

@@ -74,9 +74,11 @@ struct PhaseEvents {
 
 cudaError_t upload_basis_tables();
 // Residual of the current state dev.Q; MODE_RESIDUAL writes R (canonical layout) to Rout,
-// MODE_RK applies RK44 stage `stage` with step dt.
+// MODE_RK applies RK44 stage `stage` with step dt.  `phases` selects the parts that run (bit k:
+// 0 face traces and boundary states, 1 volume, 2 interface and boundary fluxes, 3 correction and
+// output / stage update), so a domain-decomposed stage can exchange halo traces in between.
 cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
-                            double *Rout, cudaStream_t st, const PhaseEvents *ev = nullptr);
+                            double *Rout, cudaStream_t st, const PhaseEvents *ev = nullptr, int phases = 15);
 // ---------------------------------------------------------------- batched persistent stage
 // One case of a batch: its device view, physics and precision (all cases share the precision).
 struct BatchCase {
@@ -157,6 +159,8 @@ FRX_HD inline int batch_prism_elems_per_block(int N, int block) {
 // recording an error on it.
 fr_status frx_mesh_view(fr_mesh *m, DevMesh *dev, DevPhys *phys, cudaStream_t *stream, int *device);
 fr_status frx_mesh_fail(fr_mesh *m, fr_status st, const std::string &msg);
+// True for a part of a domain-decomposed mesh that shares interfaces with other parts.
+bool frx_mesh_has_halo(const fr_mesh *m);
 
 // Prism phases of one residual evaluation (fr_prism.cu): 0 face traces, 1 volume, 3 correction
 // and output / RK update; a no-op on hexahedral meshes.
@@ -169,6 +173,11 @@ cudaError_t launch_vcjh_phase(const DevMesh &m, const DevPhys &ph, int phase, in
                               double *Rout, cudaStream_t st);
 cudaError_t vcjh_basis_create(int p, double c, int mixed, void **out);
 cudaError_t launch_prism_dt(const DevMesh &m, const DevPhys &ph, double cfl, cudaStream_t st);
+
+// Halo traces of a domain-decomposed mesh (X = Qtr with nv = 5 or Gtr with nv = 15): pack this
+// part's slots of the listed interfaces into buf, or unpack buf into the other sides' slots.
+cudaError_t launch_halo_copy(double *X, double *buf, const int64_t *code, int64_t n_halo, int nv, int Nf, int unpack,
+                             cudaStream_t st);
 
 // Mixed path: refresh the df32 copy of the state after it was set from outside.
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st);

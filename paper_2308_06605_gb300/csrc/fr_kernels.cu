@@ -55,7 +55,7 @@ __global__ void k_min_reduce(const double *__restrict__ x, int64_t n, double *__
 
 template <int N, typename T>
 static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
-                                 double *Rout, cudaStream_t st, const PhaseEvents *ev) {
+                                 double *Rout, cudaStream_t st, const PhaseEvents *ev, int phases) {
   constexpr int Np = N * N * N, Nf = N * N;
   const int64_t E = m.E;
   const T *Qin = reinterpret_cast<const T *>(m.mixed ? m.Qc : m.Q);
@@ -66,7 +66,7 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   T *Qc = m.mixed ? reinterpret_cast<T *>(m.Qc) : nullptr;
   const bool tri = m.if_tri != nullptr;
   cudaError_t err;
-  {
+  if (phases & 1) {
     const int64_t n = E * 6 * Nf;
     FR_EV_BEGIN(0);
     // Double-float: staged through shared memory (measured 35 % faster at 48^3, p = 4); FP64: one
@@ -88,7 +88,7 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
                                                                           m.n_if - m.n_interior, ph, m.if_tri);
     FR_EV_END(0);
   }
-  {
+  if (phases & 2) {
     const int threads = volume_threads<N>();
     const size_t smem = sizeof(T) * (35 * Np + 30 * Nf) + (ph.closure ? sizeof(float) * (10 * Np + 1 + 128) : 0);
     err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -103,7 +103,7 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     if ((err = launch_prism_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(1);
   }
-  {
+  if (phases & 4) {
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
     if (n > 0 && !tri)
@@ -122,7 +122,7 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
                                                                        m.if_elem, m.nu, m.if_tri);
     FR_EV_END(2);
   }
-  {
+  if (phases & 8) {
     const int64_t n = E * Np;
     FR_EV_BEGIN(3);
     if (n > 0 && ph.vc_basis) {
@@ -139,23 +139,23 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
 
 template <typename T>
 static cudaError_t dispatch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt,
-                                     double *Rout, cudaStream_t st, const PhaseEvents *ev) {
+                                     double *Rout, cudaStream_t st, const PhaseEvents *ev, int phases) {
   switch (m.N) {
-    case 2: return residual_impl<2, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 3: return residual_impl<3, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 4: return residual_impl<4, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 5: return residual_impl<5, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 6: return residual_impl<6, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 7: return residual_impl<7, T>(m, ph, mode, stage, dt, Rout, st, ev);
-    case 8: return residual_impl<8, T>(m, ph, mode, stage, dt, Rout, st, ev);
+    case 2: return residual_impl<2, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 3: return residual_impl<3, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 4: return residual_impl<4, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 5: return residual_impl<5, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 6: return residual_impl<6, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 7: return residual_impl<7, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+    case 8: return residual_impl<8, T>(m, ph, mode, stage, dt, Rout, st, ev, phases);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_residual(const DevMesh &m, const DevPhys &ph, int mode, int stage, double dt, double *Rout,
-                            cudaStream_t st, const PhaseEvents *ev) {
-  if (m.mixed) return dispatch_residual<df32>(m, ph, mode, stage, dt, Rout, st, ev);
-  return dispatch_residual<double>(m, ph, mode, stage, dt, Rout, st, ev);
+                            cudaStream_t st, const PhaseEvents *ev, int phases) {
+  if (m.mixed) return dispatch_residual<df32>(m, ph, mode, stage, dt, Rout, st, ev, phases);
+  return dispatch_residual<double>(m, ph, mode, stage, dt, Rout, st, ev, phases);
 }
 
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st) {
@@ -186,6 +186,33 @@ cudaError_t launch_max_dt(const DevMesh &m, const DevPhys &ph, double cfl, doubl
     case 8: return max_dt_impl<8>(m, ph, cfl, d_out, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Halo traces of a domain-decomposed mesh: entry k of the halo list is interface slot
+// code[k] = 2 I + s (this part's side s).  Pack copies this part's slot into buf[k] (nv values
+// of Nf points); unpack copies buf[k] into the other side's slot.  Values are moved as 8-byte
+// words, so FP64 and double-float traces travel bit for bit.
+__global__ void k_halo_copy(unsigned long long *__restrict__ X, unsigned long long *__restrict__ buf,
+                            const int64_t *__restrict__ code, int64_t n_halo, int nvNf, int unpack) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_halo * nvNf) return;
+  const int64_t k = t / nvNf;
+  const int c = (int)(t - k * nvNf);
+  const int64_t slot = unpack ? (code[k] ^ 1) : code[k];
+  if (unpack)
+    X[slot * nvNf + c] = buf[t];
+  else
+    buf[t] = X[slot * nvNf + c];
+}
+
+cudaError_t launch_halo_copy(double *X, double *buf, const int64_t *code, int64_t n_halo, int nv, int Nf, int unpack,
+                             cudaStream_t st) {
+  const int64_t n = n_halo * nv * Nf;
+  if (n == 0) return cudaSuccess;
+  k_halo_copy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<unsigned long long *>(X),
+                                                           reinterpret_cast<unsigned long long *>(buf), code, n_halo,
+                                                           nv * Nf, unpack);
+  return cudaGetLastError();
 }
 
 // OR the per-case non-finite flags into the batch word and clear them (graph-of-kernels mode).

@@ -48,6 +48,8 @@ extern "C" fr_status fr_residual_static(fr_mesh *mesh, const double *Q_device, d
   if (!Q_device || !R_device) return frx_mesh_fail(mesh, FR_EINVAL, "fr_residual_static: NULL state or residual");
   if (dev.mixed) return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: FP64 meshes only");
   if (dev.Ep > 0) return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: hexahedral meshes only");
+  if (frx_mesh_has_halo(mesh))
+    return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: parts that share interfaces with other parts");
   if (phys.vc_basis)
     return frx_mesh_fail(mesh, FR_EUNSUPPORTED, "fr_residual_static: DG-equivalent correction (c = 0) only");
   // The closure writes each element's eddy viscosity into a mesh-owned array, which would make

@@ -21,6 +21,7 @@ STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_E
                 "FR_ENONFINITE", "FR_ETIMEOUT"]
 FR_HOST, FR_DEVICE = 0, 1
 FR_RK44, FR_SSPRK33, FR_SSPRK104 = 0, 1, 2
+FR_RESIDUAL_ONLY = -1
 RK_STAGES = {FR_RK44: 4, FR_SSPRK33: 3, FR_SSPRK104: 10}
 
 
@@ -70,6 +71,11 @@ class fr_mesh_info(C.Structure):
                 ("device", C.c_int32)]
 
 
+class fr_part_info(C.Structure):
+    _fields_ = [("n_elem", C.c_int64), ("n_iface", C.c_int64), ("n_bface", C.c_int64), ("n_peers", C.c_int32),
+                ("n_halo", C.c_int64)]
+
+
 # Exported functions: name -> (restype, argtypes)
 SIGNATURES = {
     "fr_mesh_create": (C.c_int, [C.POINTER(fr_mesh_desc), C.POINTER(fr_physics), C.c_size_t, C.POINTER(C.c_void_p)]),
@@ -103,6 +109,15 @@ SIGNATURES = {
     "fr_batch_select": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_batch_free": (None, [C.c_void_p]),
     "fr_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fr_partition": (C.c_int, [C.POINTER(fr_mesh_desc), C.c_int32, C.c_void_p]),
+    "fr_part_inspect": (C.c_int, [C.POINTER(fr_mesh_desc), C.c_void_p, C.c_int32, C.POINTER(fr_part_info),
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_mesh_create_part": (C.c_int, [C.POINTER(fr_mesh_desc), C.POINTER(fr_physics), C.c_void_p, C.c_int32,
+                                      C.c_size_t, C.POINTER(C.c_void_p)]),
+    "fr_halo_query": (C.c_int, [C.c_void_p, C.POINTER(fr_part_info), C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
+    "fr_part_phase": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
     "fr_free": (None, [C.c_void_p]),
     "fr_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_basis_1d": (C.c_int, [C.c_int32, C.c_double] + [C.POINTER(C.c_double)] * 7),
@@ -257,6 +272,12 @@ def inspect(desc: MeshDesc, p: int, elem_p=None) -> dict:
             "ef_prism": ef_p, "tri_slot": tri_slot}
 
 
+def _physics(phys: Physics) -> fr_physics:
+    return fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
+                      viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision,
+                      ldg_tau=getattr(phys, "ldg_tau", 0.1), vcjh_c=getattr(phys, "vcjh_c", 0.0))
+
+
 class Mesh:
     """One FR discretisation living on the current CUDA device (owns the C-side fr_mesh).
 
@@ -270,11 +291,9 @@ class Mesh:
         self._keep = []
         d, keep = _describe(desc, p, elem_p)
         self._keep += keep
-        ph = fr_physics(gamma=phys.gamma, R=phys.R, mu=phys.mu, Pr=phys.Pr, inviscid=phys.inviscid_flux,
-                        viscous=phys.viscous, br2_eta=phys.br2_eta, precision=phys.precision,
-                        ldg_tau=getattr(phys, "ldg_tau", 0.1), vcjh_c=getattr(phys, "vcjh_c", 0.0))
+        ph = _physics(phys)
         h = C.c_void_p()
-        st = lib.fr_mesh_create(C.byref(d), C.byref(ph), stream, C.byref(h))
+        st = self._create(lib, d, ph, stream, h)
         if st != FR_OK:
             raise FRError(st, lib.fr_last_error(None).decode())
         self._h = h
@@ -285,6 +304,9 @@ class Mesh:
         self.n_prism, self.n_pts_prism, self.n_points = info.n_prism, info.n_pts_prism, info.n_points
         self.shape = (self.n_elem, self.n_pts, 5) if self.n_prism == 0 else (self.n_points, 5)
         self.device = info.device
+
+    def _create(self, lib, d, ph, stream, h):
+        return lib.fr_mesh_create(C.byref(d), C.byref(ph), stream, C.byref(h))
 
     def _check(self, st):
         if st != FR_OK:
@@ -394,6 +416,78 @@ class Mesh:
 
     def __exit__(self, *a):
         self.close()
+
+
+def partition(desc: MeshDesc, p: int, n_parts: int) -> np.ndarray:
+    """fr_partition: part id of every element (recursive coordinate bisection; host only)."""
+    lib = load()
+    d, keep = _describe(desc, p)
+    part = np.zeros(d.n_hex + d.n_prism, dtype=np.int32)
+    st = lib.fr_partition(C.byref(d), n_parts, C.c_void_p(part.ctypes.data))
+    if st != FR_OK:
+        raise FRError(st, lib.fr_last_error(None).decode())
+    del keep
+    return part
+
+
+def _halo_arrays(info):
+    return (np.zeros(max(1, info.n_peers), np.int32), np.zeros(info.n_peers + 1, np.int64),
+            np.zeros(max(1, info.n_halo), np.int64), np.zeros(info.n_elem, np.int64))
+
+
+def _halo_dict(info, arrs):
+    peers, begin, gid, eg = arrs
+    return {"n_elem": info.n_elem, "n_iface": info.n_iface, "n_bface": info.n_bface, "n_peers": info.n_peers,
+            "n_halo": info.n_halo, "peers": peers[:info.n_peers].copy(), "peer_begin": begin.copy(),
+            "gid": gid[:info.n_halo].copy(), "elem_global": eg.copy()}
+
+
+def part_inspect(desc: MeshDesc, p: int, part, rank: int) -> dict:
+    """fr_part_inspect: sizes and halo lists of part `rank` (host only, no device work)."""
+    lib = load()
+    d, keep = _describe(desc, p)
+    pa = np.ascontiguousarray(part, dtype=np.int32)
+    info = fr_part_info()
+    st = lib.fr_part_inspect(C.byref(d), C.c_void_p(pa.ctypes.data), rank, C.byref(info), None, None, None, None)
+    if st != FR_OK:
+        raise FRError(st, lib.fr_last_error(None).decode())
+    arrs = _halo_arrays(info)
+    st = lib.fr_part_inspect(C.byref(d), C.c_void_p(pa.ctypes.data), rank, C.byref(info),
+                             *[C.c_void_p(a.ctypes.data) for a in arrs])
+    if st != FR_OK:
+        raise FRError(st, lib.fr_last_error(None).decode())
+    del keep
+    return _halo_dict(info, arrs)
+
+
+class PartMesh(Mesh):
+    """Part `rank` of a domain-decomposed hexahedral mesh (fr_mesh_create_part).  States are in
+    the part's local element order: `halo()["elem_global"]` gives each local element's index in
+    the whole mesh.  With halo interfaces, stages run through `phase` (three calls per stage with
+    the caller moving halo entries between them)."""
+
+    def __init__(self, desc: MeshDesc, phys: Physics, p: int, part, rank: int, stream: int = 0):
+        self._part = np.ascontiguousarray(part, dtype=np.int32)
+        self._rank = int(rank)
+        super().__init__(desc, phys, p, stream)
+        self._halo = self.halo()
+
+    def _create(self, lib, d, ph, stream, h):
+        return lib.fr_mesh_create_part(C.byref(d), C.byref(ph), C.c_void_p(self._part.ctypes.data), self._rank,
+                                       stream, C.byref(h))
+
+    def halo(self) -> dict:
+        info = fr_part_info()
+        self._check(self._lib.fr_halo_query(self._h, C.byref(info), None, None, None, None))
+        arrs = _halo_arrays(info)
+        self._check(self._lib.fr_halo_query(self._h, C.byref(info), *[C.c_void_p(a.ctypes.data) for a in arrs]))
+        return _halo_dict(info, arrs)
+
+    def phase(self, phase: int, scheme: int = FR_RESIDUAL_ONLY, stage: int = 0, t: float = 0.0, dt: float = 0.0,
+              recv=None, send=None, R=None):
+        """fr_part_phase with device tensors (recv, send: float64 of n_halo * nv * (p+1)^2 values)."""
+        ptr = lambda x: None if x is None else C.c_void_p(x.data_ptr())        # noqa: E731
+        self._check(self._lib.fr_part_phase(self._h, phase, scheme, stage, t, dt, ptr(recv), ptr(send), ptr(R)))
 
 
 def project_state(src: "Mesh", dst: "Mesh"):
