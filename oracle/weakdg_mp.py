@@ -13,6 +13,7 @@ face gradients as the common gradient).  Nothing here uses the FP64 oracle's bas
 connectivity or gas functions, so the two pin each other.
 """
 import itertools
+from fractions import Fraction
 
 import mpmath
 import numpy as np
@@ -91,12 +92,21 @@ def _rusanov(qa, qb, n, gam):
     return [sum((Fa[j][v] + Fb[j][v]) * n[j] for j in range(3)) / 2 - L * nm * (qb[v] - qa[v]) / 2 for v in range(5)]
 
 
+def _exact(x):
+    """A constant at the working precision: Fractions and ints exactly, floats by their binary value,
+    strings as decimal numbers (e.g. "1.4" is 1.4 to 40 digits, not its nearest double)."""
+    if isinstance(x, Fraction):
+        return mp.mpf(x.numerator) / x.denominator
+    return mp.mpf(x)
+
+
 def brute_force_residual(Q, p, n1, Amat, hbox, gam, R, mu, Pr, eta, viscous):
     """Residual (float64, rounded from 40 digits) of n1 elements stacked along the first lattice
     axis of the affine map x = Amat diag(hbox) xi, periodic in all directions; Q [n1][N^3][5] in the
-    canonical point order; gam, R, mu, Pr, eta mpmath numbers or ints; BR2 viscous terms if
-    viscous."""
+    canonical point order; gam, R, mu, Pr, eta as Fractions, ints, floats or decimal strings,
+    converted at 40 digits; BR2 viscous terms if viscous."""
     mp.dps = 40
+    gam, R, mu, Pr, eta = (_exact(v) for v in (gam, R, mu, Pr, eta))
     N = p + 1
     nodes, _ = _gl_mp(N)
     xq, wq = _gl_mp(N + 2)

@@ -19,8 +19,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-import mpmath  # noqa: E402
-
 from oracle.hexfr import HexFR  # noqa: E402
 from oracle.weakdg_mp import brute_force_residual  # noqa: E402
 from paper_2308_06605_gb300 import inputs as I  # noqa: E402
@@ -38,7 +36,6 @@ def case_setup(p, n1):
 
 
 def main():
-    mp = mpmath.mp
     lines = ["# Residual dQ/dt of low-Mach Taylor-Green states at 40 digits (oracle.weakdg_mp), written by",
              "# tests/golden/make_g13_reference.py.  Per line: p n1 e m  Q_0..Q_4 (the state, repr)",
              "# R_0..R_4 (the 40-digit residual rounded to float64, printed with 21 digits)."]
@@ -47,8 +44,8 @@ def main():
         x = HexFR(desc, phys, p).x
         Q = I.tgv_state(x, Ma=0.1, perturb=1e-3, seed=3)
         L = 2 * np.pi
-        R = brute_force_residual(Q, p, n1, [[1, 0, 0], [0, 1, 0], [0, 0, 1]], (L / n1, L, L), mp.mpf(14) / 10,
-                                 mp.mpf(phys.R), mp.mpf(phys.mu), mp.mpf(71) / 100, 6, True)
+        R = brute_force_residual(Q, p, n1, [[1, 0, 0], [0, 1, 0], [0, 0, 1]], (L / n1, L, L), phys.gamma,
+                                 phys.R, phys.mu, phys.Pr, 6, True)
         for e in range(n1):
             for m in range(Q.shape[1]):
                 q = " ".join(repr(float(v)) for v in Q[e, m])

@@ -37,8 +37,7 @@ def test_oracle_matches_mpmath_weak_form(p, n1, viscous):
     Q = I.conserved(rho, vel[..., 0], vel[..., 1], vel[..., 2], pr, 1.4)
     R_ora = ora.residual(Q)
     hcell = (hbox[0] / n1, hbox[1], hbox[2])
-    R_bf = brute_force_residual(Q, p, n1, SHEAR, hcell, mp.mpf(14) / 10, 1, mp.mpf(phys.mu),
-                                mp.mpf(71) / 100, 6, viscous)
+    R_bf = brute_force_residual(Q, p, n1, SHEAR, hcell, phys.gamma, 1, phys.mu, phys.Pr, 6, viscous)
     scale = np.abs(R_bf).max(axis=(0, 1))
     err = np.abs(R_ora - R_bf).max(axis=(0, 1)) / scale
     assert np.all(err < 1e-13), err

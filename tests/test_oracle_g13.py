@@ -44,13 +44,12 @@ def test_fp64_oracle_error_is_ulps_of_magnitude_scale_not_of_entry(case):
 
 @pytest.mark.slow
 def test_fixture_reproduces_from_the_40_digit_oracle():
-    mpmath = pytest.importorskip("mpmath")
+    pytest.importorskip("mpmath")
     from oracle.weakdg_mp import brute_force_residual
     ref = load_g13_reference()
     for (p, n1), (Q, Rx) in ref.items():
         desc, phys = _case_setup(p, n1)
         L = 2 * np.pi
-        R = brute_force_residual(Q, p, n1, [[1, 0, 0], [0, 1, 0], [0, 0, 1]], (L / n1, L, L),
-                                 mpmath.mp.mpf(14) / 10, mpmath.mp.mpf(phys.R), mpmath.mp.mpf(phys.mu),
-                                 mpmath.mp.mpf(71) / 100, 6, True)
+        R = brute_force_residual(Q, p, n1, [[1, 0, 0], [0, 1, 0], [0, 0, 1]], (L / n1, L, L), phys.gamma,
+                                 phys.R, phys.mu, phys.Pr, 6, True)
         np.testing.assert_array_equal(R, Rx)
