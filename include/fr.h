@@ -49,7 +49,7 @@ typedef enum {
 enum { FR_HOST = 0, FR_DEVICE = 1 };                       /* where a state pointer lives */
 enum { FR_RUSANOV = 0, FR_ROE = 1 };                       /* inviscid common flux */
 enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1, FR_VISC_LDG = 2 }; /* viscous treatment */
-enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1 };              /* arithmetic of the element operators */
+enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1, FR_PREC_MIXED_TC = 2 };   /* element arithmetic (fr_physics) */
 enum {                                                     /* explicit Runge–Kutta schemes */
   FR_RK44 = 0,      /* classical four-stage, fourth order */
   FR_SSPRK33 = 1,   /* three-stage third-order SSP (Shu–Osher form), SSP coefficient 1 */
@@ -117,7 +117,13 @@ typedef struct {
   double br2_eta;       /* BR2 penalty factor (number of faces, 6, by default) */
   int32_t precision;    /* FR_PREC_FP64 | FR_PREC_MIXED: element operators (traces, gradients,
                            fluxes at solution points, divergence, correction) in double-float
-                           (FP32 hi + lo pairs); Riemann flux, boundary states and RK in FP64 */
+                           (FP32 hi + lo pairs); Riemann flux, boundary states and RK in FP64 |
+                           FR_PREC_MIXED_TC: as FR_PREC_MIXED, with the face interpolation (Eq. 2,
+                           the solution at the flux points) on the tensor cores: tcgen05.mma in
+                           TF32 with FP32 accumulation on exponent-aligned 10-bit slices of the
+                           data and of l(+-1) (error-free splitting, Ozaki et al. 2012), 4 slices
+                           each, combined into double-float; error a few 2^-41 of the line's
+                           largest value (hexahedra; not in fr_batch_create: FR_EUNSUPPORTED) */
   double ldg_tau;       /* LDG penalty tau (FR_VISC_LDG): at each interface the side whose face
                            normal (summed over the face) points along (1, sqrt2/2, sqrt3/4)
                            supplies the common solution, the other side the common gradient

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfr.so")
-SOURCES = ["fr_mesh.cpp", "fr_tri.cpp", "fr_curved.cpp", "fr_part.cpp", "fr_kernels.cu", "fr_vcjh.cu", "fr_prism.cu", "fr_api.cu", "fr_probe.cu",
+SOURCES = ["fr_mesh.cpp", "fr_tri.cpp", "fr_curved.cpp", "fr_part.cpp", "fr_kernels.cu", "fr_tc.cu", "fr_vcjh.cu", "fr_prism.cu", "fr_api.cu", "fr_probe.cu",
            "fr_static.cu", "fr_batch.cu", "fr_mlp.cu", "fr_project.cu"]
 # The batched stage kernel is compiled once per (precision, block size) so the variants build in parallel.
 VARIANTS = [("fr_batch_kernel.cu", f"m{m}_b{b}", [f"-DFRX_BATCH_MIXED={m}", f"-DFRX_BATCH_BLOCK={b}"])

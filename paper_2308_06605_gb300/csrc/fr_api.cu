@@ -192,7 +192,7 @@ static fr_status validate_create(const fr_mesh_desc *desc, const fr_physics *phy
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
   if (phys->viscous == FR_VISC_LDG && !(phys->ldg_tau >= 0.0))
     return fail(nullptr, FR_EINVAL, "LDG penalty must be non-negative");
-  if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED)
+  if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED && phys->precision != FR_PREC_MIXED_TC)
     return fail(nullptr, FR_EINVAL, "unknown precision");
   if (!vcjh_in_family(desc->p, phys->vcjh_c))
     return fail(nullptr, FR_EINVAL, "correction parameter c outside the energy-stable family (1 + eta <= 0)");
@@ -293,7 +293,8 @@ static fr_status finish_create(fr_mesh *m, const fr_physics *phys, uintptr_t str
   d.p = h.p; d.N = h.N; d.Np = h.Np; d.Nf = h.Nf;
   d.E = h.E; d.n_if = h.n_if; d.n_interior = h.n_interior;
   d.Ep = h.Ep; d.Nt = h.Nt; d.Npp = h.Npp;
-  d.mixed = (phys->precision == FR_PREC_MIXED) ? 1 : 0;
+  d.mixed = (phys->precision == FR_PREC_MIXED || phys->precision == FR_PREC_MIXED_TC) ? 1 : 0;
+  d.tc = (phys->precision == FR_PREC_MIXED_TC) ? 1 : 0;
   const size_t nsol = ((size_t)h.E * h.Np + (size_t)h.Ep * h.Npp) * 5;
   const size_t G = (size_t)(h.E + h.Ep);
   const size_t Nf = h.Nf;
@@ -503,7 +504,9 @@ extern "C" fr_status fr_rk_stage(fr_mesh *m, int32_t scheme, int32_t stage, doub
     FR_CUDA(m, cudaMemcpyAsync(hflag, m->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     FR_CUDA(m, cudaStreamSynchronize(m->stream));
     if (*hflag) {
+      const int f = *hflag;
       FR_CUDA(m, cudaMemsetAsync(m->dev.flag, 0, sizeof(int), m->stream));
+      if (f & 2) return fail(m, FR_ETIMEOUT, "a tensor-core kernel gave up waiting for its copies or MMAs");
       return fail(m, FR_ENONFINITE, "non-finite value in the updated state");
     }
   }
@@ -838,7 +841,9 @@ extern "C" fr_status fr_part_phase(fr_mesh *m, int32_t phase, int32_t scheme, in
     FR_CUDA(m, cudaMemcpyAsync(hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     FR_CUDA(m, cudaStreamSynchronize(m->stream));
     if (*hflag) {
+      const int f = *hflag;
       FR_CUDA(m, cudaMemsetAsync(d.flag, 0, sizeof(int), m->stream));
+      if (f & 2) return fail(m, FR_ETIMEOUT, "a tensor-core kernel gave up waiting for its copies or MMAs");
       return fail(m, FR_ENONFINITE, "non-finite value in the updated state");
     }
   }

@@ -192,6 +192,10 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
     }
+    if (c.m.tc) {
+      delete b;
+      return bfail(nullptr, FR_EUNSUPPORTED, "the tensor-core face interpolation (FR_PREC_MIXED_TC) is not batched");
+    }
     if (frx_mesh_has_halo(meshes[i])) {
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "parts that share interfaces with other parts cannot be batched");

@@ -46,6 +46,7 @@ struct DevMesh {
   int p, N, Np, Nf;
   int64_t E, n_if, n_interior;
   int mixed;        // 1: element arrays hold df32 pairs (same 8-byte slots), Qc holds the state as df32
+  int tc;           // 1 (mixed only): face interpolation on the tensor cores (FR_PREC_MIXED_TC)
   double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc, *Unc;
   int32_t *ef, *if_bc;
   int32_t *if_elem;        // [n_if][2] element of each side (-1: boundary), closure only
@@ -178,6 +179,10 @@ cudaError_t launch_prism_dt(const DevMesh &m, const DevPhys &ph, double cfl, cud
 // part's slots of the listed interfaces into buf, or unpack buf into the other sides' slots.
 cudaError_t launch_halo_copy(double *X, double *buf, const int64_t *code, int64_t n_halo, int nv, int Nf, int unpack,
                              cudaStream_t st);
+
+// Tensor-core face interpolation of the double-float state (fr_tc.cu) and its operator tables.
+cudaError_t launch_interp_tc(const DevMesh &m, cudaStream_t st);
+cudaError_t upload_tc_tables();
 
 // Mixed path: refresh the df32 copy of the state after it was set from outside.
 cudaError_t launch_state_copy(const DevMesh &m, cudaStream_t st);

@@ -73,8 +73,11 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
     // thread per face point reading the state directly (the staged form was 7 % slower there).
     if constexpr (std::is_same<T, df32>::value) {
       constexpr int epb = interp_epb<N>();
-      if (n > 0)
+      if (n > 0 && m.tc) {
+        if ((err = launch_interp_tc(m, st)) != cudaSuccess) return err;
+      } else if (n > 0) {
         k_interp_faces_smem<N, T><<<(unsigned)((E + epb - 1) / epb), kInterpThreads, 0, st>>>(Qin, m.ef, Qtr, E);
+      }
     } else if (n > 0) {
       k_interp_faces<N, T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qin, m.ef, Qtr, E);
     }
@@ -248,6 +251,7 @@ size_t batch_smem_bytes(const int *Ns, const int *has_prism, int n, int block, i
 
 cudaError_t upload_basis_tables() {
   cudaError_t e = upload_basis_local();
+  if (e == cudaSuccess) e = upload_tc_tables();
   if (e == cudaSuccess) e = batch_upload_m0_b256();
   if (e == cudaSuccess) e = batch_upload_m0_b512();
   if (e == cudaSuccess) e = batch_upload_m1_b256();
