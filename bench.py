@@ -198,7 +198,7 @@ class Case:
         self.torch = torch
         self.stream = torch.cuda.current_stream()
         phys = I.tgv_physics()
-        phys.precision = 1 if precision == "mixed" else 0
+        phys.precision = {"fp64": 0, "mixed": 1, "mixed_tc": 2}[precision]
         phys.vcjh_c = vcjh_c
         self.mesh = fr.Mesh(I.hex_box_mesh((n_edge, n_edge, n_edge), prisms=prisms), phys, p,
                             stream=self.stream.cuda_stream)
@@ -337,6 +337,27 @@ def run_prisms(steps, fp64_peak, df_peak, cases=None):
     return out
 
 
+def run_tc(steps, n=N_EDGE, p=ORDER):
+    """The double-float path with the face interpolation on the tensor cores (FR_PREC_MIXED_TC)
+    against the plain double-float path on the benchmark mesh: RK44 updates/s, the face
+    interpolation's time per stage, and each residual's error against the FP64 path."""
+    row = {"n_edge": n, "p": p, "n_points": n ** 3 * (p + 1) ** 3}
+    c64 = Case(n, p, "fp64")
+    dt = c64.dt
+    for tag, prec in (("mixed", "mixed"), ("mixed_tc", "mixed_tc")):
+        c = Case(n, p, prec, dt=dt)
+        row[tag + "_error_vs_fp64"] = residual_error(c, c64)
+        c.step()
+        ms = c.timed(max(2, steps))
+        row[tag] = c.n_pts * 4 * max(2, steps) / (ms * 1e-3)
+        k = c.kernels(2, p)
+        row[tag + "_interp_ms"] = k["interp_faces"]["avg_ms"]
+        row[tag + "_interp_gbs"] = k["interp_faces"]["gbs"]
+        c.close()
+    c64.close()
+    return row
+
+
 def run_vcjh(steps, n=48, p=4):
     """Correction function c_HU (energy-stable family, Huynh's g2) against the DG-equivalent c = 0
     on the TGV box, both precisions: updates/s of RK44 steps."""
@@ -441,6 +462,9 @@ def run_ours(args):
     fr.load()
     if args.cascade_only:
         print(json.dumps({"cascade_p7": run_cascade(args.steps, None, None)}), flush=True)
+        return 0
+    if args.tc_only:
+        print(json.dumps({"tensor_core_interp": run_tc(args.steps, N_EDGE, ORDER)}), flush=True)
         return 0
 
     def barrier():
@@ -547,6 +571,7 @@ def run_ours(args):
         prisms = run_prisms(args.steps, fp64_peak, df_peak, cases)
 
     vcjh = run_vcjh(args.steps) if not args.no_vcjh else {}
+    tc_row = run_tc(args.steps) if not args.no_tc else {}
 
     ensemble = {}
     if not args.no_ensemble:
@@ -585,6 +610,7 @@ def run_ours(args):
             "gpu_launches": 4 * 4 * args.steps, "roofline": roofline, "kernels": k_mx,
             "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
             "ensemble_64_vortex": ensemble, "prisms_tgv": prisms, "vcjh_hu_48cube_p4": vcjh,
+            "tensor_core_interp_64cube_p4": tc_row,
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}
     if args.cascade:
         line["cascade_p7"] = run_cascade(args.steps, fp64_peak, df_peak)
@@ -632,6 +658,9 @@ def main():
     ap.add_argument("--cascade", action="store_true",
                     help="also run the synthetic cascade passage (398 000 quadratic elements, p = 7, 182 M points)")
     ap.add_argument("--cascade-only", action="store_true", help="print only the cascade measurement")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core face-interpolation measurement")
+    ap.add_argument("--tc-only", action="store_true",
+                    help="print only the tensor-core face-interpolation measurement (with --n-edge / --order)")
     ap.add_argument("--n-edge", type=int, default=N_EDGE, help="elements per edge (profiling of smaller cases)")
     ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()
