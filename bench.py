@@ -2,14 +2,17 @@
 
 Workload: Taylor-Green vortex (Ma 0.1, Re 1600) on a periodic 64^3 hexahedral mesh at p = 4
 (125 Gauss-Legendre points per element, 32.8 M solution points, 164 M unknowns), compressible
-Navier-Stokes with Rusanov + BR2 fluxes and the DG-equivalent correction; FP64 path.
+Navier-Stokes with Rusanov + BR2 fluxes and the DG-equivalent correction.  The headline value is
+the double-float path with its viscous branch in FP32 (FR_PREC_MIXED_VF32, within its stated
+error at this Reynolds number); the all-double-float and the FP64 paths are reported beside it.
 One step = one RK44 time step = 4 RK stages (each: residual + stage update); the metric counts
 solution points x stages per second.  Inputs are synthetic and seeded; the device working set
 (~18 GB) is far larger than L2, so no flush is needed between iterations.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the path has no
-data exchange between GPUs at this size: "replicas only"), timing is max over ranks.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (weak scaling by
+replicas; the domain-decomposed stage with halo exchange, fr_part_phase, is not timed across GPUs
+here), timing is max over ranks.
 """
 from __future__ import annotations
 
@@ -167,7 +170,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     rate, sample, cores = oracle_rate(max_steps=args.steps)
     el = time.perf_counter() - t0
-    cfg = dict(config("mixed"))
+    cfg = dict(config("mixed_vf32"))
     cfg["reference_sample"] = ("each step: one oracle RK44 step on the 8^3 periodic hex TGV at p=4 (64 000 points; "
                                "same case, order and per-point work as the 64^3 workload, 1/512 of its points)")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
@@ -473,12 +476,17 @@ def run_ours(args):
     def max_over_ranks(v):
         return _dist_max(v, world, f"cuda:{dev}")
 
-    # Headline workload: both precisions on the same initial state and the same dt.
+    # Headline workload: every precision on the same initial state and the same dt.  The headline
+    # value is the double-float path with the viscous branch in FP32 (FR_PREC_MIXED_VF32), whose
+    # stated error holds at this Reynolds number (1600 >= 400); the all-double-float path and FP64
+    # are reported beside it.
     c64 = Case(N_EDGE, ORDER, "fp64")
     cmx = Case(N_EDGE, ORDER, "mixed", dt=c64.dt)
+    cvf = Case(N_EDGE, ORDER, "mixed_vf32", dt=c64.dt)
     err = residual_error(cmx, c64)
+    err_vf = residual_error(cvf, c64)
     n_pts = c64.n_pts
-    for c in (c64, cmx):
+    for c in (c64, cmx, cvf):
         for _ in range(args.warmup):
             c.step()
     props = torch.cuda.get_device_properties(dev)
@@ -489,27 +497,39 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    ms_vf = max_over_ranks(cvf.timed(args.steps))
     ms_mx = max_over_ranks(cmx.timed(args.steps))
     ms_64 = max_over_ranks(c64.timed(args.steps))
     barrier()
     clocks = sampler.stop()
-    value = world * n_pts * 4 * args.steps / (ms_mx * 1e-3)
+    value = world * n_pts * 4 * args.steps / (ms_vf * 1e-3)
+    value_mx = world * n_pts * 4 * args.steps / (ms_mx * 1e-3)
     value64 = world * n_pts * 4 * args.steps / (ms_64 * 1e-3)
+    k_vf = cvf.kernels(args.steps, ORDER)
     k_mx = cmx.kernels(args.steps, ORDER)
     k_64 = c64.kernels(args.steps, ORDER)
     fp64_peak = fr.probe_fma(0, 4000)
     fp32_peak = fr.probe_fma(1, 200000)
     df_peak = fp32_peak / DF_FP32_FLOPS_PER_FLOP
-    dom = max(k_mx, key=lambda n_: k_mx[n_]["share"])
     fl = perfmodel.flops_per_point(ORDER)
     by = perfmodel.bytes_per_point(ORDER)
-    ach = k_mx[dom]["gflops"] * 1e9
-    roofline = {"bound": "alu", "kernel": dom, "precision": "mixed (double-float on the FP32 pipe)",
-                "achieved": ach / 1e12, "peak": df_peak / 1e12, "unit": "TFLOP/s", "frac": ach / df_peak,
-                "traffic": TRAFFIC.get(("mixed", ORDER, N_EDGE, dom)),
-                "peak_source": "measured FP32 FMA rate (fr_probe_fma) / 18: a double-float multiply-add is 18 FP32 "
-                               "instructions for 2 algorithmic flops",
-                "algorithmic_flops_per_point": fl[dom], "algorithmic_bytes_per_point": by[dom]}
+
+    def mixed_roofline(k, fp32_viscous, tag):
+        dom = max(k, key=lambda n_: k[n_]["share"])
+        peak = perfmodel.mixed_alu_peak(ORDER, df_peak, fp32_peak, fp32_viscous) if dom == "volume" else df_peak
+        ach = k[dom]["gflops"] * 1e9
+        src = ("measured FP32 FMA rate (fr_probe_fma) / 18 (a double-float multiply-add is 18 FP32 instructions "
+               "for 2 algorithmic flops)")
+        if fp32_viscous and dom == "volume":
+            src = ("the kernel's arithmetic mix at measured rates: the viscous branch's flops at the FP32 FMA rate, "
+                   "the rest at that rate / 18 (times added)")
+        return {"bound": "alu", "kernel": dom, "precision": tag, "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC.get((tag, ORDER, N_EDGE, dom)),
+                "peak_source": src, "algorithmic_flops_per_point": fl[dom], "algorithmic_bytes_per_point": by[dom]}
+
+    roofline = mixed_roofline(k_vf, True, "mixed_vf32")
+    double_float = {"value": value_mx, "ms_per_step": ms_mx / args.steps, "kernels": k_mx,
+                    "roofline": mixed_roofline(k_mx, False, "mixed"), "error_vs_fp64": err}
     dom64 = max(k_64, key=lambda n_: k_64[n_]["share"])
     fp64 = {"value": value64, "ms_per_step": ms_64 / args.steps, "kernels": k_64,
             "roofline": {"bound": "alu", "kernel": dom64, "achieved": k_64[dom64]["gflops"] / 1e3,
@@ -520,28 +540,30 @@ def run_ours(args):
 
     # End to end through the public API with host buffers (headline path): set_state from pinned
     # host memory, four stages, get_state back to pinned host memory, every step.
-    Qh = torch.from_numpy(cmx.Q0).pin_memory()
+    cmx.close()
+    Qh = torch.from_numpy(cvf.Q0).pin_memory()
     Out = torch.empty_like(Qh).pin_memory()
     k_e2e = max(1, args.steps)
     # One untimed pass first: the first transfers from freshly pinned buffers pay one-time costs.
-    cmx.mesh.set_state(Qh)
-    cmx.step()
-    cmx.mesh.get_state(out=Out)
+    cvf.mesh.set_state(Qh)
+    cvf.step()
+    cvf.mesh.get_state(out=Out)
     torch.cuda.synchronize()
     barrier()
     phase = [0.0, 0.0, 0.0]          # host wall time of set_state, the four stages, get_state
+    phase_min = [1e30, 1e30, 1e30]
     te0 = time.perf_counter()
     for _ in range(k_e2e):
         t0 = time.perf_counter()
-        cmx.mesh.set_state(Qh)        # returns after the host buffer has been read
+        cvf.mesh.set_state(Qh)        # returns after the host buffer has been read
         t1 = time.perf_counter()
-        cmx.step()                    # the last stage reads the non-finite flag back (synchronises)
+        cvf.step()                    # the last stage reads the non-finite flag back (synchronises)
         t2 = time.perf_counter()
-        cmx.mesh.get_state(out=Out)   # returns after the result is in host memory
+        cvf.mesh.get_state(out=Out)   # returns after the result is in host memory
         t3 = time.perf_counter()
-        phase[0] += t1 - t0
-        phase[1] += t2 - t1
-        phase[2] += t3 - t2
+        for k_, dtk in enumerate((t1 - t0, t2 - t1, t3 - t2)):
+            phase[k_] += dtk
+            phase_min[k_] = min(phase_min[k_], dtk)
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - te0)
     # Plain copy rates of the same pinned buffers (context for the end-to-end number).
@@ -561,8 +583,10 @@ def run_ours(args):
            "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Out.numel() * 8),
            "copy_rates_gbs": rates,
            "phase_ms_per_step": {"set_state": 1e3 * phase[0] / k_e2e, "stages": 1e3 * phase[1] / k_e2e,
-                                 "get_state": 1e3 * phase[2] / k_e2e}}
-    cmx.close()
+                                 "get_state": 1e3 * phase[2] / k_e2e},
+           "phase_ms_min": {"set_state": 1e3 * phase_min[0], "stages": 1e3 * phase_min[1],
+                            "get_state": 1e3 * phase_min[2]}}
+    cvf.close()
     del Qh, Out
 
     prisms = {}
@@ -585,30 +609,35 @@ def run_ours(args):
         for (n, p) in SWEEP:
             row = {"n_edge": n, "n_points": n ** 3 * (p + 1) ** 3}
             dt = None
-            for prec in ("fp64", "mixed"):
+            for prec in ("fp64", "mixed", "mixed_vf32"):
                 c = Case(n, p, prec, dt=dt)
                 dt = c.dt
                 c.step()
                 ms = c.timed(2)
                 row[prec] = n ** 3 * (p + 1) ** 3 * 4 * 2 / (ms * 1e-3)
                 # Per-kernel CUDA-event times and each kernel's fraction of the arithmetic peak of
-                # its precision (FP64: the DFMA rate; double-float: the FP32 FMA rate / 18).
+                # its precision (FP64: the DFMA rate; double-float: the FP32 FMA rate / 18; the
+                # volume kernel with the viscous branch in FP32: its arithmetic mix at those rates).
                 peak = fp64_peak if prec == "fp64" else df_peak
                 k = c.kernels(2, p)
                 row[prec + "_kernels"] = {name: {"avg_ms": v["avg_ms"], "share": v["share"],
                                                  "frac_of_alu_peak": v["gflops"] * 1e9 / peak if v["gflops"] else None}
                                           for name, v in k.items()}
-                row[prec + "_volume_frac"] = k["volume"]["gflops"] * 1e9 / peak
-                row[prec + "_step_frac"] = (sum(perfmodel.flops_per_point(p).values()) * row[prec] / peak)
+                vpeak = perfmodel.mixed_alu_peak(p, df_peak, fp32_peak, True) if prec == "mixed_vf32" else peak
+                if prec == "mixed_vf32":
+                    row[prec + "_kernels"]["volume"]["frac_of_alu_peak"] = k["volume"]["gflops"] * 1e9 / vpeak
+                row[prec + "_volume_frac"] = k["volume"]["gflops"] * 1e9 / vpeak
+                if prec != "mixed_vf32":
+                    row[prec + "_step_frac"] = (sum(perfmodel.flops_per_point(p).values()) * row[prec] / peak)
                 c.close()
             sweep[f"p{p}"] = row
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
-            "config": config("mixed"), "clocks": clocks, "e2e": e2e,
-            "gpu_launches": 4 * 4 * args.steps, "roofline": roofline, "kernels": k_mx,
-            "error_vs_fp64": err, "fp64": fp64, "p_sweep_updates_per_s": sweep,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32+f64", "data": "synthetic",
+            "config": config("mixed_vf32"), "clocks": clocks, "e2e": e2e,
+            "gpu_launches": 4 * 4 * args.steps, "roofline": roofline, "kernels": k_vf,
+            "error_vs_fp64": err_vf, "double_float": double_float, "fp64": fp64, "p_sweep_updates_per_s": sweep,
             "ensemble_64_vortex": ensemble, "prisms_tgv": prisms, "vcjh_hu_48cube_p4": vcjh,
             "tensor_core_interp_64cube_p4": tc_row,
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12}

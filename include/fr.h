@@ -49,7 +49,7 @@ typedef enum {
 enum { FR_HOST = 0, FR_DEVICE = 1 };                       /* where a state pointer lives */
 enum { FR_RUSANOV = 0, FR_ROE = 1 };                       /* inviscid common flux */
 enum { FR_VISC_NONE = 0, FR_VISC_BR2 = 1, FR_VISC_LDG = 2 }; /* viscous treatment */
-enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1, FR_PREC_MIXED_TC = 2 };   /* element arithmetic (fr_physics) */
+enum { FR_PREC_FP64 = 0, FR_PREC_MIXED = 1, FR_PREC_MIXED_TC = 2, FR_PREC_MIXED_VF32 = 3 };  /* fr_physics */
 enum {                                                     /* explicit Runge–Kutta schemes */
   FR_RK44 = 0,      /* classical four-stage, fourth order */
   FR_SSPRK33 = 1,   /* three-stage third-order SSP (Shu–Osher form), SSP coefficient 1 */
@@ -121,9 +121,18 @@ typedef struct {
                            FR_PREC_MIXED_TC: as FR_PREC_MIXED, with the face interpolation (Eq. 2,
                            the solution at the flux points) on the tensor cores: tcgen05.mma in
                            TF32 with FP32 accumulation on exponent-aligned 10-bit slices of the
-                           data and of l(+-1) (error-free splitting, Ozaki et al. 2012), 4 slices
-                           each, combined into double-float; error a few 2^-41 of the line's
-                           largest value (hexahedra; not in fr_batch_create: FR_EUNSUPPORTED) */
+                           data and of l(+-1) (error-free splitting, Ozaki et al. 2012), 5 slices
+                           each, combined into double-float; error at most 2^-44 of the line's
+                           largest value times max |l| (hexahedra; not in fr_batch_create:
+                           FR_EUNSUPPORTED) |
+                           FR_PREC_MIXED_VF32: as FR_PREC_MIXED, with the viscous branch of the
+                           hexahedral volume kernel (corrected gradients of the perturbation from
+                           the element's first point, gradient traces, stress and heat flux) in
+                           plain FP32.  Its error grows like 1/Re (the branch is scaled by the
+                           viscosity): measured normwise <= 7.7e-7 per variable for Re >= 400
+                           (p <= 7, Ma <= 0.5, TGV states), 1e-5 at Re = 20; per entry <= 1.2e-8
+                           S for Re >= 400.  c = 0 only (FR_EUNSUPPORTED otherwise); prisms keep
+                           double-float; not in fr_batch_create */
   double ldg_tau;       /* LDG penalty tau (FR_VISC_LDG): at each interface the side whose face
                            normal (summed over the face) points along (1, sqrt2/2, sqrt3/4)
                            supplies the common solution, the other side the common gradient

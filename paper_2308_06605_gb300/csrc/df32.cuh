@@ -110,6 +110,13 @@ template <> struct Dot<double> {
   __device__ __forceinline__ double get() const { return s; }
 };
 
+template <> struct Dot<float> {
+  float s;
+  __device__ __forceinline__ Dot() : s(0.f) {}
+  __device__ __forceinline__ void add(float c, float x) { s = fmaf(c, x, s); }
+  __device__ __forceinline__ float get() const { return s; }
+};
+
 template <> struct Dot<df32> {
   float s, e;
   __device__ __forceinline__ Dot() : s(0.f), e(0.f) {}
@@ -140,5 +147,25 @@ using ::fmax;
 template <typename T> __device__ __forceinline__ T from_double(double d);
 template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
 template <> __device__ __forceinline__ df32 from_double<df32>(double d) { return df_from(d); }
+template <> __device__ __forceinline__ float from_double<float>(double d) { return __double2float_rn(d); }
+
+// Arithmetic of the viscous branch (gradients, gradient traces, stress and heat flux): the element
+// arithmetic T, or, with FP32_VISCOUS on the double-float path (FR_PREC_MIXED_VF32), plain FP32.
+// These terms are scaled by the viscosity, so their FP32 rounding enters the residual in
+// proportion to 1/Re (the gradients are taken of the perturbation from the element's first point,
+// so large state values do not cancel in FP32).
+template <typename T, bool FP32_VISCOUS> struct GradOf { using type = T; };
+template <> struct GradOf<df32, true> { using type = float; };
+template <typename TG> __device__ __forceinline__ TG to_g(double x);
+template <> __device__ __forceinline__ double to_g<double>(double x) { return x; }
+template <typename TG> __device__ __forceinline__ TG to_g(df32 x);
+template <> __device__ __forceinline__ float to_g<float>(df32 x) { return __fadd_rn(x.hi, x.lo); }
+template <> __device__ __forceinline__ df32 to_g<df32>(df32 x) { return x; }
+template <typename T> __device__ __forceinline__ T from_g(double x);
+template <> __device__ __forceinline__ double from_g<double>(double x) { return x; }
+template <typename T> __device__ __forceinline__ T from_g(float x);
+template <> __device__ __forceinline__ df32 from_g<df32>(float x) { return df(x, 0.f); }
+template <typename T> __device__ __forceinline__ T from_g(df32 x);
+template <> __device__ __forceinline__ df32 from_g<df32>(df32 x) { return x; }
 
 }  // namespace frx

@@ -192,8 +192,11 @@ static fr_status validate_create(const fr_mesh_desc *desc, const fr_physics *phy
     return fail(nullptr, FR_EINVAL, "unknown viscous scheme");
   if (phys->viscous == FR_VISC_LDG && !(phys->ldg_tau >= 0.0))
     return fail(nullptr, FR_EINVAL, "LDG penalty must be non-negative");
-  if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED && phys->precision != FR_PREC_MIXED_TC)
+  if (phys->precision != FR_PREC_FP64 && phys->precision != FR_PREC_MIXED && phys->precision != FR_PREC_MIXED_TC &&
+      phys->precision != FR_PREC_MIXED_VF32)
     return fail(nullptr, FR_EINVAL, "unknown precision");
+  if (phys->precision == FR_PREC_MIXED_VF32 && phys->vcjh_c != 0.0)
+    return fail(nullptr, FR_EUNSUPPORTED, "FR_PREC_MIXED_VF32 is built for the DG-equivalent correction (c = 0)");
   if (!vcjh_in_family(desc->p, phys->vcjh_c))
     return fail(nullptr, FR_EINVAL, "correction parameter c outside the energy-stable family (1 + eta <= 0)");
   if (phys->vcjh_c != 0.0 && desc->n_prism > 0)
@@ -264,9 +267,12 @@ static fr_status finish_create(fr_mesh *m, const fr_physics *phys, uintptr_t str
                       &dp.d.zero, &dp.d.half, &dp.d.one, &dp.d.tau};
     df32 *ff[11] = {&dp.f.gamma, &dp.f.gm1, &dp.f.cT, &dp.f.mu, &dp.f.m2mu3, &dp.f.kappa, &dp.f.eta,
                     &dp.f.zero, &dp.f.half, &dp.f.one, &dp.f.tau};
+    float *sf[11] = {&dp.s.gamma, &dp.s.gm1, &dp.s.cT, &dp.s.mu, &dp.s.m2mu3, &dp.s.kappa, &dp.s.eta,
+                     &dp.s.zero, &dp.s.half, &dp.s.one, &dp.s.tau};
     for (int k = 0; k < 11; ++k) {
       *dd[k] = vals[k];
       *ff[k] = df_split_host(vals[k]);
+      *sf[k] = (float)vals[k];
     }
   }
 
@@ -293,8 +299,10 @@ static fr_status finish_create(fr_mesh *m, const fr_physics *phys, uintptr_t str
   d.p = h.p; d.N = h.N; d.Np = h.Np; d.Nf = h.Nf;
   d.E = h.E; d.n_if = h.n_if; d.n_interior = h.n_interior;
   d.Ep = h.Ep; d.Nt = h.Nt; d.Npp = h.Npp;
-  d.mixed = (phys->precision == FR_PREC_MIXED || phys->precision == FR_PREC_MIXED_TC) ? 1 : 0;
+  d.mixed = (phys->precision == FR_PREC_MIXED || phys->precision == FR_PREC_MIXED_TC ||
+             phys->precision == FR_PREC_MIXED_VF32) ? 1 : 0;
   d.tc = (phys->precision == FR_PREC_MIXED_TC) ? 1 : 0;
+  d.vf32 = (phys->precision == FR_PREC_MIXED_VF32) ? 1 : 0;
   const size_t nsol = ((size_t)h.E * h.Np + (size_t)h.Ep * h.Npp) * 5;
   const size_t G = (size_t)(h.E + h.Ep);
   const size_t Nf = h.Nf;

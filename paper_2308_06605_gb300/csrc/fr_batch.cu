@@ -192,9 +192,10 @@ extern "C" fr_status fr_batch_create(fr_mesh *const *meshes, int32_t n, fr_batch
       delete b;
       return bfail(nullptr, FR_EUNSUPPORTED, "meshes with the eddy-viscosity closure cannot be batched");
     }
-    if (c.m.tc) {
+    if (c.m.tc || c.m.vf32) {
       delete b;
-      return bfail(nullptr, FR_EUNSUPPORTED, "the tensor-core face interpolation (FR_PREC_MIXED_TC) is not batched");
+      return bfail(nullptr, FR_EUNSUPPORTED,
+                   "FR_PREC_MIXED_TC and FR_PREC_MIXED_VF32 meshes are not batched (use FR_PREC_MIXED)");
     }
     if (frx_mesh_has_halo(meshes[i])) {
       delete b;

@@ -282,7 +282,7 @@ __host__ __device__ constexpr int volume_smem_values() { return 35 * N * N * N +
 // One element e handled by `nth` threads of the block (thread index tid in [0, nth)); every
 // thread of the block calls this together (it contains block barriers); inactive sub-blocks
 // (active = false) only take part in the barriers.
-template <int N, typename T, bool VC = false>
+template <int N, typename T, bool VC = false, bool FP32V = false>
 __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool active, double *sm_raw,
                                             const T *__restrict__ Q, const T *__restrict__ metrics,
                                             const int32_t *__restrict__ ef, const T *__restrict__ Qtr,
@@ -291,16 +291,27 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
                                             const double *__restrict__ hel, float *__restrict__ nu_out,
                                             const int8_t *__restrict__ if_up, int64_t n_interior) {
   constexpr int Np = N * N * N, Nf = N * N;
+  using TG = typename GradOf<T, FP32V>::type;   // arithmetic of the viscous branch
+  constexpr bool kPert = !std::is_same<TG, T>::value;
   T *sm = reinterpret_cast<T *>(sm_raw);
-  T *sQ = sm;                 // [5][Np]
-  T *sG = sQ + 5 * Np;        // [15][Np] uncorrected physical gradient, index j*5+v
-  T *sH = sG + 15 * Np;       // [15][Np] transformed flux, index d*5+v
-  T *sdQ = sH + 15 * Np;      // [6][5][Nf] Q^I - Q_own at the flux points
+  T *sQ = sm;                                                // [5][Np]
+  TG *sG = reinterpret_cast<TG *>(sQ + 5 * Np);              // [15][Np] uncorrected physical gradient, j*5+v
+  T *sH = sQ + 20 * Np;                                      // [15][Np] transformed flux, index d*5+v
+  TG *sdQ = reinterpret_cast<TG *>(sH + 15 * Np);            // [6][5][Nf] Q^I - Q_own at the flux points
+  // FP32 viscous branch: Q minus the element's first point, in FP32, in the upper half of the
+  // gradient buffer (the FP32 gradient uses only its lower half).
+  TG *sQg = kPert ? reinterpret_cast<TG *>(sQ + 5 * Np) + 15 * Np : nullptr;   // [5][Np]
   const PhysT<T> &ph = phys_of<T>(dph);
+  const PhysT<TG> &phg = phys_of<TG>(dph);
   const BasisT<T> &B = basis_ref<N, T, VC>(dph);
   const bool viscous = dph.viscous != 0;
   if (active)
-    for (int t = tid; t < 5 * Np; t += nth) sQ[(t % 5) * Np + t / 5] = Q[e * Np * 5 + t];
+    for (int t = tid; t < 5 * Np; t += nth) {
+      const T x = Q[e * Np * 5 + t];
+      sQ[(t % 5) * Np + t / 5] = x;
+      if constexpr (kPert)
+        if (viscous) sQg[(t % 5) * Np + t / 5] = to_g<TG>(x - Q[e * Np * 5 + t % 5]);
+    }
   if (viscous && active) {
     for (int t = tid; t < 6 * Nf; t += nth) {
       const int f = t / Nf, r = t % Nf;
@@ -315,13 +326,14 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
       T w = ph.half;
       if (dph.ldg && I < n_interior) w = side == (if_up[I] ? 0 : 1) ? ph.zero : ph.one;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = w * (oth[v * Nf] - own[v * Nf]);
+      for (int v = 0; v < 5; ++v) sdQ[(f * 5 + v) * Nf + r] = to_g<TG>(w * (oth[v * Nf] - own[v * Nf]));
     }
   }
   __syncthreads();
   const bool pt = active && tid < Np;
   const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
-  T S[9], invJ, q[5], G[15];
+  T S[9], invJ, q[5];
+  TG G[15];
   if (pt) {
     const T *met = metrics + e * 10 * Np + m;
 #pragma unroll
@@ -332,31 +344,35 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     if (viscous) {
       // One variable at a time: reference gradient, its correction, and both transformed to
       // physical components at once (short live ranges; the same operations as a two-pass form).
-      T sj[9];   // S[d][jj] / |J|
+      TG sj[9];   // S[d][jj] / |J|
 #pragma unroll
-      for (int c = 0; c < 9; ++c) sj[c] = S[c] * invJ;
-      const T nhm[3] = {-B.hm[i], -B.hm[j], -B.hm[k]};
+      for (int c = 0; c < 9; ++c) sj[c] = to_g<TG>(S[c] * invJ);
+      const TG nhm[3] = {-to_g<TG>(B.hm[i]), -to_g<TG>(B.hm[j]), -to_g<TG>(B.hm[k])};
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const T *sq = sQ + v * Np;
-        Dot<T> a0, a1, a2;
+        const TG *sq;
+        if constexpr (kPert)
+          sq = sQg + v * Np;
+        else
+          sq = sQ + v * Np;
+        Dot<TG> a0, a1, a2;
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          a0.add(B.D[i * N + a], sq[a + N * j + N * N * k]);
-          a1.add(B.D[j * N + a], sq[i + N * a + N * N * k]);
-          a2.add(B.D[k * N + a], sq[i + N * j + N * N * a]);
+          a0.add(to_g<TG>(B.D[i * N + a]), sq[a + N * j + N * N * k]);
+          a1.add(to_g<TG>(B.D[j * N + a]), sq[i + N * a + N * N * k]);
+          a2.add(to_g<TG>(B.D[k * N + a]), sq[i + N * j + N * N * a]);
         }
-        const T gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
+        const TG gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
         a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
-        a0.add(B.hp[i], sdQ[(1 * 5 + v) * Nf + j + N * k]);
+        a0.add(to_g<TG>(B.hp[i]), sdQ[(1 * 5 + v) * Nf + j + N * k]);
         a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
-        a1.add(B.hp[j], sdQ[(3 * 5 + v) * Nf + i + N * k]);
+        a1.add(to_g<TG>(B.hp[j]), sdQ[(3 * 5 + v) * Nf + i + N * k]);
         a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
-        a2.add(B.hp[k], sdQ[(5 * 5 + v) * Nf + i + N * j]);
-        const T gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
+        a2.add(to_g<TG>(B.hp[k]), sdQ[(5 * 5 + v) * Nf + i + N * j]);
+        const TG gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
-          Dot<T> du, dc;
+          Dot<TG> du, dc;
           du.add(sj[0 * 3 + jj], gu0);
           du.add(sj[1 * 3 + jj], gu1);
           du.add(sj[2 * 3 + jj], gu2);
@@ -426,7 +442,25 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     const T u[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
     const T p = ph.gm1 * (q[4] - ph.half * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
     T tau[3][3], hq[3];
-    if (viscous) viscous_stress<T>(q, u, ri, G, ph, visc_with(ph, rho_nu, dph), tau, hq);
+    if (viscous) {
+      if constexpr (kPert) {
+        TG qg[5], ug[3], taug[3][3], hqg[3];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qg[v] = to_g<TG>(q[v]);
+        const TG rig = phg.one / qg[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ug[c] = qg[1 + c] * rig;
+        viscous_stress<TG>(qg, ug, rig, G, phg, visc_with(phg, to_g<TG>(rho_nu), dph), taug, hqg);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          hq[a] = from_g<T>(hqg[a]);
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2) tau[a][b2] = from_g<T>(taug[a][b2]);
+        }
+      } else {
+        viscous_stress<T>(q, u, ri, G, ph, visc_with(ph, rho_nu, dph), tau, hq);
+      }
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       T f[5];
@@ -450,15 +484,18 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
       const int side = (packed >> 3) & 1;
       const int slot = slot_of(packed & 7, r % N, r / N, N);
       T *dst = Gtr + (I * 2 + side) * 15 * Nf + slot;
-      const T lj = ph.eta * liftfac[((e * 6 + f) * 3 + jj) * Nf + r];
+      const TG lj = to_g<TG>(ph.eta * liftfac[((e * 6 + f) * 3 + jj) * Nf + r]);
+      TG lg[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) lg[c] = to_g<TG>(l[c]);
 #pragma unroll 1
       for (int v = 0; v < 5; ++v) {
-        const T *sg = sG + (jj * 5 + v) * Np + base;
-        Dot<T> acc;
+        const TG *sg = sG + (jj * 5 + v) * Np + base;
+        Dot<TG> acc;
 #pragma unroll
-        for (int c = 0; c < N; ++c) acc.add(l[c], sg[c * sd]);
+        for (int c = 0; c < N; ++c) acc.add(lg[c], sg[c * sd]);
         acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
-        dst[(jj * 5 + v) * Nf] = acc.get();
+        dst[(jj * 5 + v) * Nf] = from_g<T>(acc.get());
       }
     }
   }
@@ -480,15 +517,15 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   }
 }
 
-template <int N, typename T>
+template <int N, typename T, bool FP32V = false>
 __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
     k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
              const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
              DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out,
              const int8_t *__restrict__ if_up, int64_t n_interior) {
   extern __shared__ double sm_raw[];
-  volume_body<N, T>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr, Rpart,
-                    dph, hel, nu_out, if_up, n_interior);
+  volume_body<N, T, false, FP32V>(blockIdx.x, threadIdx.x, blockDim.x, true, sm_raw, Q, metrics, ef, Qtr, liftfac, Gtr,
+                                  Rpart, dph, hel, nu_out, if_up, n_interior);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -31,6 +31,7 @@ struct DevPhys {
   const float *cscale;     // [23] input mean (11), input std (11), output scale (device)
   PhysT<double> d;
   PhysT<df32> f;
+  PhysT<float> s;          // the viscous branch of the double-float path
   // Source term S of Eq. 3 (fr_set_source): body acceleration and sponge, FP64.
   int src_body, src_sponge;
   double accel[3];
@@ -47,6 +48,7 @@ struct DevMesh {
   int64_t E, n_if, n_interior;
   int mixed;        // 1: element arrays hold df32 pairs (same 8-byte slots), Qc holds the state as df32
   int tc;           // 1 (mixed only): face interpolation on the tensor cores (FR_PREC_MIXED_TC)
+  int vf32;         // 1 (mixed only): viscous branch of the volume kernel in FP32 (FR_PREC_MIXED_VF32)
   double *Q, *Un, *acc, *Rpart, *metrics, *liftfac, *normals, *Qtr, *Gtr, *FI, *h, *dtbuf, *Qc, *Unc;
   int32_t *ef, *if_bc;
   int32_t *if_elem;        // [n_if][2] element of each side (-1: boundary), closure only

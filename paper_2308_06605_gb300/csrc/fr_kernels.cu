@@ -94,14 +94,19 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   if (phases & 2) {
     const int threads = volume_threads<N>();
     const size_t smem = sizeof(T) * (35 * Np + 30 * Nf) + (ph.closure ? sizeof(float) * (10 * Np + 1 + 128) : 0);
-    err = cudaFuncSetAttribute(k_volume<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Double-float path with the viscous branch in FP32 (FR_PREC_MIXED_VF32), or the element
+    // arithmetic throughout.
+    auto kern = k_volume<N, T, false>;
+    if constexpr (std::is_same<T, df32>::value)
+      if (m.vf32) kern = k_volume<N, T, true>;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     FR_EV_BEGIN(1);
     if (E > 0 && ph.vc_basis) {
       if ((err = launch_vcjh_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     } else if (E > 0) {
-      k_volume<N, T><<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu, m.if_up,
-                                                         m.n_interior);
+      kern<<<(unsigned)E, threads, smem, st>>>(Qin, met, m.ef, Qtr, lift, Gtr, Rpart, ph, m.h, m.nu, m.if_up,
+                                               m.n_interior);
     }
     if ((err = launch_prism_phase(m, ph, 1, mode, stage, dt, Rout, st)) != cudaSuccess) return err;
     FR_EV_END(1);

@@ -16,6 +16,7 @@ namespace frx {
 template <typename T> __device__ __forceinline__ const PhysT<T> &phys_of(const DevPhys &p);
 template <> __device__ __forceinline__ const PhysT<double> &phys_of<double>(const DevPhys &p) { return p.d; }
 template <> __device__ __forceinline__ const PhysT<df32> &phys_of<df32>(const DevPhys &p) { return p.f; }
+template <> __device__ __forceinline__ const PhysT<float> &phys_of<float>(const DevPhys &p) { return p.s; }
 
 // ------------------------------------------------------------------------------------------
 // Gas dynamics (ideal gas, Stokes hypothesis, constant mu, Fourier heat flux).

@@ -8,7 +8,7 @@
 // "Error-free transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012):
 //   * a line x_a (double-float hi + lo) with sigma = 2^E > max |x| is written as
-//     x = sigma sum_{s=0..3} 2^{-beta (s+1)} X_s + O(2^{-4 beta} sigma), beta = 10, where every X_s is
+//     x = sigma sum_{s=0..4} 2^{-beta (s+1)} X_s + O(2^{-5 beta} sigma), beta = 10, where every X_s is
 //     an integer with |X_0| <= 2^beta, |X_s| <= 2^{beta-1} (round-to-nearest slicing), exactly
 //     representable in TF32;
 //   * each operator row (l(-1) or l(+1)) likewise with its own tau = 2^F > max |l|, slices O_t;
@@ -16,10 +16,13 @@
 //     at once (B, 16 x 8: row 2t + j = slice t of operator row j), so D_s[r][2t + j] =
 //     sum_a X_s[r][a] O_t[j][a]: integers below 8 * 2^{2 beta} = 2^23, hence exact in the FP32
 //     accumulator whatever the order of its additions;
-//   * per output the level sums A_L = sum_{s+t=L} D_s (L = 0..3, each below 2^24: exact) are
-//     combined into a double-float value, sum_L 2^{-beta L} A_L, scaled by sigma tau 2^{-2 beta}.
-// Dropped terms (s or t > 3, s + t > 3) and the last slice's rounding leave an error of a few
-// 2^{-41} sigma tau per output, below the double-float path's own rounding at the magnitude scale.
+//   * per output the level sums A_L = sum_{s+t=L} D_s (L = 0..4; exact below 2^24 for L <= 3,
+//     the last level's rounding is 2^{-24} of a 2^{-40} term) are combined into a double-float
+//     value, sum_L 2^{-beta L} A_L, scaled by sigma tau 2^{-2 beta}.
+// Dropped terms (s + t > 4) and the last slice's rounding leave 2^{-51} sigma tau per output; the
+// double-float result's own rounding (48 bits of a value up to 8 sigma tau) brings the total to at
+// most 2^{-44} sigma tau.  (With four slices, 2^{-41}, the error of a Ma 0.1 continuity residual
+// reached 1e-6 of its largest entry: the trace jump is amplified by the Rusanov dissipation.)
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,8 +36,9 @@ namespace frx {
 namespace {
 
 constexpr int kBeta = 10;
-constexpr int kSlices = 4;
+constexpr int kSlices = 5;
 constexpr int kTcThreads = 128;
+constexpr int kTmemCols = 128;                   // 5 accumulators of 16 columns, rounded to a power of 2
 constexpr long long kWaitLimit = 4000000000ll;   // clock cycles (about 2 s) before a wait gives up
 
 // Operator slices per order (index N - 1): the B tile of 16 rows x K = 8 in the K-major core-matrix
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(kTcThreads) k_interp_tc(const df32 *__restrict
     s_issued = 0;
   }
   if (warp == 0) {
-    tc::tmem_alloc(&tbase, 64);
+    tc::tmem_alloc(&tbase, kTmemCols);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -164,11 +168,15 @@ __global__ void __launch_bounds__(kTcThreads) k_interp_tc(const df32 *__restrict
       X[0][a] = rintf(u);
       u = (u - X[0][a]) * up;
       X[1][a] = rintf(u);
-      u = fmaf(x[a].lo, sc_lo, (u - X[1][a]) * up);
-      X[2][a] = rintf(u);
-      u = (u - X[2][a]) * up;
+      // hi's remaining bits plus lo, kept exact as a pair: the third slice rounds their sum and
+      // the pair's rounding error is carried into the next remainder.
+      const df32 w = two_sum((u - X[1][a]) * up, x[a].lo * sc_lo);
+      X[2][a] = rintf(w.hi);
+      u = ((w.hi - X[2][a]) + w.lo) * up;
       X[3][a] = rintf(u);
-      if (!nonzero) X[0][a] = X[1][a] = X[2][a] = X[3][a] = 0.f;
+      u = (u - X[3][a]) * up;
+      X[4][a] = rintf(u);
+      if (!nonzero) X[0][a] = X[1][a] = X[2][a] = X[3][a] = X[4][a] = 0.f;
     }
   }
 #pragma unroll
@@ -203,12 +211,18 @@ __global__ void __launch_bounds__(kTcThreads) k_interp_tc(const df32 *__restrict
     tc::mbar_wait(&bar, 1, kWaitLimit);
   }
   if (done) {
-    float D[kSlices][8];
+    // Columns 2t + j of D_s for s + t <= 4: 10 columns of D_0, 8 of the others.
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
+    float D0[16], D[kSlices][8];
+    tc::tmem_ld16(tbase + lane, D0);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) tc::tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + 16 * s, D[s]);
+    for (int s = 1; s < kSlices; ++s) tc::tmem_ld8(tbase + lane + 16 * s, D[s]);
     tc::tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) D[0][c] = D0[c];
     if (live) {
-      const float sigma = pow2f(Ex), m10 = pow2f(-kBeta), m20 = pow2f(-2 * kBeta), m30 = pow2f(-3 * kBeta);
+      const float sigma = pow2f(Ex), m10 = pow2f(-kBeta), m20 = pow2f(-2 * kBeta), m30 = pow2f(-3 * kBeta),
+                  m40 = pow2f(-4 * kBeta);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         // Level sums (exact: integers below 2^24), then sum_L 2^{-beta L} A_L as a double-float.
@@ -216,8 +230,9 @@ __global__ void __launch_bounds__(kTcThreads) k_interp_tc(const df32 *__restrict
         const float A1 = D[0][2 + j] + D[1][j];
         const float A2 = D[0][4 + j] + D[1][2 + j] + D[2][j];
         const float A3 = D[0][6 + j] + D[1][4 + j] + D[2][2 + j] + D[3][j];
+        const float A4 = D0[8 + j] + D[1][6 + j] + D[2][4 + j] + D[3][2 + j] + D[4][j];
         const df32 h = two_sum(A0, A1 * m10);
-        const float lo = fmaf(A3, m30, A2 * m20);
+        const float lo = fmaf(A4, m40, fmaf(A3, m30, A2 * m20));
         df32 r = two_sum(h.hi, h.lo + lo);
         const float scale = sigma * c_tc_tau[N - 1][j] * m20;
         r.hi *= scale;
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads) k_interp_tc(const df32 *__restrict
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 64);
+  if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
 template <int N>

@@ -22,7 +22,7 @@ STATUS_NAMES = ["FR_OK", "FR_EINVAL", "FR_ENOMEM", "FR_ECUDA", "FR_EMESH", "FR_E
 FR_HOST, FR_DEVICE = 0, 1
 FR_RK44, FR_SSPRK33, FR_SSPRK104 = 0, 1, 2
 FR_RESIDUAL_ONLY = -1
-FR_PREC_FP64, FR_PREC_MIXED, FR_PREC_MIXED_TC = 0, 1, 2
+FR_PREC_FP64, FR_PREC_MIXED, FR_PREC_MIXED_TC, FR_PREC_MIXED_VF32 = 0, 1, 2, 3
 RK_STAGES = {FR_RK44: 4, FR_SSPRK33: 3, FR_SSPRK104: 10}
 
 

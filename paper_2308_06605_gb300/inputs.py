@@ -515,7 +515,7 @@ class Physics:
     ldg_tau: float = 0.1        # LDG penalty
     vcjh_c: float = 0.0
     precision: int = 0          # 0 = FP64, 1 = double-float element operators, 2 = the same with the face
-                                # interpolation on the tensor cores
+                                # interpolation on the tensor cores, 3 = with the viscous branch in FP32
 
 
 def tgv_physics(Ma: float = 0.1, Re: float = 1600.0, gamma: float = 1.4, Pr: float = 0.71) -> Physics:

@@ -41,6 +41,28 @@ def flops_per_point(p: int, viscous: bool = True) -> dict:
     return f
 
 
+def volume_split(p: int) -> tuple:
+    """(flops of the viscous branch, flops of the rest) per point of the volume kernel: the branch
+    FR_PREC_MIXED_VF32 runs in FP32 (reference gradient, its correction, the jumps, the physical
+    gradient, the stress and heat flux, the gradient traces) and the rest (inviscid fluxes,
+    transformation, divergence) in double-float."""
+    N = p + 1
+    fp_pt = 6.0 / N
+    visc = 2 * 3 * 5 * N + 3 * 5 * 2 * 2 + fp_pt * 5 * 2 + _PHYS_GRAD + _VISCOUS + fp_pt * 15 * (2 * N + 2)
+    rest = 2 * 3 * 5 * N + _INVISCID + _TRANSFORM
+    return visc, rest
+
+
+def mixed_alu_peak(p: int, df_peak: float, fp32_peak: float, fp32_viscous: bool) -> float:
+    """Algorithmic-flop peak of the mixed volume kernel for its arithmetic mix: all double-float
+    (df_peak), or the viscous branch at the FP32 rate and the rest in double-float (the time of
+    each part at its own peak, added)."""
+    if not fp32_viscous:
+        return df_peak
+    visc, rest = volume_split(p)
+    return (visc + rest) / (rest / df_peak + visc / fp32_peak)
+
+
 def bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dict:
     N = p + 1
     Np, Nf = N ** 3, N ** 2
