@@ -127,11 +127,14 @@ typedef struct {
                            FR_EUNSUPPORTED) |
                            FR_PREC_MIXED_VF32: as FR_PREC_MIXED, with the viscous branch of the
                            hexahedral volume kernel (corrected gradients of the perturbation from
-                           the element's first point, gradient traces, stress and heat flux) in
-                           plain FP32.  Its error grows like 1/Re (the branch is scaled by the
-                           viscosity): measured normwise <= 7.7e-7 per variable for Re >= 400
-                           (p <= 7, Ma <= 0.5, TGV states), 1e-5 at Re = 20; per entry <= 1.2e-8
-                           S for Re >= 400.  c = 0 only (FR_EUNSUPPORTED otherwise); prisms keep
+                           the element's first point, gradient traces, stress and heat flux) and
+                           the interface viscous flux in plain FP32.  Its error is FP32 rounding of
+                           the viscous terms amplified by the second derivative: about 1e-6 of the
+                           viscous part of the residual, so relative to the residual it grows
+                           like 1/Re and with the viscous share (measured normwise <= 7.7e-7 per
+                           variable on perturbed TGV states at Re >= 400, p <= 7; 1.9e-6 at the
+                           initial TGV state at Re 1600, whose residual is almost purely viscous;
+                           1e-5 at Re = 20).  c = 0 only (FR_EUNSUPPORTED otherwise); prisms keep
                            double-float; not in fr_batch_create */
   double ldg_tau;       /* LDG penalty tau (FR_VISC_LDG): at each interface the side whose face
                            normal (summed over the face) points along (1, sqrt2/2, sqrt3/4)

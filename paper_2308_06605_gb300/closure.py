@@ -180,7 +180,7 @@ def stable_dt(h, p, lam=11.5, cfl=0.3):
 
 
 def experiment(n=16, p_fine=4, p_coarse=2, Re=1600.0, train_seeds=(1, 2, 3, 4), eval_seed=0, t0=2.0, t1=6.0,
-               dt_snap=0.1, epochs=60):
+               dt_snap=0.1, epochs=60, fine_precision=None):
     """Generate data, train, and compare the coarse runs with and without the closure against the
     filtered fine run of a held-out seed.  Returns a summary dict."""
     phys = I.tgv_physics(Ma=0.1, Re=Re)
@@ -188,7 +188,11 @@ def experiment(n=16, p_fine=4, p_coarse=2, Re=1600.0, train_seeds=(1, 2, 3, 4), 
     dt_f = dt_snap / max(1, int(np.ceil(dt_snap / stable_dt(h, p_fine))))
     times = list(np.round(np.arange(t0, t1 + 1e-9, dt_snap), 10))
     phys_f = I.tgv_physics(Ma=0.1, Re=Re)
-    phys_f.precision = 1
+    # Fine runs on the double-float path; from Re 400 up its FP32 viscous branch stays within the
+    # stated error (FR_PREC_MIXED_VF32), so it is used there.
+    if fine_precision is None:
+        fine_precision = fr.FR_PREC_MIXED_VF32 if Re >= 400.0 else fr.FR_PREC_MIXED
+    phys_f.precision = fine_precision
     Xs, nus = [], []
     for s in train_seeds:
         snaps = fine_run(n, p_fine, s, times, phys_f, dt_f)
@@ -237,3 +241,36 @@ def experiment(n=16, p_fine=4, p_coarse=2, Re=1600.0, train_seeds=(1, 2, 3, 4), 
             "eps_ref": e_ref.tolist(), "eps_plain": dissipation(K_plain, dt_snap).tolist(),
             "eps_closure": dissipation(K_model, dt_snap).tolist(), "times": times,
             "params": params, "scales": scales}
+
+
+def main(argv=None):
+    """Run the pipeline and print its summary as one JSON line (without the network's weights).
+    The learned-closure configuration: python -m paper_2308_06605_gb300.closure --n 32 --p-fine 6
+    --p-coarse 2 --re 5000 --seeds 1 2 3 4 5 --t0 1.0 --t1 2.0."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--p-fine", type=int, default=4)
+    ap.add_argument("--p-coarse", type=int, default=2)
+    ap.add_argument("--re", type=float, default=1600.0)
+    ap.add_argument("--seeds", type=int, nargs="+", default=[1, 2, 3, 4])
+    ap.add_argument("--eval-seed", type=int, default=0)
+    ap.add_argument("--t0", type=float, default=2.0)
+    ap.add_argument("--t1", type=float, default=6.0)
+    ap.add_argument("--dt-snap", type=float, default=0.1)
+    ap.add_argument("--epochs", type=int, default=60)
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    r = experiment(n=a.n, p_fine=a.p_fine, p_coarse=a.p_coarse, Re=a.re, train_seeds=tuple(a.seeds),
+                   eval_seed=a.eval_seed, t0=a.t0, t1=a.t1, dt_snap=a.dt_snap, epochs=a.epochs)
+    r.pop("params")
+    r.pop("scales")
+    r["wall_s"] = time.perf_counter() - t0
+    r["train_seeds"] = list(a.seeds)
+    print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
 // 3. Common normal flux at the flux points of two-sided interfaces (Rusanov + BR2).  The
 // inviscid part (pressure/energy recovery) is FP64 in both paths.
 // ------------------------------------------------------------------------------------------
-template <int N, typename T>
+template <int N, typename T, bool FP32V = false>
 __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                                            const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if,
                                            const DevPhys &dph, const int32_t *__restrict__ if_elem,
@@ -572,7 +572,37 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] = ph.half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
   }
-  if (dph.viscous) {
+  if constexpr (!std::is_same<typename GradOf<T, FP32V>::type, T>::value) {
+    if (dph.viscous) {
+      // FR_PREC_MIXED_VF32: the whole viscous part in FP32 (the gradient traces written by the
+      // volume kernel's FP32 branch are exact FP32 values).
+      using TG = typename GradOf<T, FP32V>::type;
+      const PhysT<TG> &phg = phys_of<TG>(dph);
+      TG qg[5], Gg[15], ng[3], Fv[3][5];
+      const int sup = (dph.ldg && if_up[I]) ? 0 : 1;
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        qg[v] = dph.ldg ? to_g<TG>(sup == 0 ? qL[v] : qR[v]) : phg.half * (to_g<TG>(qL[v]) + to_g<TG>(qR[v]));
+#pragma unroll
+      for (int c = 0; c < 15; ++c) {
+        const TG g0 = to_g<TG>(Gtr[(I * 2 + 0) * 15 * Nf + c * Nf + q]);
+        const TG g1 = to_g<TG>(Gtr[(I * 2 + 1) * 15 * Nf + c * Nf + q]);
+        Gg[c] = dph.ldg ? (sup == 0 ? g1 : g0) : phg.half * (g0 + g1);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ng[c] = to_g<TG>(nT[c]);
+      TG rho_nu = phg.zero;
+      if (dph.closure) rho_nu = qg[0] * (TG)(0.5 * ((double)nu[if_elem[2 * I]] + (double)nu[if_elem[2 * I + 1]]));
+      viscous_flux<TG>(qg, Gg, phg, visc_with(phg, rho_nu, dph), Fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[v] -= from_g<T>(Fv[0][v] * ng[0] + Fv[1][v] * ng[1] + Fv[2][v] * ng[2]);
+      if (dph.ldg) {
+        const T tn = ph.tau * nn;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] += tn * (qL[v] - qR[v]);
+      }
+    }
+  } else if (dph.viscous) {
     T qc[5], G[15];
     if (dph.ldg) {
       // LDG: the supplying side's solution, the other side's gradient.
@@ -606,13 +636,13 @@ __device__ __forceinline__ void iface_body(int64_t t, const T *__restrict__ Qtr,
 
 // 5 resident blocks of 128 threads (96 registers, a few spills): the double-float interface
 // kernel measured 4 % faster than with 128 registers and 4 blocks; the FP64 one is unchanged.
-template <int N, typename T>
+template <int N, typename T, bool FP32V = false>
 __global__ void __launch_bounds__(128, 5) k_iface_flux(const T *__restrict__ Qtr, const T *__restrict__ Gtr,
                              const T *__restrict__ normals, T *__restrict__ FI, int64_t n_if, DevPhys dph,
                              const int32_t *__restrict__ if_elem, const float *__restrict__ nu,
                              const int8_t *__restrict__ if_up) {
-  iface_body<N, T>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem, nu,
-                   if_up);
+  iface_body<N, T, FP32V>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, Qtr, Gtr, normals, FI, n_if, dph, if_elem,
+                          nu, if_up);
 }
 
 // ------------------------------------------------------------------------------------------

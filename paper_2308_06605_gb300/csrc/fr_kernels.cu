@@ -114,9 +114,12 @@ static cudaError_t residual_impl(const DevMesh &m, const DevPhys &ph, int mode, 
   if (phases & 4) {
     const int64_t n = m.n_interior * Nf;
     FR_EV_BEGIN(2);
-    if (n > 0 && !tri)
-      k_iface_flux<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu,
-                                                                       m.if_up);
+    if (n > 0 && !tri) {
+      auto ik = k_iface_flux<N, T, false>;
+      if constexpr (std::is_same<T, df32>::value)
+        if (m.vf32) ik = k_iface_flux<N, T, true>;
+      ik<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph, m.if_elem, m.nu, m.if_up);
+    }
     if (n > 0 && tri)
       k_iface_flux_tri<N, T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Qtr, Gtr, nrm, FI, m.n_interior, ph,
                                                                          m.if_elem, m.nu, m.if_tri, m.if_up);

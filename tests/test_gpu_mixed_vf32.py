@@ -1,11 +1,14 @@
 """Double-float path with the viscous branch in FP32 (FR_PREC_MIXED_VF32) vs the FP64 oracle.
 
 The viscous branch (corrected gradients of the perturbation from each element's first point,
-gradient traces, stress and heat flux) is scaled by the viscosity, so its FP32 rounding enters
-the residual in proportion to 1/Re.  Stated error for Re >= 400 (Ma <= 0.5, p <= 7):
+gradient traces, stress and heat flux, the interface viscous flux) runs in FP32; its rounding is
+about 1e-6 of the viscous part of the residual, so relative to the residual it grows like 1/Re
+and with the viscous share.  Asserted on perturbed TGV states for Re >= 400 (Ma <= 0.5, p <= 7):
   per entry   |R - R_oracle| <= 2e-8 * S
   normwise    max|R - R_oracle| / max|R_oracle| <= 1e-6 per variable.
-The errors are printed per variable (run with -s); a low-Re case documents the growth."""
+(States whose residual is almost purely viscous, like the initial TGV state of the benchmark,
+exceed the normwise figure: 1.9e-6 there.)  The errors are printed per variable (run with -s); a
+low-Re case documents the growth."""
 import numpy as np
 import pytest
 
