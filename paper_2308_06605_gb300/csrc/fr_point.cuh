@@ -231,31 +231,14 @@ __device__ __forceinline__ void contravariant_flux(const T q[5], const T u[3], T
 // registers (acc, U_n) and the stage state (FP64 Q, or its double-float copy Qc on the mixed
 // path) and ORs a non-finite result into *flag at the last stage.
 // ------------------------------------------------------------------------------------------
-// Exact widening of an FP32 value to FP64 with integer operations (off the FP64 pipe, which the RK
-// update of the double-float path saturates): sign, exponent rebias (127 -> 1023), mantissa shifted
-// into place.  FP32 subnormals (below 2^-126) become zero, infinities and NaNs keep their class.
-__device__ __forceinline__ double widen_f32(float x) {
-  const uint32_t u = __float_as_uint(x);
-  const uint32_t e = (u >> 23) & 0xffu;
-  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
-  const uint64_t mant = (uint64_t)(u & 0x7fffffu) << 29;
-  const uint64_t ex = e == 0 ? 0 : (e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u));
-  return __longlong_as_double((long long)(sign | (ex << 52) | (e == 0 ? 0 : mant)));
-}
-
 template <typename T>
 __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int mode, int stage, double dt,
                                              double *__restrict__ Rout, double *__restrict__ Q, T *__restrict__ Qc,
                                              double *__restrict__ Un, T *__restrict__ Unc, double *__restrict__ acc,
                                              int *__restrict__ flag, const DevPhys &dph) {
-  // FP64 residual: needed by the output, the source terms, the SSP schemes and the FP64 path; the
-  // plain RK44 update of the double-float path below works on the double-float value directly.
-  const bool plain_df_rk = std::is_same<T, df32>::value && mode == MODE_RK && !dph.src_body && !dph.src_sponge;
   double rd[5];
-  if (!plain_df_rk) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) rd[v] = to_double(rv[v] * s);
-  }
+  for (int v = 0; v < 5; ++v) rd[v] = to_double(rv[v] * s);
   if (dph.src_body || dph.src_sponge) {
     // Source term at the state the residual was evaluated on (the element kernels' input).
     double q[5];
@@ -336,19 +319,14 @@ __device__ __forceinline__ void finish_point(int64_t t, const T rv[5], T s, int 
       }
       return;
     }
-    const double bdt = bk * dt;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const int64_t o = t * 5 + v;
-      // bk dt R = bk dt (hi + lo): two FMAs on the exactly widened parts, no FP64 conversions; with
-      // a source term (only the last stage reaches here) the FP64 residual including it.
-      const T r = rv[v] * s;
-      const double rh = plain_df_rk ? widen_f32(r.hi) : rd[v], rl = plain_df_rk ? widen_f32(r.lo) : 0.0;
       if (stage < 3) {
-        acc[o] = fma(bdt, rh, fma(bdt, rl, stage == 0 ? 0.0 : acc[o]));
-        Qc[o] = Unc[o] + adt * r;
+        acc[o] = fma(bk * dt, rd[v], stage == 0 ? 0.0 : acc[o]);
+        Qc[o] = Unc[o] + adt * (rv[v] * s);
       } else {
-        const double nv = fma(bdt, rh, fma(bdt, rl, Un[o] + acc[o]));
+        const double nv = fma(bk * dt, rd[v], Un[o] + acc[o]);
         Un[o] = nv;
         Q[o] = nv;
         const T nc = from_double<T>(nv);
