@@ -52,7 +52,7 @@ def derivative_1d(p):
 
 def coarse_state(Qf, p_fine, p_coarse):
     """Filtered conserved state on the coarse points: [E][Nc^3][5]."""
-    return np.einsum('cm,emv->ecv', filter_3d(p_fine, p_coarse), Qf)
+    return np.matmul(filter_3d(p_fine, p_coarse), Qf)
 
 
 def features_targets(Qf, h, p_fine, p_coarse, with_transfer=False):
@@ -61,14 +61,15 @@ def features_targets(Qf, h, p_fine, p_coarse, with_transfer=False):
     F = filter_3d(p_fine, p_coarse)
     rho = Qf[..., 0]
     u = Qf[..., 1:4] / rho[..., None]
-    ub = np.einsum('cm,emi->eci', F, u)                           # filtered velocity
-    uu = np.einsum('cm,emij->ecij', F, u[..., :, None] * u[..., None, :])
+    E = Qf.shape[0]
+    ub = np.matmul(F, u)                                          # filtered velocity [E][Nc^3][3]
+    uu = np.matmul(F, (u[..., :, None] * u[..., None, :]).reshape(E, -1, 9)).reshape(E, -1, 3, 3)
     tau = uu - ub[..., :, None] * ub[..., None, :]
     Nc = p_coarse + 1
     D = derivative_1d(p_coarse) * (2.0 / h)
     Id = np.eye(Nc)
     Dops = [np.kron(Id, np.kron(Id, D)), np.kron(Id, np.kron(D, Id)), np.kron(D, np.kron(Id, Id))]
-    grad = np.stack([np.einsum('cm,emi->eci', Dops[j], ub) for j in range(3)], axis=-1)   # du_i/dx_j
+    grad = np.stack([np.matmul(Dops[j], ub) for j in range(3)], axis=-1)   # du_i/dx_j
     S = 0.5 * (grad + np.swapaxes(grad, -1, -2))
     _, w = gl_nodes(Nc)
     W = np.kron(w, np.kron(w, w)) / 8.0                           # element-mean weights
@@ -180,9 +181,11 @@ def stable_dt(h, p, lam=11.5, cfl=0.3):
 
 
 def experiment(n=16, p_fine=4, p_coarse=2, Re=1600.0, train_seeds=(1, 2, 3, 4), eval_seed=0, t0=2.0, t1=6.0,
-               dt_snap=0.1, epochs=60, fine_precision=None):
+               dt_snap=0.1, epochs=60, fine_precision=None, log=None):
     """Generate data, train, and compare the coarse runs with and without the closure against the
-    filtered fine run of a held-out seed.  Returns a summary dict."""
+    filtered fine run of a held-out seed.  Returns a summary dict; log (a callable taking one
+    string) receives a progress line after each stage."""
+    log = log or (lambda msg: None)
     phys = I.tgv_physics(Ma=0.1, Re=Re)
     h = 2 * np.pi / n
     dt_f = dt_snap / max(1, int(np.ceil(dt_snap / stable_dt(h, p_fine))))
@@ -196,14 +199,18 @@ def experiment(n=16, p_fine=4, p_coarse=2, Re=1600.0, train_seeds=(1, 2, 3, 4), 
     Xs, nus = [], []
     for s in train_seeds:
         snaps = fine_run(n, p_fine, s, times, phys_f, dt_f)
+        log(f"fine run seed {s}: {len(times)} snapshots, dt {dt_f:.4g}")
         for tt in times:
             X, nu = features_targets(snaps[tt], h, p_fine, p_coarse)
             Xs.append(X)
             nus.append(nu)
+        del snaps
     X = np.concatenate(Xs)
     nu = np.concatenate(nus)
     params, scales, losses = train(X, nu, p_coarse, epochs=epochs)
+    log(f"trained on {X.shape[0]} samples: loss {losses[0]:.4g} -> {losses[-1]:.4g}")
     ref = fine_run(n, p_fine, eval_seed, times, phys_f, dt_f)
+    log(f"held-out fine run seed {eval_seed}")
     # A priori, on the held-out seed, through the solver's own in-kernel (BF16) inference: the
     # coarse mesh holds the filtered state; its residual evaluation computes nu_t per element.
     # Sub-grid energy transfer Pi = -<tau^d:S> vs the model 2 nu_t <S:S>, against no model (0)
@@ -262,9 +269,11 @@ def main(argv=None):
     ap.add_argument("--dt-snap", type=float, default=0.1)
     ap.add_argument("--epochs", type=int, default=60)
     a = ap.parse_args(argv)
+    import sys
     t0 = time.perf_counter()
+    log = lambda msg: print(f"[{time.perf_counter() - t0:8.1f} s] {msg}", file=sys.stderr, flush=True)  # noqa: E731
     r = experiment(n=a.n, p_fine=a.p_fine, p_coarse=a.p_coarse, Re=a.re, train_seeds=tuple(a.seeds),
-                   eval_seed=a.eval_seed, t0=a.t0, t1=a.t1, dt_snap=a.dt_snap, epochs=a.epochs)
+                   eval_seed=a.eval_seed, t0=a.t0, t1=a.t1, dt_snap=a.dt_snap, epochs=a.epochs, log=log)
     r.pop("params")
     r.pop("scales")
     r["wall_s"] = time.perf_counter() - t0
