@@ -108,6 +108,7 @@ template <> struct Dot<double> {
   __device__ __forceinline__ Dot() : s(0.0) {}
   __device__ __forceinline__ void add(double c, double x) { s = fma(c, x, s); }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double raw() const { return s; }
 };
 
 template <> struct Dot<float> {
@@ -115,6 +116,7 @@ template <> struct Dot<float> {
   __device__ __forceinline__ Dot() : s(0.f) {}
   __device__ __forceinline__ void add(float c, float x) { s = fmaf(c, x, s); }
   __device__ __forceinline__ float get() const { return s; }
+  __device__ __forceinline__ float raw() const { return s; }
 };
 
 template <> struct Dot<df32> {
@@ -135,6 +137,9 @@ template <> struct Dot<df32> {
     const df32 r = two_sum(s, e);
     return fast_two_sum(r.hi, r.lo);
   }
+  // The same value s + e with one fast_two_sum: normalised when |s| >= |e|; under cancellation
+  // (|e| > |s|) an unevaluated pair whose sum is the dot product to the same absolute error.
+  __device__ __forceinline__ df32 raw() const { return fast_two_sum(s, e); }
 };
 
 __device__ __forceinline__ df32 fabs(df32 x) { return x.hi < 0.f ? -x : x; }

@@ -304,7 +304,19 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   const PhysT<T> &ph = phys_of<T>(dph);
   const PhysT<TG> &phg = phys_of<TG>(dph);
   const BasisT<T> &B = basis_ref<N, T, VC>(dph);
+  // Sums of products end with Dot::raw(): the compensated sum s + e renormalised by one
+  // fast_two_sum only (an error of the order of 2^-48 of the sum of the terms' magnitudes).
   const bool viscous = dph.viscous != 0;
+  const bool pt = active && tid < Np;
+  const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
+  // The point's metric terms are loaded before the staging loops so that their latency overlaps them.
+  T S[9], invJ, q[5];
+  if (pt) {
+    const T *met = metrics + e * 10 * Np + m;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
+    invJ = met[9 * Np];
+  }
   if (active)
     for (int t = tid; t < 5 * Np; t += nth) {
       const T x = Q[e * Np * 5 + t];
@@ -330,15 +342,8 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
     }
   }
   __syncthreads();
-  const bool pt = active && tid < Np;
-  const int m = tid < Np ? tid : 0, i = m % N, j = (m / N) % N, k = m / (N * N);
-  T S[9], invJ, q[5];
   TG G[15];
   if (pt) {
-    const T *met = metrics + e * 10 * Np + m;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) S[c] = met[c * Np];
-    invJ = met[9 * Np];
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v] = sQ[v * Np + m];
     if (viscous) {
@@ -348,7 +353,13 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
 #pragma unroll
       for (int c = 0; c < 9; ++c) sj[c] = to_g<TG>(S[c] * invJ);
       const TG nhm[3] = {-to_g<TG>(B.hm[i]), -to_g<TG>(B.hm[j]), -to_g<TG>(B.hm[k])};
-#pragma unroll
+      // The variable loop stays rolled (a smaller instruction footprint): the corrected gradient
+      // goes through shared memory, in this thread's own entries of the transformed-flux buffer,
+      // which only this thread writes later (R gradient values of type TG per entry of type T).
+      constexpr int R = sizeof(T) / sizeof(TG);
+      TG *sGc = reinterpret_cast<TG *>(sH);
+      auto gslot = [&](int c) { return ((c / R) * Np + m) * R + c % R; };
+#pragma unroll 1
       for (int v = 0; v < 5; ++v) {
         const TG *sq;
         if constexpr (kPert)
@@ -362,14 +373,14 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
           a1.add(to_g<TG>(B.D[j * N + a]), sq[i + N * a + N * N * k]);
           a2.add(to_g<TG>(B.D[k * N + a]), sq[i + N * j + N * N * a]);
         }
-        const TG gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
+        const TG gu0 = a0.raw(), gu1 = a1.raw(), gu2 = a2.raw();
         a0.add(nhm[0], sdQ[(0 * 5 + v) * Nf + j + N * k]);
         a0.add(to_g<TG>(B.hp[i]), sdQ[(1 * 5 + v) * Nf + j + N * k]);
         a1.add(nhm[1], sdQ[(2 * 5 + v) * Nf + i + N * k]);
         a1.add(to_g<TG>(B.hp[j]), sdQ[(3 * 5 + v) * Nf + i + N * k]);
         a2.add(nhm[2], sdQ[(4 * 5 + v) * Nf + i + N * j]);
         a2.add(to_g<TG>(B.hp[k]), sdQ[(5 * 5 + v) * Nf + i + N * j]);
-        const TG gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
+        const TG gc0 = a0.raw(), gc1 = a1.raw(), gc2 = a2.raw();
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
           Dot<TG> du, dc;
@@ -379,11 +390,14 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
           dc.add(sj[0 * 3 + jj], gc0);
           dc.add(sj[1 * 3 + jj], gc1);
           dc.add(sj[2 * 3 + jj], gc2);
-          G[jj * 5 + v] = dc.get();
+          const TG gc = dc.raw();
+          sGc[gslot(jj * 5 + v)] = gc;
           // Face-gradient source: BR2 the uncorrected gradient (+ eta r_f), LDG the corrected one.
-          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();
+          sG[(jj * 5 + v) * Np + m] = dph.ldg ? gc : du.raw();
         }
       }
+#pragma unroll
+      for (int c = 0; c < 15; ++c) G[c] = sGc[gslot(c)];
     }
   }
   T rho_nu = ph.zero;
@@ -495,7 +509,7 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
 #pragma unroll
         for (int c = 0; c < N; ++c) acc.add(lg[c], sg[c * sd]);
         acc.add(lj, sdQ[(f * 5 + v) * Nf + r]);
-        dst[(jj * 5 + v) * Nf] = from_g<T>(acc.get());
+        dst[(jj * 5 + v) * Nf] = from_g<T>(acc.raw());
       }
     }
   }
@@ -512,7 +526,7 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
         acc.add(B.Dt[j * N + a], h1[i + N * a + N * N * k]);
         acc.add(B.Dt[k * N + a], h2[i + N * j + N * N * a]);
       }
-      out[v] = acc.get();
+      out[v] = acc.raw();
     }
   }
 }
