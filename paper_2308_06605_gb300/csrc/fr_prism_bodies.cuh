@@ -167,8 +167,10 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
       T sj[9];   // S[d][jj] / |J|
 #pragma unroll
       for (int c = 0; c < 9; ++c) sj[c] = S[c] * invJ;
-      // One variable at a time: reference gradient, liftings, correction, physical transform.
-#pragma unroll
+      // One variable at a time: reference gradient, liftings, correction, physical transform.  The
+      // loop stays rolled (a smaller instruction footprint): the corrected gradient goes through this
+      // thread's own entries of the transformed-flux buffer, which only this thread writes later.
+#pragma unroll 1
       for (int v = 0; v < 5; ++v) {
         const T *sq = sQ + v * Np;
         Dot<T> a0, a1, a2;
@@ -180,7 +182,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         }
 #pragma unroll
         for (int c = 0; c < N; ++c) a2.add(D1[c], sq[q + Nt * c]);
-        const T gu0 = a0.get(), gu1 = a1.get(), gu2 = a2.get();
+        const T gu0 = a0.raw(), gu1 = a1.raw(), gu2 = a2.raw();
         // Lifted jumps: quadrilateral faces (edge e = f - 2) and the two triangles.
         Dot<T> l2, l3, l4;
 #pragma unroll
@@ -189,7 +191,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
           l3.add(LQ1[a], sdQ[(3 * 5 + v) * Nf + a + N * k]);
           l4.add(LQ2[a], sdQ[(4 * 5 + v) * Nf + a + N * k]);
         }
-        const T L2 = l2.get(), L3 = l3.get(), L4 = l4.get();
+        const T L2 = l2.raw(), L3 = l3.raw(), L4 = l4.raw();
         sL[(0 * 5 + v) * Np + m] = L2;
         sL[(1 * 5 + v) * Np + m] = L3;
         sL[(2 * 5 + v) * Np + m] = L4;
@@ -200,7 +202,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         a1.add(ph.one, L3);
         a2.add(-hmk, sdQ[(0 * 5 + v) * Nf + q]);
         a2.add(hpk, sdQ[(1 * 5 + v) * Nf + q]);
-        const T gc0 = a0.get(), gc1 = a1.get(), gc2 = a2.get();
+        const T gc0 = a0.raw(), gc1 = a1.raw(), gc2 = a2.raw();
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
           Dot<T> du, dc;
@@ -210,10 +212,13 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
           dc.add(sj[0 * 3 + jj], gc0);
           dc.add(sj[1 * 3 + jj], gc1);
           dc.add(sj[2 * 3 + jj], gc2);
-          G[jj * 5 + v] = dc.get();
-          sG[(jj * 5 + v) * Np + m] = dph.ldg ? G[jj * 5 + v] : du.get();   // LDG: corrected
+          const T gc = dc.raw();
+          sH[(jj * 5 + v) * Np + m] = gc;
+          sG[(jj * 5 + v) * Np + m] = dph.ldg ? gc : du.raw();   // LDG: corrected
         }
       }
+#pragma unroll
+      for (int c = 0; c < 15; ++c) G[c] = sH[c * Np + m];
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
         const T ej = ph.eta * invJ;
@@ -257,14 +262,14 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
         Dot<T> lf;
 #pragma unroll
         for (int c = 0; c < N; ++c) lf.add(l[c] * hh[c], sW[(f * 3 + jj) * Np + r + Nt * c]);
-        const T lfac = lf.get();
+        const T lfac = lf.raw();
 #pragma unroll 1
         for (int v = 0; v < 5; ++v) {
           Dot<T> acc;
 #pragma unroll
           for (int c = 0; c < N; ++c) acc.add(l[c], sG[(jj * 5 + v) * Np + r + Nt * c]);
           acc.add(lfac, sdQ[(f * 5 + v) * Nf + r]);
-          dst[(jj * 5 + v) * Nf] = acc.get();
+          dst[(jj * 5 + v) * Nf] = acc.raw();
         }
       } else {
         const int a = r % N, b = r / N;
@@ -279,7 +284,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
             acc.add(Ea[j], g[j]);
             acc.add(Ea[j] * w[j], lq[v * Np + j]);
           }
-          dst[(jj * 5 + v) * Nf] = acc.get();
+          dst[(jj * 5 + v) * Nf] = acc.raw();
         }
       }
     }
@@ -299,7 +304,7 @@ __device__ __forceinline__ void prism_volume_body(int64_t e, int tid, int nth, b
       }
 #pragma unroll
       for (int c = 0; c < N; ++c) acc.add(D1t[c], h2[Nt * c]);
-      out[v] = acc.get();
+      out[v] = acc.raw();
     }
   }
 }
