@@ -531,8 +531,17 @@ __device__ __forceinline__ void volume_body(int64_t e, int tid, int nth, bool ac
   }
 }
 
+// Resident blocks at p = 5 and 6: 3 blocks of 224 and (double-float) 2 of 352 threads at 80
+// registers, with some spills, measured faster than the register-limited 2 and 1 (double-float
+// p = 6: 9.16 -> 7.73 ms per launch at 40^3; p = 5: 8.80 -> 8.61 ms at 48^3; FP64 p = 5: 25.63 ->
+// 25.26 ms; FP64 p = 6 unchanged at 2 blocks, so it keeps 1).
+template <int N, typename T>
+constexpr int volume_min_blocks_of() {
+  return N == 6 ? 3 : ((N == 7 && !std::is_same<T, double>::value) ? 2 : volume_min_blocks<N>());
+}
+
 template <int N, typename T, bool FP32V = false>
-__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks<N>())
+__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks_of<N, T>())
     k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
              const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
              DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out,
