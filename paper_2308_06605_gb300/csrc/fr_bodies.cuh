@@ -540,8 +540,16 @@ constexpr int volume_min_blocks_of() {
   return N == 6 ? 3 : ((N == 7 && !std::is_same<T, double>::value) ? 2 : volume_min_blocks<N>());
 }
 
+// With the viscous branch in FP32 (96 registers, no spills) the kernels of p = 3 and 4 fit 10 and
+// 5 blocks per SM, which hides more of their load latency (p = 4: 6.44 -> 5.96 ms per launch at
+// 64^3; p = 3: 3.27 -> 3.00 ms); the double-float ones measured slower at those counts.
+template <int N, typename T, bool FP32V>
+constexpr int volume_min_blocks_v() {
+  return (FP32V && N == 5) ? 5 : ((FP32V && N == 4) ? 10 : volume_min_blocks_of<N, T>());
+}
+
 template <int N, typename T, bool FP32V = false>
-__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks_of<N, T>())
+__global__ void __launch_bounds__(volume_threads<N>(), volume_min_blocks_v<N, T, FP32V>())
     k_volume(const T *__restrict__ Q, const T *__restrict__ metrics, const int32_t *__restrict__ ef,
              const T *__restrict__ Qtr, const T *__restrict__ liftfac, T *__restrict__ Gtr, T *__restrict__ Rpart,
              DevPhys dph, const double *__restrict__ hel, float *__restrict__ nu_out,
