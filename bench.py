@@ -676,8 +676,7 @@ def run_ours(args):
 # DRAM traffic per launch of the dominant kernel from ncu captures (precision, p, n_edge, kernel)
 # -> bytes; scaled from a 32^3 capture by the element count.  Only valid for the kernel version
 # that was profiled.
-TRAFFIC = {("fp64", 4, 64, "volume"): 8 * 1.52181e9, ("mixed", 4, 64, "volume"): 8 * 1.51813e9,
-           ("mixed_vf32", 4, 64, "volume"): 8 * 1.51921e9}
+TRAFFIC = {("fp64", 4, 64, "volume"): 8 * 1.52181e9, ("mixed", 4, 64, "volume"): 8 * 1.51813e9}
 
 
 def main():
