@@ -132,7 +132,7 @@ typedef struct {
                            the viscous terms amplified by the second derivative: about 1e-6 of the
                            viscous part of the residual, so relative to the residual it grows
                            like 1/Re and with the viscous share (measured normwise <= 7.7e-7 per
-                           variable on perturbed TGV states at Re >= 400, p <= 7; 1.9e-6 at the
+                           variable on perturbed TGV states at Re >= 400, p <= 7; 2.1e-6 at the
                            initial TGV state at Re 1600, whose residual is almost purely viscous;
                            1e-5 at Re = 20).  c = 0 only (FR_EUNSUPPORTED otherwise); prisms keep
                            double-float; not in fr_batch_create */
