@@ -74,8 +74,9 @@ def bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dict:
         vol += per_el(2 * 6 * Nf * 5)                                 # own + other traces
         vol += per_el(6 * 3 * Nf) + per_el(6 * 15 * Nf)               # lift factors, gradient traces
     b["volume"] = vol
-    # Interfaces: 3 per element.
-    iface = 3 * Nf * (2 * 5 + 3 + 5 + (2 * 15 if viscous else 0))
+    # Interfaces: 3 per element; two trace slots, the area-scaled normal and |n|, the common flux,
+    # two gradient-trace slots.
+    iface = 3 * Nf * (2 * 5 + 4 + 5 + (2 * 15 if viscous else 0))
     b["iface_flux"] = per_el(iface)
     corr = per_el(5 * Np) + per_el(3 * Nf * 5) + per_el(Np)          # Rpart, common flux, 1/|J|
     corr += per_el(5 * Np) * (4 if mode == "rk" else 1)                # Un, acc r/w, Q write (RK)
@@ -122,7 +123,7 @@ def prism_bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dic
     if viscous:
         vol += per_el(2 * 5 * fp) + per_el(15 * fp)
     b["volume"] = vol
-    b["iface_flux"] = per_el(fp / 2 * (2 * 5 + 3 + 5 + (2 * 15 if viscous else 0)))
+    b["iface_flux"] = per_el(fp / 2 * (2 * 5 + 4 + 5 + (2 * 15 if viscous else 0)))
     corr = per_el(5 * Np) + per_el(fp / 2 * 5) + per_el(Np)
     corr += per_el(5 * Np) * (4 if mode == "rk" else 1)
     b["correct"] = corr
