@@ -296,10 +296,10 @@ fr_status fr_max_dt(fr_mesh *mesh, double cfl, double *dt);
 /*
  * Domain decomposition (paper, section "Pre-processing": the mesh is distributed over processes,
  * the faces on partition boundaries are paired (Algorithm 2, "MatchMPIFaces"), and every step
- * exchanges the data of those faces).  Hexahedral meshes.  A part holds its own elements and
- * every interface touching them; an interface shared with another part (a halo interface) keeps
- * the global mesh's record, so each part writes its own side's traces and receives the other
- * side's from the peer.  BR2 and LDG are compact, so one exchange of solution traces (before the
+ * exchanges the data of those faces).  Hexahedral and mixed hexahedral/prismatic meshes.  A part
+ * holds its own elements and every interface touching them; an interface shared with another
+ * part (a halo interface) keeps the global mesh's record, so each part writes its own side's
+ * traces and receives the other side's from the peer.  BR2 and LDG are compact, so one exchange of solution traces (before the
  * volume kernel needs the jumps) and one of gradient traces (before the interface fluxes) per
  * stage make each part's residual equal to the residual of the whole mesh restricted to the part.
  */
@@ -325,16 +325,16 @@ fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part)
  * work).  info is filled; each array may be NULL: peers [n_peers] (ascending), peer_begin
  * [n_peers + 1] (halo entries of peer k are [peer_begin[k], peer_begin[k+1])), gid [n_halo] (the
  * global interface number of each halo entry; ascending within a peer), elem_global [n_elem] (the
- * input index of each local element; local elements are in input order).  The halo entries a part
- * sends to a peer and those the peer receives from it are the same interfaces in the same order.
- * FR_EUNSUPPORTED for meshes with prisms; FR_EINVAL for a negative part id or an empty part.
+ * input index of each local element; local elements are in input order: the part's hexahedra,
+ * then its prisms).  The halo entries a part sends to a peer and those the peer receives from it
+ * are the same interfaces in the same order.  FR_EINVAL for a negative part id or an empty part.
  */
 fr_status fr_part_inspect(const fr_mesh_desc *desc, const int32_t *part, int32_t rank, fr_part_info *info,
                           int32_t *peers, int64_t *peer_begin, int64_t *gid, int64_t *elem_global);
 
 /*
- * fr_mesh_create_part — the mesh of part `rank` of the partition `part` ([n_hex] host array, ids
- * >= 0), on the current device.  States, residuals and fr_solution_points are in the part's local
+ * fr_mesh_create_part — the mesh of part `rank` of the partition `part` ([n_hex + n_prism] host
+ * array, ids >= 0), on the current device.  States, residuals and fr_solution_points are in the part's local
  * element order (elem_global of fr_halo_query maps them to input indices).  A part without halo
  * interfaces behaves like fr_mesh_create; a part with them runs its stages through fr_part_phase
  * (fr_residual, fr_rk_stage, fr_residual_static and fr_batch_create return FR_EUNSUPPORTED for it)

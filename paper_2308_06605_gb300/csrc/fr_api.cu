@@ -712,7 +712,6 @@ static fr_status build_part(const fr_mesh_desc *desc, const int32_t *part, int32
   const int64_t n = desc->n_hex + desc->n_prism;
   for (int64_t e = 0; e < n; ++e)
     if (part[e] < 0) return fail(nullptr, FR_EINVAL, "negative part id");
-  if (desc->n_prism > 0) return fail(nullptr, FR_EUNSUPPORTED, "domain decomposition is built for hexahedral meshes");
   HostMesh g;
   std::string err;
   fr_status st;
@@ -727,7 +726,7 @@ static fr_status build_part(const fr_mesh_desc *desc, const int32_t *part, int32
 }
 
 static void fill_part_info(const HostMesh &h, const HaloLists &halo, fr_part_info *info) {
-  info->n_elem = h.E;
+  info->n_elem = h.E + h.Ep;
   info->n_iface = h.n_interior;
   info->n_bface = h.n_if - h.n_interior;
   info->n_peers = (int32_t)halo.peers.size();
@@ -792,14 +791,14 @@ extern "C" fr_status fr_halo_query(const fr_mesh *m, fr_part_info *info, int32_t
                                    int64_t *gid, int64_t *elem_global) {
   if (!m || !info) return FR_EINVAL;
   if (!m->is_part) {
-    info->n_elem = m->host.E;
+    info->n_elem = m->host.E + m->host.Ep;
     info->n_iface = m->host.n_interior;
     info->n_bface = m->host.n_if - m->host.n_interior;
     info->n_peers = 0;
     info->n_halo = 0;
     if (peer_begin) peer_begin[0] = 0;
     if (elem_global)
-      for (int64_t e = 0; e < m->host.E; ++e) elem_global[e] = e;
+      for (int64_t e = 0; e < m->host.E + m->host.Ep; ++e) elem_global[e] = e;
     return FR_OK;
   }
   fill_part_info(m->host, m->halo, info);

@@ -77,24 +77,27 @@ fr_status partition_elements(const std::vector<double> &cent, const std::vector<
 
 fr_status extract_part(const HostMesh &g, const std::vector<int32_t> &part, int rank, HostMesh &m, HaloLists &halo,
                        std::string &err) {
-  if (g.Ep > 0) {
-    err = "domain decomposition is built for hexahedral meshes";
-    return FR_EUNSUPPORTED;
-  }
-  if ((int64_t)part.size() != g.E) {
+  const int64_t G = g.E + g.Ep;   // global elements: hexahedra, then prisms
+  if ((int64_t)part.size() != G) {
     err = "partition has the wrong length";
     return FR_EINVAL;
   }
-  const int Np = g.Np, Nf = g.Nf;
-  std::vector<int64_t> g2l((size_t)g.E, -1);
+  const int Np = g.Np, Nf = g.Nf, Npp = g.Npp;
+  // Local numbering keeps the global layout: the part's hexahedra, then its prisms.
+  std::vector<int64_t> g2l((size_t)G, -1);
   halo = HaloLists{};
+  int64_t E = 0, Ep = 0;
   for (int64_t e = 0; e < g.E; ++e)
     if (part[e] == rank) {
-      g2l[e] = (int64_t)halo.elem_global.size();
+      g2l[e] = E++;
       halo.elem_global.push_back(e);
     }
-  const int64_t E = (int64_t)halo.elem_global.size();
-  if (E == 0) {
+  for (int64_t e = g.E; e < G; ++e)
+    if (part[e] == rank) {
+      g2l[e] = E + Ep++;
+      halo.elem_global.push_back(e);
+    }
+  if (E + Ep == 0) {
     err = "the part owns no element";
     return FR_EINVAL;
   }
@@ -140,19 +143,34 @@ fr_status extract_part(const HostMesh &g, const std::vector<int32_t> &part, int 
   m.ef.resize((size_t)E * 6);
   m.metrics.resize((size_t)E * 10 * Np);
   m.liftfac.resize((size_t)E * 6 * 3 * Nf);
-  m.xsol.resize((size_t)E * Np * 3);
-  m.h.resize((size_t)E);
+  m.xsol.resize(((size_t)E * Np + (size_t)Ep * Npp) * 3);
+  m.h.resize((size_t)(E + Ep));
+  auto remap = [&](int32_t packed) { return (int32_t)((gif2l[packed >> 4] << 4) | (packed & 15)); };
   for (int64_t le = 0; le < E; ++le) {
     const int64_t e = halo.elem_global[le];
-    for (int f = 0; f < 6; ++f) {
-      const int32_t packed = g.ef[e * 6 + f];
-      const int64_t I = packed >> 4;
-      m.ef[le * 6 + f] = (int32_t)((gif2l[I] << 4) | (packed & 15));
-    }
+    for (int f = 0; f < 6; ++f) m.ef[le * 6 + f] = remap(g.ef[e * 6 + f]);
     std::copy_n(g.metrics.begin() + e * 10 * Np, 10 * Np, m.metrics.begin() + le * 10 * Np);
     std::copy_n(g.liftfac.begin() + e * 18 * Nf, 18 * Nf, m.liftfac.begin() + le * 18 * Nf);
     std::copy_n(g.xsol.begin() + e * Np * 3, Np * 3, m.xsol.begin() + le * Np * 3);
     m.h[le] = g.h[e];
+  }
+  if (g.Ep > 0) {
+    m.Ep = Ep;
+    m.Nt = g.Nt;
+    m.Npp = Npp;
+    m.ptab = g.ptab;
+    m.tri_slot = g.tri_slot;
+    m.ef_p.resize((size_t)Ep * 5);
+    m.metrics_p.resize((size_t)Ep * 10 * Npp);
+    for (int64_t lp = 0; lp < Ep; ++lp) {
+      const int64_t e = halo.elem_global[E + lp], ep = e - g.E;
+      for (int f = 0; f < 5; ++f) m.ef_p[lp * 5 + f] = remap(g.ef_p[ep * 5 + f]);
+      std::copy_n(g.metrics_p.begin() + ep * 10 * Npp, 10 * Npp, m.metrics_p.begin() + lp * 10 * Npp);
+      std::copy_n(g.xsol.begin() + (g.E * Np + ep * Npp) * 3, Npp * 3, m.xsol.begin() + (E * Np + lp * Npp) * 3);
+      m.h[E + lp] = g.h[e];
+    }
+    m.if_tri.resize((size_t)n_if);
+    for (int64_t li = 0; li < n_if; ++li) m.if_tri[li] = g.if_tri[l2g_if[li]];
   }
   m.if_bc.resize((size_t)n_if);
   m.if_elem.resize((size_t)n_if * 2);

@@ -135,6 +135,63 @@ def test_partitioned_rk44_steps_equal_whole_mesh(precision):
         whole.close()
 
 
+class MixedParts(Parts):
+    """Parts of a mesh with prisms: states and residuals are [n_points][5] (hexahedral points,
+    then prism points); each part's rows are its elements' point ranges."""
+
+    def __init__(self, desc, phys, p, n_parts, E, Np, Npp):
+        super().__init__(desc, phys, p, n_parts)
+        self.rows = []
+        for h in self.halo:
+            eg = np.asarray(h["elem_global"])
+            self.rows.append(np.concatenate(
+                [e * Np + np.arange(Np) if e < E else E * Np + (e - E) * Npp + np.arange(Npp) for e in eg]))
+
+    def set_state(self, Q):
+        for m, rows in zip(self.meshes, self.rows):
+            m.set_state(np.ascontiguousarray(Q[rows].reshape(m.shape)))
+
+    def gather(self, arrays, shape):
+        out = np.empty(shape)
+        for a, rows in zip(arrays, self.rows):
+            out[rows] = np.asarray(a).reshape(-1, 5)
+        return out
+
+
+@pytest.mark.parametrize("split", ["checker", "all"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_partitioned_mixed_mesh_equals_whole_mesh(split, precision):
+    """Hexahedra and prisms across part boundaries (triangular and quadrilateral halo
+    interfaces): residual and two RK44 steps equal to the whole mesh's, bit for bit."""
+    torch = pytest.importorskip("torch")
+    ensure_lib()
+    desc = I.hex_box_mesh((4, 4, 3), prisms=split, seed=2)
+    phys = I.tgv_physics(Ma=0.2, Re=400.0)
+    phys.precision = precision
+    p = 3
+    with fr.Mesh(desc, phys, p) as whole:
+        Q = np.ascontiguousarray(I.tgv_state(whole.solution_points(), Ma=0.2, perturb=1e-2, seed=3))
+        whole.set_state(Q)
+        R_whole = whole.residual()
+        dt = whole.max_dt(0.3)
+        parts = MixedParts(desc, phys, p, 3, whole.n_elem, whole.n_pts, whole.n_pts_prism)
+        try:
+            assert all(h["n_halo"] > 0 for h in parts.halo)
+            parts.set_state(Q)
+            Rd = [torch.empty(m.shape, dtype=torch.float64, device="cuda") for m in parts.meshes]
+            parts.stage(R=Rd)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(parts.gather([r.cpu().numpy() for r in Rd], R_whole.shape), R_whole)
+            for _ in range(2):
+                whole.rk_step(0.0, dt)
+                for st in range(4):
+                    parts.stage(fr.FR_RK44, st, dt)
+            got = parts.gather([m.get_state() for m in parts.meshes], Q.shape)
+            np.testing.assert_array_equal(got, whole.get_state())
+        finally:
+            parts.close()
+
+
 def test_part_refusals_and_single_part():
     torch = pytest.importorskip("torch")
     ensure_lib()

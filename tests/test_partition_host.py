@@ -84,10 +84,44 @@ def test_partition_refusals():
     with pytest.raises(fr.FRError) as ei:
         fr.part_inspect(d, 2, np.zeros(36, np.int32), 1)        # part 1 owns nothing
     assert ei.value.status == fr.FR_EINVAL
-    dp = I.hex_box_mesh((2, 2, 2), prisms="all")
-    with pytest.raises(fr.FRError) as ei:
-        fr.part_inspect(dp, 2, np.zeros(16, np.int32), 0)
-    assert ei.value.status == fr.FR_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("split", ["checker", "all"])
+def test_halo_lists_match_on_mixed_meshes(split):
+    """Hexahedra and prisms (checkerboard columns, or every column split): the parts own every
+    element once (hexahedra first, then prisms, each in input order), the halo lists of every
+    pair agree, and each global interface is internal to one part or shared by exactly two."""
+    d = I.hex_box_mesh((4, 4, 3), prisms=split, seed=2)
+    p, n_parts = 3, 3
+    part = fr.partition(d, p, n_parts)
+    g = fr.inspect(d, p)
+    E, Ep = g["n_elem"], g["n_prism"]
+    info = [fr.part_inspect(d, p, part, r) for r in range(n_parts)]
+    owned = np.concatenate([h["elem_global"] for h in info])
+    assert np.array_equal(np.sort(owned), np.arange(E + Ep))
+    for r, h in enumerate(info):
+        eg = np.asarray(h["elem_global"])
+        assert np.array_equal(eg, np.sort(eg)) and np.all(part[eg] == r)
+    side_elem = {}
+    for e in range(E):
+        for f in range(6):
+            side_elem.setdefault(int(g["ef"][e, f]) >> 4, []).append(e)
+    for ep in range(Ep):
+        for f in range(5):
+            side_elem.setdefault(int(g["ef_prism"][ep, f]) >> 4, []).append(E + ep)
+    seen = np.zeros(g["n_iface"], dtype=int)
+    for r, h in enumerate(info):
+        for k, q in enumerate(h["peers"]):
+            mine = h["gid"][h["peer_begin"][k]:h["peer_begin"][k + 1]]
+            kk = list(info[q]["peers"]).index(r)
+            theirs = info[q]["gid"][info[q]["peer_begin"][kk]:info[q]["peer_begin"][kk + 1]]
+            assert np.array_equal(mine, theirs) and np.all(np.diff(mine) > 0)
+            seen[mine] += 1
+    for I_ in range(g["n_iface"]):
+        assert seen[I_] == (0 if len({int(part[e]) for e in side_elem[I_]}) == 1 else 2)
+    for r, h in enumerate(info):
+        internal = sum(1 for I_ in range(g["n_iface"]) if {int(part[e]) for e in side_elem[I_]} == {r})
+        assert h["n_iface"] == internal + h["n_halo"]
 
 
 def _slot(code, a, b, N):
