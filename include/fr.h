@@ -321,6 +321,16 @@ typedef struct {
 fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part);
 
 /*
+ * fr_partition_cost — fr_partition with each element weighted by its solution points times the
+ * cost of one point of its type: cost_hex for hexahedra, cost_prism for prisms (any positive unit,
+ * e.g. the measured time per point of each type at this order and arithmetic, or the algorithmic
+ * flops per point), so parts of mixed meshes balance work rather than points.  FR_EINVAL for a
+ * cost that is not finite and positive; otherwise as fr_partition.
+ */
+fr_status fr_partition_cost(const fr_mesh_desc *desc, int32_t n_parts, double cost_hex, double cost_prism,
+                            int32_t *part);
+
+/*
  * fr_part_inspect — host only: what fr_mesh_create_part would build for part `rank` (no device
  * work).  info is filled; each array may be NULL: peers [n_peers] (ascending), peer_begin
  * [n_peers + 1] (halo entries of peer k are [peer_begin[k], peer_begin[k+1])), gid [n_halo] (the

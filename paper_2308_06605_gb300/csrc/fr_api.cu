@@ -691,18 +691,33 @@ static fr_status check_desc_arrays(const fr_mesh_desc *desc) {
   return FR_OK;
 }
 
-extern "C" fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part) {
+// Partition with element weights: the solution-point count of each element, or, when the costs
+// per solution point of a hexahedron and of a prism are given (> 0), that count times the cost.
+static fr_status partition_weighted(const fr_mesh_desc *desc, int32_t n_parts, double cost_hex, double cost_prism,
+                                    int32_t *part) {
   if (!desc || !part) return fail(nullptr, FR_EINVAL, "desc or part is NULL");
+  if (!(cost_hex > 0.0) || !(cost_prism > 0.0) || !std::isfinite(cost_hex) || !std::isfinite(cost_prism))
+    return fail(nullptr, FR_EINVAL, "costs per solution point must be finite and positive");
   if (fr_status sv = check_desc_arrays(desc); sv != FR_OK) return sv;
   if (fr_status sv = check_vertex_ids(desc); sv != FR_OK) return sv;
   std::vector<double> cent, w;
   std::vector<int32_t> pv;
   std::string err;
   element_centroids(desc, cent, w);
+  for (int64_t e = 0; e < (int64_t)w.size(); ++e) w[e] *= e < desc->n_hex ? cost_hex : cost_prism;
   fr_status st = partition_elements(cent, w, n_parts, pv, err);
   if (st != FR_OK) return fail(nullptr, st, err);
   std::memcpy(part, pv.data(), pv.size() * sizeof(int32_t));
   return FR_OK;
+}
+
+extern "C" fr_status fr_partition(const fr_mesh_desc *desc, int32_t n_parts, int32_t *part) {
+  return partition_weighted(desc, n_parts, 1.0, 1.0, part);
+}
+
+extern "C" fr_status fr_partition_cost(const fr_mesh_desc *desc, int32_t n_parts, double cost_hex, double cost_prism,
+                                       int32_t *part) {
+  return partition_weighted(desc, n_parts, cost_hex, cost_prism, part);
 }
 
 // Host build of part `rank`: the global connectivity, then the part and its halo lists.

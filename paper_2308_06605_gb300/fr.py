@@ -111,6 +111,7 @@ SIGNATURES = {
     "fr_batch_free": (None, [C.c_void_p]),
     "fr_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fr_partition": (C.c_int, [C.POINTER(fr_mesh_desc), C.c_int32, C.c_void_p]),
+    "fr_partition_cost": (C.c_int, [C.POINTER(fr_mesh_desc), C.c_int32, C.c_double, C.c_double, C.c_void_p]),
     "fr_part_inspect": (C.c_int, [C.POINTER(fr_mesh_desc), C.c_void_p, C.c_int32, C.POINTER(fr_part_info),
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_mesh_create_part": (C.c_int, [C.POINTER(fr_mesh_desc), C.POINTER(fr_physics), C.c_void_p, C.c_int32,
@@ -419,12 +420,17 @@ class Mesh:
         self.close()
 
 
-def partition(desc: MeshDesc, p: int, n_parts: int) -> np.ndarray:
-    """fr_partition: part id of every element (recursive coordinate bisection; host only)."""
+def partition(desc: MeshDesc, p: int, n_parts: int, cost=None) -> np.ndarray:
+    """fr_partition: part id of every element (recursive coordinate bisection; host only),
+    balancing solution points, or with cost = (per hexahedral point, per prism point) the work
+    (fr_partition_cost)."""
     lib = load()
     d, keep = _describe(desc, p)
     part = np.zeros(d.n_hex + d.n_prism, dtype=np.int32)
-    st = lib.fr_partition(C.byref(d), n_parts, C.c_void_p(part.ctypes.data))
+    if cost is None:
+        st = lib.fr_partition(C.byref(d), n_parts, C.c_void_p(part.ctypes.data))
+    else:
+        st = lib.fr_partition_cost(C.byref(d), n_parts, float(cost[0]), float(cost[1]), C.c_void_p(part.ctypes.data))
     if st != FR_OK:
         raise FRError(st, lib.fr_last_error(None).decode())
     del keep

@@ -111,6 +111,12 @@ def prism_flops_per_point(p: int, viscous: bool = True) -> dict:
     return f
 
 
+def point_cost(p: int, viscous: bool = True) -> tuple:
+    """(hexahedral, prism) algorithmic flops of one solution point through one stage: the
+    per-type costs for fr_partition_cost."""
+    return (sum(flops_per_point(p, viscous).values()), sum(prism_flops_per_point(p, viscous).values()))
+
+
 def prism_bytes_per_point(p: int, viscous: bool = True, mode: str = "rk") -> dict:
     N = p + 1
     Nt = N * (N + 1) // 2

@@ -124,6 +124,35 @@ def test_halo_lists_match_on_mixed_meshes(split):
         assert h["n_iface"] == internal + h["n_halo"]
 
 
+def _part_work(desc, p, part, n_parts, cost):
+    g = fr.inspect(desc, p)
+    E = g["n_elem"]
+    w = np.r_[np.full(E, g["n_pts"] * cost[0]), np.full(g["n_prism"], g["n_pts_prism"] * cost[1])]
+    return np.bincount(part, weights=w, minlength=n_parts)
+
+
+def test_cost_weighted_partition_balances_work_on_mixed_meshes():
+    """fr_partition_cost: unit costs reproduce fr_partition; with a prism point costing more (the
+    algorithmic flops per point of each type) the parts' work is at least as balanced as with the
+    point-count partition, and the cut moves."""
+    from paper_2308_06605_gb300 import perfmodel as PM
+    d = I.hex_box_mesh((6, 5, 4), prisms="checker", seed=7)
+    p, n_parts = 4, 4
+    assert np.array_equal(fr.partition(d, p, n_parts, cost=(1.0, 1.0)), fr.partition(d, p, n_parts))
+    cost = PM.point_cost(p)
+    assert cost[1] > 2 * cost[0]
+    by_points = fr.partition(d, p, n_parts)
+    by_work = fr.partition(d, p, n_parts, cost=cost)
+    assert not np.array_equal(by_points, by_work)
+    imb = lambda w: w.max() / w.mean()                                   # noqa: E731
+    assert imb(_part_work(d, p, by_work, n_parts, cost)) <= imb(_part_work(d, p, by_points, n_parts, cost)) + 1e-12
+    assert imb(_part_work(d, p, by_work, n_parts, cost)) < 1.1
+    for bad in ((0.0, 1.0), (1.0, -2.0), (float("nan"), 1.0), (1.0, float("inf"))):
+        with pytest.raises(fr.FRError) as ei:
+            fr.partition(d, p, n_parts, cost=bad)
+        assert ei.value.status == fr.FR_EINVAL
+
+
 def _slot(code, a, b, N):
     if code & 4:
         a, b = b, a
